@@ -1,0 +1,18 @@
+"""FP64 CPU oracle for the binned local linear FPCA smoother (test infrastructure).
+
+This package is test infrastructure only. It is the plain, slow, obviously
+correct statement of what the CUDA path computes, written from the paper
+(Chen & Jiang, "Multi-dimensional Functional Principal Component Analysis",
+Sections 2-3). Only the test suite, the smoke check and the benchmark's
+CPU-baseline arm may import it; the library path never does, and it shares no
+code with the CUDA sources.
+
+Modules
+  smoother  binning (Section 3.2), local linear smoothers Eq. (2.3)-(2.4),
+            per-point solve and status
+  eigen     matrixisation and rescaling (Section 3.1, Eq. 3.1) and the random
+            projection (Section 3.4)
+  cv        cross-validation of the covariance bandwidth (Section 3.3)
+  mlp       the bandwidth-proposal network (forward, manual backward, AdamW)
+"""
+from . import smoother, eigen, cv  # noqa: F401
