@@ -1,0 +1,203 @@
+/*
+ * fpca.h -- C ABI of the GB300 (sm_103a) binned local linear FPCA smoother.
+ *
+ * The library estimates the mean mu(t) and the 2d-dimensional covariance
+ * surface Gamma(s,t) of functional data observed on a d-dimensional domain
+ * (Chen & Jiang, "Multi-dimensional Functional Principal Component
+ * Analysis"): binning (Section 3.2), the local linear smoothers Eq. (2.3) and
+ * Eq. (2.4), matrixisation (Section 3.1, Eq. 3.1) and the random-projection
+ * eigendecomposition (Section 3.4).
+ *
+ * Conventions (every entry point)
+ *  - Array arguments are DEVICE pointers allocated and owned by the caller,
+ *    unless the comment says "host".  The library never frees them.
+ *  - Work is queued on the context's CUDA stream and returns before it
+ *    finishes; results are valid after fpca_sync() or a later stream sync.
+ *  - Argument checks are synchronous: a bad argument returns
+ *    FPCA_E_INVALID_ARG (or FPCA_E_UNSUPPORTED for a valid but unbuilt
+ *    combination) with a message in fpca_last_error(); nothing is launched.
+ *  - Device-side failures (a bounded wait that ran out, a CUDA launch
+ *    error) are recorded in a device error word and returned by the next
+ *    fpca_sync(): FPCA_E_TIMEOUT or FPCA_E_CUDA.
+ *  - Nothing aborts, exits or throws across this interface.
+ *  - A singular local system is not an error: it is reported per output
+ *    point in a status array (FPCA_PT_*).
+ *
+ * Grid: d in {1,2,3}; bins [k/M, (k+1)/M) per axis (last bin closed),
+ * centres (k + 1/2)/M, flattened in C order (axis 0 slowest).  P = prod M_k.
+ * The covariance grid is P x P, row = s, column = t.
+ */
+#ifndef FPCA_H
+#define FPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FPCA_OK = 0,
+  FPCA_E_INVALID_ARG = 1,
+  FPCA_E_UNSUPPORTED = 2,
+  FPCA_E_CUDA = 3,
+  FPCA_E_OOM = 4,
+  FPCA_E_TIMEOUT = 5,
+  FPCA_E_NUMERIC = 6
+} fpca_status;
+
+/* Arithmetic of a stage.
+ *  F64   FP64 throughout (CUDA cores).
+ *  F32   FP32 moment sums, FP32 local solve escalated to FP64 where a pivot
+ *        ratio falls below 1e-2.
+ *  F32C  as F32 with Kahan-compensated moment sums.
+ *  BF16  binning products on tcgen05 tensor cores, BF16 operands, FP32
+ *        accumulation in tensor memory; pair counts stay exact integers. */
+typedef enum { FPCA_F64 = 0, FPCA_F32 = 1, FPCA_BF16 = 2, FPCA_F32C = 4 } fpca_prec;
+
+/* Per-point status of a local fit (uint8 arrays). */
+enum { FPCA_PT_OK = 0, FPCA_PT_FALLBACK = 1, FPCA_PT_EMPTY = 2 };
+
+/* Data layouts. */
+enum { FPCA_DENSE = 0, FPCA_SPARSE = 1 };
+/* Covariance responses: residual products R R with R = Y - mu_hat
+ * (Gamma_hat = b0), or raw products Y Y as printed in Eq. (2.4)
+ * (Gamma_hat = b0 - mu_hat(s) mu_hat(t)). */
+enum { FPCA_COV_RESIDUAL = 0, FPCA_COV_RAW = 1 };
+
+typedef struct {
+  int d;      /* 1..3 */
+  int m[3];   /* bins per axis (entries beyond d ignored) */
+} fpca_grid;
+
+/* Observations, Eq. (2.2): Y_ij = X_i(t_ij) + eps_ij.
+ *  Dense (functional data on the grid nodes): y is n x P row-major, FP64
+ *    (y_prec = FPCA_F64) or FP32 (FPCA_F32); mask is n x P uint8 (1 =
+ *    observed) or NULL for fully observed data.
+ *  Sparse (longitudinal data): subject i owns observations
+ *    offs[i] .. offs[i+1]-1; t is N x d FP64 locations in [0,1]^d, y is N
+ *    FP64 values.  Locations are binned by floor(t M) clamped to M-1. */
+typedef struct {
+  int layout;              /* FPCA_DENSE or FPCA_SPARSE */
+  int n;                   /* subjects */
+  const void* y;
+  int y_prec;
+  const uint8_t* mask;     /* dense only, may be NULL */
+  const int64_t* offs;     /* sparse only: n + 1 entries */
+  const double* t;         /* sparse only: N x d */
+} fpca_data;
+
+/* Covariance bins of Eq. (2.4), fold-major: F = max(nfold, 1) slices of
+ * P x P, slice f holding the pairs of subjects in fold f.  Element type of
+ * w, v, q: double when prec == FPCA_F64, float otherwise. */
+typedef struct {
+  int nfold;
+  int prec;
+  const int32_t* cnt;      /* F x P x P pair counts, exact */
+  const void* w;           /* sum of subject weights 1/(N_i(N_i-1)) */
+  const void* v;           /* sum of weighted response products */
+  const void* q;           /* sum of weighted squared products (CV), or NULL */
+} fpca_covbins;
+
+typedef struct fpca_ctx fpca_ctx;
+
+/* Context: binds a device and a stream (NULL = the legacy default stream)
+ * and owns a workspace that grows on demand.  Returns FPCA_E_CUDA if the
+ * device cannot be used and FPCA_E_UNSUPPORTED if it is not sm_103. */
+fpca_status fpca_create(fpca_ctx** ctx, int device, void* cuda_stream);
+void fpca_destroy(fpca_ctx* ctx);
+fpca_status fpca_set_stream(fpca_ctx* ctx, void* cuda_stream);
+/* Text of the last error on this context ("" if none); owned by ctx. */
+const char* fpca_last_error(const fpca_ctx* ctx);
+/* Waits for the stream and returns the first recorded device-side error. */
+fpca_status fpca_sync(fpca_ctx* ctx);
+/* Number of kernels this context has launched so far (host counter). */
+uint64_t fpca_launch_count(const fpca_ctx* ctx);
+
+/* Mean bins with the 1/N_i weights of Eq. (2.3) (Section 3.2 binning).
+ * Outputs (length P each): cnt = observations per bin (exact);
+ * w = sum_i n_ib / N_i; v = sum_i sum_{j in b} Y_ij / N_i;
+ * v2 = sum_i sum_{j in b} Y_ij^2 / N_i (may be NULL).  Subjects with
+ * N_i = 0 are skipped. */
+fpca_status fpca_bin_mean(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                          int32_t* cnt, double* w, double* v, double* v2);
+
+/* Local linear mean, Eq. (2.3), at every bin centre from the mean bins, with
+ * the product Epanechnikov kernel and bandwidths h[0..d-1] (host).  The
+ * kernel's support is |c - x| < h per axis; a point whose window holds
+ * fewer than d+1 non-empty bins, or whose normal matrix has a Cholesky pivot
+ * at most 1e-9 of its diagonal (natural variable order), gets the local
+ * constant fit and FPCA_PT_FALLBACK; a window without weight gets NaN and
+ * FPCA_PT_EMPTY.  FP64 throughout.  mu, status: length P. */
+fpca_status fpca_smooth_mean(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt,
+                             const double* w, const double* v, const double* h,
+                             double* mu, uint8_t* status);
+
+/* Covariance bins of Eq. (2.4) over ordered pairs j != l of one subject,
+ * subject weight 1/(N_i(N_i - 1)) (subjects with N_i < 2 skipped).
+ *  mu: the fitted mean at the bin centres (length P, FP64).
+ *  mode: FPCA_COV_RESIDUAL (products of Y - mu) or FPCA_COV_RAW (Y Y).
+ *  Dense data: C = M'M, W = M' diag(w) M, V = R' diag(w) R with the p == q
+ *   entries (only j == l pairs) set to zero.  prec FPCA_F64 uses FP64
+ *   CUDA-core products (w, v double); FPCA_BF16 uses tcgen05 tensor cores
+ *   with BF16 operands and FP32 accumulation (w, v float); counts are exact
+ *   for n < 2^24.  fold/nfold/q are not used for dense data (pass NULL/0).
+ *  Sparse data: integer-exact pair scatter; FPCA_F64 or FPCA_F32 sums.
+ *   fold (length n, values 0..nfold-1) splits the pairs into nfold slices;
+ *   q (may be NULL) receives sum w (R R)^2 for cross-validation.
+ * cnt, w, v, q are F x P x P (F = max(nfold, 1)) and are overwritten. */
+fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                         const double* mu, int prec, int mode,
+                         const int32_t* fold, int nfold,
+                         int32_t* cnt, void* w, void* v, void* q);
+
+/* Local linear covariance surface, Eq. (2.4), at every pair of bin centres,
+ * for nh bandwidths h (host, nh x d), and what the eigen step needs from it.
+ *  bins: from fpca_bin_cov; all folds are pooled for the fit.
+ *  prec: FPCA_F64, FPCA_F32 or FPCA_F32C (see fpca_prec).
+ *  mu_raw: for raw-mode bins, the fitted mean (Gamma_hat = b0 - mu mu);
+ *   NULL for residual-mode bins (Gamma_hat = b0).
+ *  gamma (optional): nh x P x P, double for FPCA_F64 else float; NaN where
+ *   EMPTY, the local constant fit where FALLBACK.
+ *  status (optional): nh x P x P uint8, rules as in fpca_smooth_mean with
+ *   2d+1 unknowns.
+ *  omega/l/y (optional, all or none): y = Sigma Omega, nh x P x l float,
+ *   with Sigma = Gamma_hat with EMPTY points set to zero (Section 3.4), omega
+ *   P x l float.
+ *  cv (optional, nfold >= 2): nh doubles, the subject-level K-fold CV score
+ *   of each bandwidth (fit on the other folds' bins, scored on the fold's
+ *   held-out products; +inf when EMPTY points hold > 1% of the held-out
+ *   weight).
+ * At least one output must be given. */
+fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
+                                    const fpca_covbins* bins, const double* h, int nh,
+                                    int prec, const double* mu_raw,
+                                    const float* omega, int l,
+                                    void* gamma, uint8_t* status, float* y, double* cv);
+
+/* Eigenpairs of the matrixised covariance (Section 3.1, Eq. 3.1):
+ * Sigma = (G + G')/2 with NaN entries and rows/columns outside the domain
+ * set to zero; lambda = theta dV, phi = psi / sqrt(dV), dV = 1/P; each
+ * eigenvector's largest-magnitude entry made positive; FVE_k =
+ * sum_{j<=k} lambda_j / (trace(Sigma) dV).
+ *  gamma: P x P, double (gamma_prec FPCA_F64) or float (FPCA_F32).
+ *  domain: P int32 mean-bin counts from fpca_bin_mean (a node is inside
+ *   Omega when its count is > 0), or NULL for the whole box.
+ *  full = 1: dense cyclic Jacobi eigensolver on Sigma (FP64; P <= 1024).
+ *  full = 0: random projection (Section 3.4) with the caller's Gaussian
+ *   test matrix omega (P x l float, l > k): Y = Sigma Omega, power_iters
+ *   rounds of Q = orth(Y), Y = Sigma Q, then Q = orth(Y), B = Q' Sigma Q and
+ *   the FP64 Jacobi eigenpairs of B (Rayleigh-Ritz).
+ * Outputs (device, FP64): evals k, evecs P x k (column-major: vector j at
+ * evecs + j*P), fve k (may be NULL). */
+fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gamma,
+                           int gamma_prec, const int32_t* domain,
+                           const float* omega, int l, int k, int power_iters, int full,
+                           double* evals, double* evecs, double* fve);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPCA_H */

@@ -147,12 +147,14 @@ def bin_cov_dense(r, mask):
     with w_i = 1/(N_i(N_i-1)).  The p == q entries hold only j == l pairs and
     are zero.  ``r`` holds the responses (residuals, or raw Y for raw mode).
     """
-    mk = np.asarray(mask).astype(np.int64)
+    mk = np.asarray(mask).astype(bool)
+    mf = mk.astype(np.float64)
     Ni = mk.sum(axis=1)
     wi = pair_weights(Ni)
-    rr = np.where(mk.astype(bool), np.asarray(r, dtype=np.float64), 0.0)
-    C = mk.T @ mk
-    W = (mk * wi[:, None]).T.astype(np.float64) @ mk.astype(np.float64)
+    rr = np.where(mk, np.asarray(r, dtype=np.float64), 0.0)
+    # 0/1 products summed in float64 are exact integers below 2^53
+    C = np.rint(mf.T @ mf).astype(np.int64)
+    W = (mf * wi[:, None]).T @ mf
     V = (rr * wi[:, None]).T @ rr
     np.fill_diagonal(C, 0)
     np.fill_diagonal(W, 0.0)

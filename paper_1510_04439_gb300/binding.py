@@ -1,0 +1,219 @@
+"""Python binding of the C ABI in include/fpca.h (argument marshalling only).
+
+Every computation runs in libfpca.so's CUDA kernels; this module only turns
+torch tensors (device memory, owned by the caller) into pointers and sizes.
+It never falls back to a CPU path: if the library is missing or no sm_103
+device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfpca.so")
+
+# fpca_status
+OK, E_INVALID_ARG, E_UNSUPPORTED, E_CUDA, E_OOM, E_TIMEOUT, E_NUMERIC = range(7)
+# fpca_prec
+F64, F32, BF16, F32C = 0, 1, 2, 4
+# per-point status
+PT_OK, PT_FALLBACK, PT_EMPTY = 0, 1, 2
+DENSE, SPARSE = 0, 1
+COV_RESIDUAL, COV_RAW = 0, 1
+
+# the symbols include/fpca.h declares
+SYMBOLS = (
+    "fpca_create", "fpca_destroy", "fpca_set_stream", "fpca_last_error", "fpca_sync",
+    "fpca_launch_count", "fpca_bin_mean", "fpca_smooth_mean", "fpca_bin_cov",
+    "fpca_smooth_cov_project", "fpca_rproj_eig",
+)
+
+
+class FpcaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fpca status {status}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("m", ctypes.c_int * 3)]
+
+    @classmethod
+    def of(cls, m):
+        g = cls()
+        g.d = len(m)
+        for k in range(3):
+            g.m[k] = int(m[k]) if k < len(m) else 1
+        return g
+
+
+class Data(ctypes.Structure):
+    _fields_ = [
+        ("layout", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("y", ctypes.c_void_p),
+        ("y_prec", ctypes.c_int),
+        ("mask", ctypes.c_void_p),
+        ("offs", ctypes.c_void_p),
+        ("t", ctypes.c_void_p),
+    ]
+
+
+class CovBins(ctypes.Structure):
+    _fields_ = [
+        ("nfold", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("cnt", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("v", ctypes.c_void_p),
+        ("q", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libfpca.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl_p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.fpca_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    lib.fpca_destroy.argtypes = [vp]
+    lib.fpca_destroy.restype = None
+    lib.fpca_set_stream.argtypes = [vp, vp]
+    lib.fpca_last_error.argtypes = [vp]
+    lib.fpca_last_error.restype = ctypes.c_char_p
+    lib.fpca_sync.argtypes = [vp]
+    lib.fpca_launch_count.argtypes = [vp]
+    lib.fpca_launch_count.restype = ctypes.c_uint64
+    lib.fpca_bin_mean.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp, vp]
+    lib.fpca_smooth_mean.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp]
+    lib.fpca_bin_cov.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32, i32, vp,
+                                 i32, vp, vp, vp, vp]
+    lib.fpca_smooth_cov_project.argtypes = [vp, ctypes.POINTER(Grid), ctypes.POINTER(CovBins),
+                                            dbl_p, i32, i32, vp, vp, i32, vp, vp, vp, vp]
+    lib.fpca_rproj_eig.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, vp, vp, i32, i32, i32, i32,
+                                   vp, vp, vp]
+    for name in SYMBOLS:
+        f = getattr(lib, name)
+        if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count"):
+            f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _doubles(vals):
+    vals = [float(x) for x in vals]
+    return (ctypes.c_double * len(vals))(*vals)
+
+
+class Context:
+    """An fpca_ctx bound to one CUDA device and a stream (torch stream or None)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        st = self.lib.fpca_create(ctypes.byref(h), int(device), s)
+        if st != OK:
+            raise FpcaError(st, "fpca_create failed (no usable sm_103 device?)")
+        self.h = h
+        self.device = torch.device("cuda", device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fpca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise FpcaError(st, self.lib.fpca_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self._check(self.lib.fpca_set_stream(self.h, None if stream is None else
+                                             ctypes.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        self._check(self.lib.fpca_sync(self.h))
+
+    @property
+    def launches(self):
+        return int(self.lib.fpca_launch_count(self.h))
+
+    # ---- data descriptors --------------------------------------------------
+    @staticmethod
+    def dense(y, mask=None):
+        d = Data()
+        d.layout = DENSE
+        d.n = int(y.shape[0])
+        d.y = y.data_ptr()
+        d.y_prec = F64 if y.dtype.itemsize == 8 else F32
+        d.mask = None if mask is None else mask.data_ptr()
+        return d
+
+    @staticmethod
+    def sparse(offs, t, y):
+        d = Data()
+        d.layout = SPARSE
+        d.n = int(offs.shape[0]) - 1
+        d.y = y.data_ptr()
+        d.y_prec = F64
+        d.offs = offs.data_ptr()
+        d.t = t.data_ptr()
+        return d
+
+    # ---- entry points --------------------------------------------------------
+    def bin_mean(self, data, m, cnt, w, v, v2=None):
+        self._check(self.lib.fpca_bin_mean(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                           _ptr(cnt), _ptr(w), _ptr(v), _ptr(v2)))
+
+    def smooth_mean(self, m, cnt, w, v, h, mu, status=None):
+        self._check(self.lib.fpca_smooth_mean(self.h, ctypes.byref(Grid.of(m)), _ptr(cnt), _ptr(w),
+                                              _ptr(v), _doubles(h), _ptr(mu), _ptr(status)))
+
+    def bin_cov(self, data, m, mu, prec, cnt, w, v, q=None, mode=COV_RESIDUAL, fold=None, nfold=0):
+        self._check(self.lib.fpca_bin_cov(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                          _ptr(mu), int(prec), int(mode), _ptr(fold), int(nfold),
+                                          _ptr(cnt), _ptr(w), _ptr(v), _ptr(q)))
+
+    def smooth_cov_project(self, m, cnt, w, v, h, prec, q=None, nfold=0, mu_raw=None, omega=None,
+                           gamma=None, status=None, y=None, cv=None):
+        bins = CovBins()
+        bins.nfold = int(nfold)
+        bins.prec = F64 if w.dtype.itemsize == 8 else F32
+        bins.cnt, bins.w, bins.v = cnt.data_ptr(), w.data_ptr(), v.data_ptr()
+        bins.q = None if q is None else q.data_ptr()
+        hs = [x for row in h for x in row]
+        nh = len(h)
+        l = 0 if omega is None else int(omega.shape[1])
+        self._check(self.lib.fpca_smooth_cov_project(
+            self.h, ctypes.byref(Grid.of(m)), ctypes.byref(bins), _doubles(hs), nh, int(prec),
+            _ptr(mu_raw), _ptr(omega), l, _ptr(gamma), _ptr(status), _ptr(y), _ptr(cv)))
+
+    def rproj_eig(self, m, gamma, k, evals, evecs, fve=None, domain=None, omega=None,
+                  power_iters=0, full=False):
+        l = 0 if omega is None else int(omega.shape[1])
+        gp = F64 if gamma.dtype.itemsize == 8 else F32
+        self._check(self.lib.fpca_rproj_eig(self.h, ctypes.byref(Grid.of(m)), _ptr(gamma), gp,
+                                            _ptr(domain), _ptr(omega), l, int(k),
+                                            int(power_iters), int(bool(full)), _ptr(evals),
+                                            _ptr(evecs), _ptr(fve)))

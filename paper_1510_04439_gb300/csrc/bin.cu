@@ -1,0 +1,354 @@
+// Binning (Section 3.2) of the sums in Eq. (2.3) and Eq. (2.4).
+//
+// Mean bins carry, per grid bin b: the observation count, W_b = sum 1/N_i and
+// V_b = sum Y_ij / N_i (V2 with Y^2).  Covariance bins carry, per ordered
+// bin pair (p, q): the pair count, W = sum w_i, V = sum w_i R_ij R_il with
+// w_i = 1/(N_i (N_i - 1)), over pairs j != l of one subject.
+#include <cuda_bf16.h>
+
+#include "fpca_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double load_y(const void* y, int prec, size_t idx) {
+  return prec == FPCA_F64 ? static_cast<const double*>(y)[idx]
+                          : static_cast<double>(static_cast<const float*>(y)[idx]);
+}
+
+__device__ __forceinline__ int bin_index(const double* t, int d, const int* m) {
+  int flat = 0;
+  for (int k = 0; k < d; ++k) {
+    double x = floor(__dmul_rn(t[k], (double)m[k]));
+    int ik = (int)fmin(fmax(x, 0.0), (double)(m[k] - 1));
+    flat = flat * m[k] + ik;
+  }
+  return flat;
+}
+
+// N_i: observed nodes of subject i (mask row sum), one block per subject.
+__global__ void k_subject_counts(int n, int P, const uint8_t* __restrict__ mask,
+                                 int32_t* __restrict__ Ni) {
+  const int i = blockIdx.x;
+  int c = 0;
+  if (mask) {
+    const uint8_t* row = mask + (size_t)i * P;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) c += row[p] != 0;
+  } else {
+    for (int p = threadIdx.x; p < P; p += blockDim.x) c += 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) Ni[i] = s;
+  }
+}
+
+// Dense mean bins: one thread per node, subjects in order (weights 1/N_i).
+__global__ void k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y_prec,
+                                 const uint8_t* __restrict__ mask,
+                                 const int32_t* __restrict__ Ni, int32_t* __restrict__ cnt,
+                                 double* __restrict__ w, double* __restrict__ v,
+                                 double* __restrict__ v2) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  int c = 0;
+  double sw = 0.0, sv = 0.0, sv2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const size_t idx = (size_t)i * P + p;
+    if (mask && !mask[idx]) continue;
+    const int N = Ni[i];
+    if (N <= 0) continue;
+    const double wi = 1.0 / (double)N;
+    const double yy = load_y(y, y_prec, idx);
+    c += 1;
+    sw = __dadd_rn(sw, wi);
+    sv = __dadd_rn(sv, __dmul_rn(wi, yy));
+    sv2 = __dadd_rn(sv2, __dmul_rn(wi, __dmul_rn(yy, yy)));
+  }
+  cnt[p] = c;
+  w[p] = sw;
+  v[p] = sv;
+  if (v2) v2[p] = sv2;
+}
+
+// Sparse mean bins: one thread per subject, atomic scatter into the bins.
+__global__ void k_bin_mean_sparse(int n, int d, int m0, int m1, int m2,
+                                  const int64_t* __restrict__ offs, const double* __restrict__ t,
+                                  const double* __restrict__ y, int32_t* cnt, double* w,
+                                  double* v, double* v2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m[3] = {m0, m1, m2};
+  const int64_t lo = offs[i], hi = offs[i + 1];
+  if (hi <= lo) return;
+  const double wi = 1.0 / (double)(hi - lo);
+  for (int64_t j = lo; j < hi; ++j) {
+    const int b = bin_index(t + j * d, d, m);
+    const double yy = y[j];
+    atomicAdd(cnt + b, 1);
+    atomicAdd(w + b, wi);
+    atomicAdd(v + b, __dmul_rn(wi, yy));
+    if (v2) atomicAdd(v2 + b, __dmul_rn(wi, __dmul_rn(yy, yy)));
+  }
+}
+
+// Operand planes of the tensor-core Gram products, K-major (subject index
+// contiguous), BF16, zero-padded to Kpad subjects:
+//   plane 0: M_ip                 (pair counts  C = M'M)
+//   plane 1: w_i M_ip             (W = (wM)'M, exact 0/1 right operand)
+//   plane 2: sqrt(w_i) R_ip M_ip  (V = R~'R~)
+// A 32 x 32 tile is transposed through shared memory.
+__global__ void k_cov_operands_bf16(int n, int P, int Kpad, const void* __restrict__ y,
+                                    int y_prec, const uint8_t* __restrict__ mask,
+                                    const int32_t* __restrict__ Ni, const double* __restrict__ mu,
+                                    int mode, __nv_bfloat16* __restrict__ ops) {
+  __shared__ float tm[32][33], tw[32][33], tr[32][33];
+  const int i0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, p = p0 + threadIdx.x;
+    float fm = 0.f, fw = 0.f, fr = 0.f;
+    if (i < n && p < P) {
+      const size_t idx = (size_t)i * P + p;
+      const bool obs = mask ? mask[idx] != 0 : true;
+      const int N = Ni[i];
+      if (obs) {
+        const double wi = N >= 2 ? 1.0 / ((double)N * (double)(N - 1)) : 0.0;
+        const double yy = load_y(y, y_prec, idx);
+        const double rr = mode == FPCA_COV_RESIDUAL ? yy - mu[p] : yy;
+        fm = 1.f;
+        fw = (float)wi;
+        fr = (float)(sqrt(wi) * rr);
+      }
+    }
+    tm[r][threadIdx.x] = fm;
+    tw[r][threadIdx.x] = fw;
+    tr[r][threadIdx.x] = fr;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)P * Kpad;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int p = p0 + r, i = i0 + threadIdx.x;
+    if (p < P && i < Kpad) {
+      const size_t o = (size_t)p * Kpad + i;
+      ops[o] = __float2bfloat16_rn(tm[threadIdx.x][r]);
+      ops[plane + o] = __float2bfloat16_rn(tw[threadIdx.x][r]);
+      ops[2 * plane + o] = __float2bfloat16_rn(tr[threadIdx.x][r]);
+    }
+  }
+}
+
+// FP64 covariance bins of gridded data on CUDA cores: a 16 x 16 output tile
+// per block, subjects streamed through shared memory in chunks of 16.
+__global__ void k_cov_dense_f64(int n, int P, const void* __restrict__ y, int y_prec,
+                                const uint8_t* __restrict__ mask, const int32_t* __restrict__ Ni,
+                                const double* __restrict__ mu, int mode, int32_t* __restrict__ cnt,
+                                double* __restrict__ w, double* __restrict__ v) {
+  __shared__ double rp[16][17], rq[16][17], mp[16][17], mq[16][17], wsub[16];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int p = blockIdx.y * 16 + ty, q = blockIdx.x * 16 + tx;
+  int c = 0;
+  double sw = 0.0, sv = 0.0;
+  for (int i0 = 0; i0 < n; i0 += 16) {
+    // load subject chunk: rows i0..i0+15 for the 16 p and 16 q columns
+    {
+      const int i = i0 + ty;
+      const int pc = blockIdx.y * 16 + tx, qc = blockIdx.x * 16 + tx;
+      double obs_p = 0.0, obs_q = 0.0, r_p = 0.0, r_q = 0.0;
+      if (i < n) {
+        if (pc < P) {
+          const size_t idx = (size_t)i * P + pc;
+          obs_p = (mask ? mask[idx] != 0 : true) ? 1.0 : 0.0;
+          if (obs_p != 0.0) {
+            const double yy = load_y(y, y_prec, idx);
+            r_p = mode == FPCA_COV_RESIDUAL ? yy - mu[pc] : yy;
+          }
+        }
+        if (qc < P) {
+          const size_t idx = (size_t)i * P + qc;
+          obs_q = (mask ? mask[idx] != 0 : true) ? 1.0 : 0.0;
+          if (obs_q != 0.0) {
+            const double yy = load_y(y, y_prec, idx);
+            r_q = mode == FPCA_COV_RESIDUAL ? yy - mu[qc] : yy;
+          }
+        }
+      }
+      mp[ty][tx] = obs_p;
+      rp[ty][tx] = r_p;
+      mq[ty][tx] = obs_q;
+      rq[ty][tx] = r_q;
+      if (tx == 0) {
+        const int N = i < n ? Ni[i] : 0;
+        wsub[ty] = N >= 2 ? 1.0 / ((double)N * (double)(N - 1)) : 0.0;
+      }
+    }
+    __syncthreads();
+    const int kmax = min(16, n - i0);
+    for (int k = 0; k < kmax; ++k) {
+      const double both = mp[k][ty] * mq[k][tx];
+      c += both != 0.0;
+      sw = __dadd_rn(sw, __dmul_rn(wsub[k], both));
+      sv = __dadd_rn(sv, __dmul_rn(__dmul_rn(wsub[k], rp[k][ty]), rq[k][tx]));
+    }
+    __syncthreads();
+  }
+  if (p < P && q < P) {
+    const size_t o = (size_t)p * P + q;
+    const bool diag = p == q;
+    cnt[o] = diag ? 0 : c;
+    w[o] = diag ? 0.0 : sw;
+    v[o] = diag ? 0.0 : sv;
+  }
+}
+
+// Observation -> subject map for the sparse pair scatter.
+__global__ void k_obs_subject(int n, const int64_t* __restrict__ offs, int32_t* __restrict__ subj) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t j = offs[i]; j < offs[i + 1]; ++j) subj[j] = i;
+}
+
+// Per-observation bin and response (residual or raw).
+__global__ void k_obs_prep(long long N, int d, int m0, int m1, int m2,
+                           const double* __restrict__ t, const double* __restrict__ y,
+                           const double* __restrict__ mu, int mode, int32_t* __restrict__ ob,
+                           double* __restrict__ orr) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int m[3] = {m0, m1, m2};
+  const int b = bin_index(t + j * d, d, m);
+  ob[j] = b;
+  orr[j] = mode == FPCA_COV_RESIDUAL ? y[j] - mu[b] : y[j];
+}
+
+// Sparse covariance bins: thread per observation j, loop over its subject's
+// other observations l; integer-exact atomic pair counts and atomic sums.
+template <typename T>
+__global__ void k_cov_sparse(long long N, int P, const int64_t* __restrict__ offs,
+                             const int32_t* __restrict__ subj, const int32_t* __restrict__ ob,
+                             const double* __restrict__ orr, const int32_t* __restrict__ fold,
+                             int nfold, int32_t* cnt, T* w, T* v, T* q) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int i = subj[j];
+  const int64_t lo = offs[i], hi = offs[i + 1];
+  const long long Ni = hi - lo;
+  if (Ni < 2) return;
+  const double wi = 1.0 / ((double)Ni * (double)(Ni - 1));
+  const long long PP = (long long)P * P;
+  const long long row = (nfold > 0 ? (long long)fold[i] : 0ll) * PP + (long long)ob[j] * P;
+  const double rj = orr[j];
+  for (int64_t l = lo; l < hi; ++l) {
+    if (l == j) continue;
+    const long long at = row + ob[l];
+    const double prod = rj * orr[l];
+    atomicAdd(cnt + at, 1);
+    atomicAdd(w + at, (T)wi);
+    atomicAdd(v + at, (T)(wi * prod));
+    if (q) atomicAdd(q + at, (T)(wi * prod * prod));
+  }
+}
+
+}  // namespace
+
+fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8_t* mask,
+                                        int32_t* Ni) {
+  k_subject_counts<<<n, 256, 0, ctx->stream>>>(n, P, mask, Ni);
+  FPCA_LAUNCHED(ctx, "subject_counts");
+  return FPCA_OK;
+}
+
+fpca_status launch_bin_mean_dense(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                  const uint8_t* mask, const int32_t* Ni, int32_t* cnt,
+                                  double* w, double* v, double* v2) {
+  k_bin_mean_dense<<<(P + 127) / 128, 128, 0, ctx->stream>>>(n, P, y, y_prec, mask, Ni, cnt, w,
+                                                              v, v2);
+  FPCA_LAUNCHED(ctx, "bin_mean_dense");
+  return FPCA_OK;
+}
+
+fpca_status launch_bin_mean_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const int64_t* offs,
+                                   const double* t, const double* y, int32_t* cnt, double* w,
+                                   double* v, double* v2) {
+  const int P = grid_P(g);
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * P, ctx->stream);
+  cudaMemsetAsync(w, 0, sizeof(double) * P, ctx->stream);
+  cudaMemsetAsync(v, 0, sizeof(double) * P, ctx->stream);
+  if (v2) cudaMemsetAsync(v2, 0, sizeof(double) * P, ctx->stream);
+  k_bin_mean_sparse<<<(n + 127) / 128, 128, 0, ctx->stream>>>(
+      n, g->d, g->m[0], g->d > 1 ? g->m[1] : 1, g->d > 2 ? g->m[2] : 1, offs, t, y, cnt, w, v,
+      v2);
+  FPCA_LAUNCHED(ctx, "bin_mean_sparse");
+  return FPCA_OK;
+}
+
+fpca_status launch_cov_operands_bf16(fpca_ctx* ctx, int n, int P, int Kpad, const void* y,
+                                     int y_prec, const uint8_t* mask, const int32_t* Ni,
+                                     const double* mu, int mode, uint16_t* ops) {
+  dim3 grid((P + 31) / 32, Kpad / 32);
+  k_cov_operands_bf16<<<grid, dim3(32, 8), 0, ctx->stream>>>(
+      n, P, Kpad, y, y_prec, mask, Ni, mu, mode, reinterpret_cast<__nv_bfloat16*>(ops));
+  FPCA_LAUNCHED(ctx, "cov_operands_bf16");
+  return FPCA_OK;
+}
+
+fpca_status launch_cov_dense_f64(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                 const uint8_t* mask, const int32_t* Ni, const double* mu,
+                                 int mode, int32_t* cnt, double* w, double* v) {
+  dim3 grid((P + 15) / 16, (P + 15) / 16);
+  k_cov_dense_f64<<<grid, dim3(16, 16), 0, ctx->stream>>>(n, P, y, y_prec, mask, Ni, mu, mode,
+                                                          cnt, w, v);
+  FPCA_LAUNCHED(ctx, "cov_dense_f64");
+  return FPCA_OK;
+}
+
+fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const int64_t* offs,
+                              const double* t, const double* y, const double* mu, int mode,
+                              const int32_t* fold, int nfold, int prec, int32_t* cnt, void* w,
+                              void* v, void* q) {
+  const int P = grid_P(g);
+  const long long PP = (long long)P * P;
+  const int F = nfold > 0 ? nfold : 1;
+  // total observation count (offs[n]) is needed on the host to size the launch
+  int64_t Nobs = 0;
+  cudaError_t e = cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "reading offs[n]: %s", cudaGetErrorString(e));
+  if (Nobs < 0 || Nobs > (1ll << 31))
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "offs[n] = %lld out of range", (long long)Nobs);
+  const size_t esz = prec == FPCA_F64 ? sizeof(double) : sizeof(float);
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * PP * F, ctx->stream);
+  cudaMemsetAsync(w, 0, esz * PP * F, ctx->stream);
+  cudaMemsetAsync(v, 0, esz * PP * F, ctx->stream);
+  if (q) cudaMemsetAsync(q, 0, esz * PP * F, ctx->stream);
+  if (Nobs == 0) return fpca_check_launch(ctx, "cov_sparse memset");
+  void* ws = fpca_workspace(ctx, WsCarve::round(4 * Nobs) * 2 + WsCarve::round(8 * Nobs) + 1024);
+  if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace");
+  WsCarve carve(ws);
+  int32_t* subj = carve.take<int32_t>(Nobs);
+  int32_t* ob = carve.take<int32_t>(Nobs);
+  double* orr = carve.take<double>(Nobs);
+  k_obs_subject<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, offs, subj);
+  FPCA_LAUNCHED(ctx, "obs_subject");
+  const int nb = (int)((Nobs + 255) / 256);
+  k_obs_prep<<<nb, 256, 0, ctx->stream>>>(Nobs, g->d, g->m[0], g->d > 1 ? g->m[1] : 1,
+                                          g->d > 2 ? g->m[2] : 1, t, y, mu, mode, ob, orr);
+  FPCA_LAUNCHED(ctx, "obs_prep");
+  if (prec == FPCA_F64) {
+    k_cov_sparse<double><<<nb, 256, 0, ctx->stream>>>(Nobs, P, offs, subj, ob, orr, fold, nfold,
+                                                      cnt, static_cast<double*>(w),
+                                                      static_cast<double*>(v),
+                                                      static_cast<double*>(q));
+  } else {
+    k_cov_sparse<float><<<nb, 256, 0, ctx->stream>>>(Nobs, P, offs, subj, ob, orr, fold, nfold,
+                                                     cnt, static_cast<float*>(w),
+                                                     static_cast<float*>(v),
+                                                     static_cast<float*>(q));
+  }
+  FPCA_LAUNCHED(ctx, "cov_sparse");
+  return FPCA_OK;
+}

@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "fpca.h"
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct fpca_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  void* ws = nullptr;        // workspace, grown on demand
+  size_t ws_bytes = 0;
+  int* d_err = nullptr;      // device error word (DERR_*)
+  uint64_t launches = 0;     // kernels queued by this context
+  int num_sms = 0;
+  size_t smem_optin = 0;
+};
+
+// Device error codes written by kernels into ctx->d_err.
+enum { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BOUNDS = 2 };
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+#define FPCA_WAIT_LIMIT_NS 2000000000ull
+
+fpca_status fpca_fail(fpca_ctx* ctx, fpca_status st, const char* fmt, ...);
+// Checks the last launch; records the CUDA error text on failure.
+fpca_status fpca_check_launch(fpca_ctx* ctx, const char* what);
+// Returns a device buffer of at least `bytes`, growing the workspace (which
+// synchronises the stream first). nullptr on allocation failure.
+void* fpca_workspace(fpca_ctx* ctx, size_t bytes);
+
+#define FPCA_LAUNCHED(ctx, name)                                   \
+  do {                                                             \
+    (ctx)->launches++;                                             \
+    fpca_status _s = fpca_check_launch((ctx), (name));             \
+    if (_s != FPCA_OK) return _s;                                  \
+  } while (0)
+
+// Bump allocator over one workspace block (256-byte aligned pieces).
+struct WsCarve {
+  char* base;
+  size_t off = 0;
+  explicit WsCarve(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+  static size_t round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+};
+
+inline int grid_P(const fpca_grid* g) {
+  int P = 1;
+  for (int k = 0; k < g->d; ++k) P *= g->m[k];
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the .cu files (all queue on ctx->stream)
+// ---------------------------------------------------------------------------
+// bin.cu
+fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8_t* mask,
+                                        int32_t* Ni);
+fpca_status launch_bin_mean_dense(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                  const uint8_t* mask, const int32_t* Ni, int32_t* cnt,
+                                  double* w, double* v, double* v2);
+fpca_status launch_bin_mean_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const int64_t* offs,
+                                   const double* t, const double* y, int32_t* cnt, double* w,
+                                   double* v, double* v2);
+fpca_status launch_cov_operands_bf16(fpca_ctx* ctx, int n, int P, int Kpad, const void* y,
+                                     int y_prec, const uint8_t* mask, const int32_t* Ni,
+                                     const double* mu, int mode, uint16_t* ops);
+fpca_status launch_cov_dense_f64(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                 const uint8_t* mask, const int32_t* Ni, const double* mu,
+                                 int mode, int32_t* cnt, double* w, double* v);
+fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const int64_t* offs,
+                              const double* t, const double* y, const double* mu, int mode,
+                              const int32_t* fold, int nfold, int prec, int32_t* cnt, void* w,
+                              void* v, void* q);
+// gemm_tc.cu: C = X'X for the three operand planes (mask, sqrt(w) mask, sqrt(w) R)
+fpca_status launch_gram_tc(fpca_ctx* ctx, int P, int Kpad, const uint16_t* ops, int32_t* cnt,
+                           float* w, float* v);
+// smooth.cu
+fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt,
+                               const double* w, const double* v, const double* h, double* mu,
+                               uint8_t* status);
+fpca_status smooth_cov_run(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins* bins,
+                           const double* h, int nh, int prec, const double* mu_raw,
+                           const float* omega, int l, void* gamma, uint8_t* status, float* y,
+                           double* cv);
+// eig.cu
+fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, int gamma_prec,
+                          const int32_t* domain, const float* omega, int l, int k,
+                          int power_iters, int full, double* evals, double* evecs,
+                          double* fve);
