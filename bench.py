@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the dense FPCA path: smoothed covariance grid points per second.
+
+Workload: n = 1000 surfaces on a 64 x 64 grid, points outside the disk of
+radius 0.5 masked and 10% of the rest dropped, 8 components, sigma = 0.5,
+h = 0.15 for mean and covariance; covariance grid 4096 x 4096 = 16.8M 4-D
+points.  One step = the whole path on device-resident inputs:
+  mean bins -> mean smoother -> covariance bins (BF16 tcgen05 Gram products)
+  -> FP32 compensated moment sweeps + per-point solve -> matrixisation,
+  random projection (rank 8 + 10 oversampling, 2 power iterations),
+  Rayleigh-Ritz.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no exchange step); value = all ranks' points / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "smoothed covariance grid points/s"
+UNIT = "points/s"
+WORKLOAD = "dense_2d_disk_64x64_n1000_h0.15"
+H = (0.15, 0.15)
+K_EIG, L_RP, Q_POWER = 8, 18, 2
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU time budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (CPU): Gamma_hat at sampled output pairs by window sums
+# ----------------------------------------------------------------------------
+
+def oracle_sample_rate(seconds, min_points=20, seed=0):
+    """Points/s of the FP64 oracle's covariance smoother on this workload.
+
+    The oracle bins the full data once (not timed), then evaluates Gamma_hat
+    by its per-point window sums at random output pairs inside the domain
+    until ``seconds`` of CPU time have passed.
+    """
+    import numpy as np
+
+    import fpca_synth as fs
+    from oracle import smoother as sm
+    D = fs.dense_2d_disk()
+    y = D.y.astype(np.float32).astype(np.float64)
+    cnt, Wm, Vm, _ = sm.bin_mean_dense(y, D.mask, D.m)
+    mu, _ = sm.smooth_mean(D.m, H, cnt, Wm, Vm)
+    mu = np.where(np.isnan(mu), 0.0, mu)
+    C, W, V = sm.bin_cov_dense(sm.residuals_dense(y, D.mask, mu), D.mask)
+    rng = np.random.default_rng(seed)
+    inside = np.nonzero(cnt > 0)[0]
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        pairs = np.stack([rng.choice(inside, 10), rng.choice(inside, 10)], 1)
+        sm.smooth_cov_points(pairs, D.m, H, C, W, V)
+        done += len(pairs)
+        el = time.perf_counter() - t0
+        if el >= seconds and done >= min_points:
+            break
+    return done / el, done, el
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import fpca_synth as fs
+    from oracle import smoother as sm
+    D = fs.dense_2d_disk()
+    y = D.y.astype(np.float32).astype(np.float64)
+    cnt, Wm, Vm, _ = sm.bin_mean_dense(y, D.mask, D.m)
+    mu, _ = sm.smooth_mean(D.m, H, cnt, Wm, Vm)
+    mu = np.where(np.isnan(mu), 0.0, mu)
+    C, W, V = sm.bin_cov_dense(sm.residuals_dense(y, D.mask, mu), D.mask)
+    rng = np.random.default_rng(1)
+    inside = np.nonzero(cnt > 0)[0]
+    per_step = 60
+
+    def step():
+        pairs = np.stack([rng.choice(inside, per_step), rng.choice(inside, per_step)], 1)
+        sm.smooth_cov_points(pairs, D.m, H, C, W, V)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = per_step * args.steps / el
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{per_step} output pairs per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle window sums at {per_step} random in-domain "
+                                   "output pairs per step; bins precomputed"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[2][1 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def mean_window(M, T):
+    """Average in-grid window length of a 1-D sum with offsets -T..T over M outputs."""
+    return sum(min(T, M - 1 - x) - max(-T, -x) + 1 for x in range(M)) / M
+
+
+def taps(h, M):
+    hm = h * M
+    for j in range(M - 1, 0, -1):
+        if j / hm < 1.0:
+            return j
+    return 0
+
+
+def load_traffic(kernel):
+    """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, if it
+    was taken on the current source of that kernel; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec["bytes_per_launch"] if digest == rec["sha256"] else None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = dist_env()
+    import numpy as np
+    import torch
+
+    import fpca_synth as fs
+    from paper_1510_04439_gb300 import binding as B
+    from paper_1510_04439_gb300 import pipeline
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    D = fs.dense_2d_disk()
+    P = D.P
+    om_np = fs.gaussian_test_matrix(P, L_RP, fs.SEED_BASE)
+    y_host = torch.from_numpy(D.y.astype(np.float32)).pin_memory()
+    m_host = torch.from_numpy(D.mask).pin_memory()
+    y = y_host.to(dev)
+    mask = m_host.to(dev)
+    omega = torch.from_numpy(om_np.astype(np.float32)).to(dev)
+    bufs = pipeline.alloc_dense(torch, dev, P, K_EIG, B.BF16, B.F32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = B.Context(local_rank, stream)
+
+    def step(yy, mm):
+        pipeline.run_dense(ctx, D.m, yy, mm, H, H, K_EIG, bufs, bin_prec=B.BF16,
+                           smooth_prec=B.F32C, omega=omega, power_iters=Q_POWER)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def maxreduce(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 3)):
+        step(y, mask)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps ----
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    l0 = ctx.launches
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(y, mask)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launches - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.sync()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms = maxreduce(ms)
+    units = float(P) * P
+    value = world * units / (ms * 1e-3)
+
+    # ---- end to end: pinned host inputs in, eigenpairs out, every step ----
+    ev_h = torch.empty(K_EIG, dtype=torch.float64).pin_memory()
+    vec_h = torch.empty(K_EIG, P, dtype=torch.float64).pin_memory()
+    fve_h = torch.empty(K_EIG, dtype=torch.float64).pin_memory()
+    y_in = torch.empty_like(y)
+    m_in = torch.empty_like(mask)
+    barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        y_in.copy_(y_host, non_blocking=True)
+        m_in.copy_(m_host, non_blocking=True)
+        step(y_in, m_in)
+        ev_h.copy_(bufs.evals, non_blocking=True)
+        vec_h.copy_(bufs.evecs, non_blocking=True)
+        fve_h.copy_(bufs.fve, non_blocking=True)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = maxreduce(sum(a.elapsed_time(b) for a, b in evs) / args.steps)
+    h2d = y_host.numel() * y_host.element_size() + m_host.numel() * m_host.element_size()
+    d2h = (ev_h.numel() + vec_h.numel() + fve_h.numel()) * 8
+
+    # ---- roofline of the dominant kernel (t-side sweep + per-point solve) ----
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    hp = prof.get("cov_hpass_solve")
+    roof = None
+    if hp:
+        M0, M1 = D.m
+        T0, T1 = taps(H[0], M0), taps(H[1], M1)
+        # 15 sums across t-plane rows, 21 along them (incl. the non-empty count),
+        # one FMA per in-grid tap, plus ~100 flops of 5x5 elimination per point
+        flops_pt = 2.0 * (15 * mean_window(M0, T0) + 21 * mean_window(M1, T1)) + 100.0
+        per_launch_ms = hp[0] / hp[1]
+        achieved = flops_pt * units / (per_launch_ms * 1e-3) / 1e12
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        traffic = load_traffic("cov_hpass_solve")
+        roof = {"kernel": "cov_hpass_solve", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "ms_per_launch": per_launch_ms, "flops_per_point": flops_pt,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "dominant_kernel_by_time": dom}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, npts, el = oracle_sample_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle window sums at {npts} random in-domain output pairs "
+                         f"({el:.1f} s; bins precomputed, numpy default threading)"}
+
+    if rank == 0:
+        kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
+                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [64, 64], "n": 1000, "cov_points": int(units),
+                       "h": list(H), "k": K_EIG, "l": L_RP, "power_iters": Q_POWER,
+                       "precision": "BF16 tcgen05 binning (FP32 accumulate, exact counts); "
+                                    "FP32 Kahan-compensated moments; FP32 solve with FP64 "
+                                    "escalation; FP64 Rayleigh-Ritz",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": world * units / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": ms_e2e},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

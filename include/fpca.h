@@ -115,6 +115,19 @@ fpca_status fpca_sync(fpca_ctx* ctx);
 /* Number of kernels this context has launched so far (host counter). */
 uint64_t fpca_launch_count(const fpca_ctx* ctx);
 
+/* Kernel timing (off by default).  When enabled, a CUDA event is recorded on
+ * the context stream at the start of every entry point and after every
+ * kernel launch; a kernel's time is the interval between its event and the
+ * previous one (so a stream memset or host gap before a kernel is counted
+ * with it).  fpca_profile_enable clears the totals.  fpca_profile_count
+ * waits for the stream, folds finished intervals into per-kernel-name totals
+ * and returns the number of names; fpca_profile_entry reads entry i (name
+ * owned by ctx, valid until the next fpca_profile_count). */
+fpca_status fpca_profile_enable(fpca_ctx* ctx, int enable);
+int fpca_profile_count(fpca_ctx* ctx);
+fpca_status fpca_profile_entry(fpca_ctx* ctx, int i, const char** name, double* total_ms,
+                               uint64_t* launches);
+
 /* Mean bins with the 1/N_i weights of Eq. (2.3) (Section 3.2 binning).
  * Outputs (length P each): cnt = observations per bin (exact);
  * w = sum_i n_ib / N_i; v = sum_i sum_{j in b} Y_ij / N_i;
@@ -162,13 +175,18 @@ fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* 
  *   EMPTY, the local constant fit where FALLBACK.
  *  status (optional): nh x P x P uint8, rules as in fpca_smooth_mean with
  *   2d+1 unknowns.
- *  omega/l/y (optional, all or none): y = Sigma Omega, nh x P x l float,
- *   with Sigma = Gamma_hat with EMPTY points set to zero (Section 3.4), omega
- *   P x l float.
- *  cv (optional, nfold >= 2): nh doubles, the subject-level K-fold CV score
- *   of each bandwidth (fit on the other folds' bins, scored on the fold's
- *   held-out products; +inf when EMPTY points hold > 1% of the held-out
- *   weight).
+ *  omega/l/y (optional, all or none): y = G Omega, nh x P x l float, with
+ *   G = Gamma_hat (EMPTY points counted as zero; no symmetrisation and no
+ *   domain mask), omega P x l float, l <= 64 -- the first product of the
+ *   random projection (Section 3.4) taken while each row of Gamma_hat is
+ *   still on chip.
+ *  cv (optional, bins->nfold >= 2, bins->q given, residual mode): nh
+ *   doubles, the subject-level K-fold CV score of each bandwidth: for fold f
+ *   the surface is fitted on the pooled bins minus fold f's bins and scored
+ *   on fold f's held-out products at the bin centres, sum (Q_f - 2 G V_f +
+ *   G^2 W_f) over non-EMPTY points divided by their held-out weight; +inf
+ *   when EMPTY points hold more than 1% of the held-out weight
+ *   (Section 3.3 selects bandwidths by cross-validation).
  * At least one output must be given. */
 fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
                                     const fpca_covbins* bins, const double* h, int nh,
@@ -186,7 +204,7 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
  *   Omega when its count is > 0), or NULL for the whole box.
  *  full = 1: dense cyclic Jacobi eigensolver on Sigma (FP64; P <= 1024).
  *  full = 0: random projection (Section 3.4) with the caller's Gaussian
- *   test matrix omega (P x l float, l > k): Y = Sigma Omega, power_iters
+ *   test matrix omega (P x l float, k < l <= 64): Y = Sigma Omega, power_iters
  *   rounds of Q = orth(Y), Y = Sigma Q, then Q = orth(Y), B = Q' Sigma Q and
  *   the FP64 Jacobi eigenpairs of B (Rayleigh-Ritz).
  * Outputs (device, FP64): evals k, evecs P x k (column-major: vector j at

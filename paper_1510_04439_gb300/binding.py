@@ -26,7 +26,8 @@ COV_RESIDUAL, COV_RAW = 0, 1
 SYMBOLS = (
     "fpca_create", "fpca_destroy", "fpca_set_stream", "fpca_last_error", "fpca_sync",
     "fpca_launch_count", "fpca_bin_mean", "fpca_smooth_mean", "fpca_bin_cov",
-    "fpca_smooth_cov_project", "fpca_rproj_eig",
+    "fpca_smooth_cov_project", "fpca_rproj_eig", "fpca_profile_enable", "fpca_profile_count",
+    "fpca_profile_entry",
 )
 
 
@@ -101,6 +102,10 @@ def load(path=LIB_PATH):
                                             dbl_p, i32, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.fpca_rproj_eig.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, vp, vp, i32, i32, i32, i32,
                                    vp, vp, vp]
+    lib.fpca_profile_enable.argtypes = [vp, i32]
+    lib.fpca_profile_count.argtypes = [vp]
+    lib.fpca_profile_entry.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count"):
@@ -159,10 +164,28 @@ class Context:
     def launches(self):
         return int(self.lib.fpca_launch_count(self.h))
 
+    def profile(self, enable=True):
+        """Turn per-kernel timing on or off (clears the totals)."""
+        self._check(self.lib.fpca_profile_enable(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} of the timed launches so far."""
+        out = {}
+        for i in range(self.lib.fpca_profile_count(self.h)):
+            name = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            cnt = ctypes.c_uint64()
+            self._check(self.lib.fpca_profile_entry(self.h, i, ctypes.byref(name), ctypes.byref(ms),
+                                                    ctypes.byref(cnt)))
+            out[name.value.decode()] = (ms.value, int(cnt.value))
+        return out
+
     # ---- data descriptors --------------------------------------------------
     @staticmethod
     def dense(y, mask=None):
+        """Dense data descriptor; it holds references to ``y`` and ``mask``."""
         d = Data()
+        d._keep = (y, mask)
         d.layout = DENSE
         d.n = int(y.shape[0])
         d.y = y.data_ptr()
@@ -172,7 +195,9 @@ class Context:
 
     @staticmethod
     def sparse(offs, t, y):
+        """Sparse data descriptor; it holds references to its tensors."""
         d = Data()
+        d._keep = (offs, t, y)
         d.layout = SPARSE
         d.n = int(offs.shape[0]) - 1
         d.y = y.data_ptr()

@@ -25,6 +25,63 @@ fpca_status fpca_check_launch(fpca_ctx* ctx, const char* what) {
   return FPCA_OK;
 }
 
+static cudaEvent_t prof_event(fpca_ctx* ctx) {
+  cudaEvent_t e = nullptr;
+  if (!ctx->prof_pool.empty()) {
+    e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaEventRecord(e, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->prof_pool.push_back(e);
+    return nullptr;
+  }
+  return e;
+}
+
+void fpca_prof_mark(fpca_ctx* ctx) {
+  if (!ctx->prof) return;
+  cudaEvent_t e = prof_event(ctx);
+  if (e) {
+    // an unpaired previous mark is recycled once resolved
+    if (ctx->prof_last) ctx->prof_pending.push_back({std::string(), ctx->prof_last, nullptr});
+    ctx->prof_last = e;
+  }
+}
+
+void fpca_prof_end(fpca_ctx* ctx, const char* name) {
+  cudaEvent_t e = prof_event(ctx);
+  if (!e) return;
+  if (ctx->prof_last) ctx->prof_pending.push_back({std::string(name), ctx->prof_last, e});
+  ctx->prof_last = e;
+}
+
+static void prof_resolve(fpca_ctx* ctx) {
+  if (ctx->prof_pending.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  std::vector<cudaEvent_t> done;
+  for (auto& r : ctx->prof_pending) {
+    if (r.b && !r.name.empty()) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        auto& t = ctx->prof_totals[r.name];
+        t.first += ms;
+        t.second += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    done.push_back(r.a);
+  }
+  ctx->prof_pending.clear();
+  // every start event is some record's `a`; the current last mark stays live
+  for (cudaEvent_t e : done)
+    if (e != ctx->prof_last) ctx->prof_pool.push_back(e);
+}
+
 void* fpca_workspace(fpca_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return ctx->ws;
   // Growing: the old block may still be in use by queued work.
@@ -143,6 +200,9 @@ fpca_status fpca_create(fpca_ctx** out, int device, void* cuda_stream) {
 void fpca_destroy(fpca_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  prof_resolve(ctx);
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+  if (ctx->prof_last) cudaEventDestroy(ctx->prof_last);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -157,6 +217,33 @@ fpca_status fpca_set_stream(fpca_ctx* ctx, void* cuda_stream) {
 const char* fpca_last_error(const fpca_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 uint64_t fpca_launch_count(const fpca_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fpca_status fpca_profile_enable(fpca_ctx* ctx, int enable) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  prof_resolve(ctx);
+  ctx->prof_totals.clear();
+  ctx->prof = enable ? 1 : 0;
+  return FPCA_OK;
+}
+
+int fpca_profile_count(fpca_ctx* ctx) {
+  if (!ctx) return 0;
+  prof_resolve(ctx);
+  ctx->prof_names.clear();
+  for (auto& kv : ctx->prof_totals) ctx->prof_names.push_back(kv.first);
+  return (int)ctx->prof_names.size();
+}
+
+fpca_status fpca_profile_entry(fpca_ctx* ctx, int i, const char** name, double* total_ms,
+                               uint64_t* launches) {
+  if (!ctx || i < 0 || i >= (int)ctx->prof_names.size())
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "profile entry %d out of range", i);
+  const auto& t = ctx->prof_totals[ctx->prof_names[i]];
+  if (name) *name = ctx->prof_names[i].c_str();
+  if (total_ms) *total_ms = t.first;
+  if (launches) *launches = t.second;
+  return FPCA_OK;
+}
 
 fpca_status fpca_sync(fpca_ctx* ctx) {
   if (!ctx) return FPCA_E_INVALID_ARG;
@@ -177,6 +264,7 @@ fpca_status fpca_sync(fpca_ctx* ctx) {
 fpca_status fpca_bin_mean(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
                           int32_t* cnt, double* w, double* v, double* v2) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
   if (!valid_grid(ctx, grid, 1 << 20) || !valid_data(ctx, data)) return FPCA_E_INVALID_ARG;
   if (!cnt || !w || !v) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "cnt, w and v are required");
   long long P = 1;
@@ -198,6 +286,7 @@ fpca_status fpca_smooth_mean(fpca_ctx* ctx, const fpca_grid* grid, const int32_t
                              const double* w, const double* v, const double* h, double* mu,
                              uint8_t* status) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
   if (!valid_grid(ctx, grid, 1 << 20)) return FPCA_E_INVALID_ARG;
   if (!valid_h(ctx, h, grid->d)) return FPCA_E_INVALID_ARG;
   if (!cnt || !w || !v || !mu)
@@ -209,6 +298,7 @@ fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* 
                          const double* mu, int prec, int mode, const int32_t* fold, int nfold,
                          int32_t* cnt, void* w, void* v, void* q) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
   if (!valid_grid(ctx, grid, 4096) || !valid_data(ctx, data)) return FPCA_E_INVALID_ARG;
   if (!cnt || !w || !v) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "cnt, w and v are required");
   if (mode != FPCA_COV_RESIDUAL && mode != FPCA_COV_RAW)
@@ -269,6 +359,7 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
                                     const double* mu_raw, const float* omega, int l,
                                     void* gamma, uint8_t* status, float* y, double* cv) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
   if (!valid_grid(ctx, grid, 4096)) return FPCA_E_INVALID_ARG;
   if (!bins || !bins->cnt || !bins->w || !bins->v)
     return fpca_fail(ctx, FPCA_E_INVALID_ARG, "bins need cnt, w and v");
@@ -284,6 +375,8 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
   if (cv && bins->nfold < 2)
     return fpca_fail(ctx, FPCA_E_INVALID_ARG, "cv needs bins with nfold >= 2");
   if (cv && !bins->q) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "cv needs bins.q");
+  if (cv && mu_raw)
+    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "cv is built for residual-mode bins");
   if (!gamma && !status && !y && !cv)
     return fpca_fail(ctx, FPCA_E_INVALID_ARG, "no output requested");
   if (grid->d > 2)
@@ -302,6 +395,7 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
                            int k, int power_iters, int full, double* evals, double* evecs,
                            double* fve) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
   if (!valid_grid(ctx, grid, 1 << 20)) return FPCA_E_INVALID_ARG;
   if (!gamma || !evals || !evecs)
     return fpca_fail(ctx, FPCA_E_INVALID_ARG, "gamma, evals and evecs are required");
@@ -312,8 +406,8 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
   if (full) {
     if (P > 1024) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "dense eigensolver built for P <= 1024");
   } else {
-    if (!omega || l <= k || l > 128)
-      return fpca_fail(ctx, FPCA_E_INVALID_ARG, "random projection needs omega and k < l <= 128");
+    if (!omega || l <= k || l > 64)
+      return fpca_fail(ctx, FPCA_E_INVALID_ARG, "random projection needs omega and k < l <= 64");
     if (power_iters < 0 || power_iters > 16)
       return fpca_fail(ctx, FPCA_E_INVALID_ARG, "power_iters must be 0..16");
   }

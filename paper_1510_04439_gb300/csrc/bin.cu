@@ -76,15 +76,19 @@ __global__ void k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y
 }
 
 // Sparse mean bins: one thread per subject, atomic scatter into the bins.
-__global__ void k_bin_mean_sparse(int n, int d, int m0, int m1, int m2,
+__global__ void k_bin_mean_sparse(int n, long long N, int d, int m0, int m1, int m2,
                                   const int64_t* __restrict__ offs, const double* __restrict__ t,
                                   const double* __restrict__ y, int32_t* cnt, double* w,
-                                  double* v, double* v2) {
+                                  double* v, double* v2, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int m[3] = {m0, m1, m2};
   const int64_t lo = offs[i], hi = offs[i + 1];
-  if (hi <= lo) return;
+  if (lo < 0 || hi < lo || hi > N) {
+    atomicExch(err, DERR_BOUNDS);
+    return;
+  }
+  if (hi == lo) return;
   const double wi = 1.0 / (double)(hi - lo);
   for (int64_t j = lo; j < hi; ++j) {
     const int b = bin_index(t + j * d, d, m);
@@ -204,11 +208,19 @@ __global__ void k_cov_dense_f64(int n, int P, const void* __restrict__ y, int y_
   }
 }
 
-// Observation -> subject map for the sparse pair scatter.
-__global__ void k_obs_subject(int n, const int64_t* __restrict__ offs, int32_t* __restrict__ subj) {
+// Observation -> subject map for the sparse pair scatter.  Offsets outside
+// 0 <= offs[i] <= offs[i+1] <= N are reported (DERR_BOUNDS) and the subject
+// is skipped, here and in the scatter.
+__global__ void k_obs_subject(int n, long long N, const int64_t* __restrict__ offs,
+                              int32_t* __restrict__ subj, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  for (int64_t j = offs[i]; j < offs[i + 1]; ++j) subj[j] = i;
+  const int64_t lo = offs[i], hi = offs[i + 1];
+  if (lo < 0 || hi < lo || hi > N) {
+    atomicExch(err, DERR_BOUNDS);
+    return;
+  }
+  for (int64_t j = lo; j < hi; ++j) subj[j] = i;
 }
 
 // Per-observation bin and response (residual or raw).
@@ -230,13 +242,18 @@ template <typename T>
 __global__ void k_cov_sparse(long long N, int P, const int64_t* __restrict__ offs,
                              const int32_t* __restrict__ subj, const int32_t* __restrict__ ob,
                              const double* __restrict__ orr, const int32_t* __restrict__ fold,
-                             int nfold, int32_t* cnt, T* w, T* v, T* q) {
+                             int nfold, int32_t* cnt, T* w, T* v, T* q, int* __restrict__ err) {
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= N) return;
   const int i = subj[j];
+  if (i < 0) return;  // subject with invalid offsets
   const int64_t lo = offs[i], hi = offs[i + 1];
   const long long Ni = hi - lo;
   if (Ni < 2) return;
+  if (nfold > 0 && (fold[i] < 0 || fold[i] >= nfold)) {
+    atomicExch(err, DERR_BOUNDS);
+    return;
+  }
   const double wi = 1.0 / ((double)Ni * (double)(Ni - 1));
   const long long PP = (long long)P * P;
   const long long row = (nfold > 0 ? (long long)fold[i] : 0ll) * PP + (long long)ob[j] * P;
@@ -274,13 +291,19 @@ fpca_status launch_bin_mean_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, con
                                    const double* t, const double* y, int32_t* cnt, double* w,
                                    double* v, double* v2) {
   const int P = grid_P(g);
+  int64_t Nobs = 0;
+  cudaError_t e = cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "reading offs[n]: %s", cudaGetErrorString(e));
+  if (Nobs < 0) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "offs[n] = %lld", (long long)Nobs);
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * P, ctx->stream);
   cudaMemsetAsync(w, 0, sizeof(double) * P, ctx->stream);
   cudaMemsetAsync(v, 0, sizeof(double) * P, ctx->stream);
   if (v2) cudaMemsetAsync(v2, 0, sizeof(double) * P, ctx->stream);
   k_bin_mean_sparse<<<(n + 127) / 128, 128, 0, ctx->stream>>>(
-      n, g->d, g->m[0], g->d > 1 ? g->m[1] : 1, g->d > 2 ? g->m[2] : 1, offs, t, y, cnt, w, v,
-      v2);
+      n, (long long)Nobs, g->d, g->m[0], g->d > 1 ? g->m[1] : 1, g->d > 2 ? g->m[2] : 1, offs, t,
+      y, cnt, w, v, v2, ctx->d_err);
   FPCA_LAUNCHED(ctx, "bin_mean_sparse");
   return FPCA_OK;
 }
@@ -332,7 +355,8 @@ fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const in
   int32_t* subj = carve.take<int32_t>(Nobs);
   int32_t* ob = carve.take<int32_t>(Nobs);
   double* orr = carve.take<double>(Nobs);
-  k_obs_subject<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, offs, subj);
+  cudaMemsetAsync(subj, 0xff, sizeof(int32_t) * Nobs, ctx->stream);  // -1: no valid subject
+  k_obs_subject<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, Nobs, offs, subj, ctx->d_err);
   FPCA_LAUNCHED(ctx, "obs_subject");
   const int nb = (int)((Nobs + 255) / 256);
   k_obs_prep<<<nb, 256, 0, ctx->stream>>>(Nobs, g->d, g->m[0], g->d > 1 ? g->m[1] : 1,
@@ -342,12 +366,12 @@ fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const in
     k_cov_sparse<double><<<nb, 256, 0, ctx->stream>>>(Nobs, P, offs, subj, ob, orr, fold, nfold,
                                                       cnt, static_cast<double*>(w),
                                                       static_cast<double*>(v),
-                                                      static_cast<double*>(q));
+                                                      static_cast<double*>(q), ctx->d_err);
   } else {
     k_cov_sparse<float><<<nb, 256, 0, ctx->stream>>>(Nobs, P, offs, subj, ob, orr, fold, nfold,
                                                      cnt, static_cast<float*>(w),
                                                      static_cast<float*>(v),
-                                                     static_cast<float*>(q));
+                                                     static_cast<float*>(q), ctx->d_err);
   }
   FPCA_LAUNCHED(ctx, "cov_sparse");
   return FPCA_OK;

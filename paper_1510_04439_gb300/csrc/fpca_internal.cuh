@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <map>
 #include <string>
+#include <vector>
 
 #include "fpca.h"
 
@@ -21,6 +23,18 @@ struct fpca_ctx {
   uint64_t launches = 0;     // kernels queued by this context
   int num_sms = 0;
   size_t smem_optin = 0;
+  // opt-in kernel timing: an event after every launch, durations between
+  // consecutive events (the first one is marked at the top of each call)
+  int prof = 0;
+  cudaEvent_t prof_last = nullptr;
+  struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  std::map<std::string, std::pair<double, uint64_t>> prof_totals;
+  std::vector<std::string> prof_names;  // stable storage for fpca_profile_entry
 };
 
 // Device error codes written by kernels into ctx->d_err.
@@ -36,11 +50,17 @@ fpca_status fpca_check_launch(fpca_ctx* ctx, const char* what);
 // synchronises the stream first). nullptr on allocation failure.
 void* fpca_workspace(fpca_ctx* ctx, size_t bytes);
 
+// Marks the start of an API call's work on the stream (kernel timing).
+void fpca_prof_mark(fpca_ctx* ctx);
+// Records the end of the kernel just launched (kernel timing).
+void fpca_prof_end(fpca_ctx* ctx, const char* name);
+
 #define FPCA_LAUNCHED(ctx, name)                                   \
   do {                                                             \
     (ctx)->launches++;                                             \
     fpca_status _s = fpca_check_launch((ctx), (name));             \
     if (_s != FPCA_OK) return _s;                                  \
+    if ((ctx)->prof) fpca_prof_end((ctx), (name));                 \
   } while (0)
 
 // Bump allocator over one workspace block (256-byte aligned pieces).

@@ -308,9 +308,13 @@ __device__ __forceinline__ void kadd(T& s, T& c, T w, T x) {
 // ---------------------------------------------------------------------------
 // vertical pass: 1-D sums along the row index of P x P arrays
 // ---------------------------------------------------------------------------
+// One input array per job; the value read is in[e] - sub[e] (sub may be
+// NULL), or for counts the indicator [in[e] - sub[e] > 0].  Subtracting a
+// fold's bins from the pooled bins gives the training bins of that fold.
 struct VJob {
   const void* in;
-  int in_int;       // 1: int32 counts read as the indicator [count > 0]
+  const void* sub;
+  int in_int;       // 1: int32 counts read as the indicator
   int npow;         // outputs
   int row[3];       // table rows used (0 K, 1 K u, 2 K u^2, 3 box)
   void* out[3];
@@ -337,10 +341,15 @@ __global__ void __launch_bounds__(VCOLS)
     const long long row = base + (long long)a * stride;
     T val = T(0);
     if (col < P) {
-      if (jb.in_int)
-        val = static_cast<const int32_t*>(jb.in)[row * P + col] > 0 ? T(1) : T(0);
-      else
-        val = static_cast<const T*>(jb.in)[row * P + col];
+      const long long e = row * P + col;
+      if (jb.in_int) {
+        int c = static_cast<const int32_t*>(jb.in)[e];
+        if (jb.sub) c -= static_cast<const int32_t*>(jb.sub)[e];
+        val = c > 0 ? T(1) : T(0);
+      } else {
+        val = static_cast<const T*>(jb.in)[e];
+        if (jb.sub) val -= static_cast<const T*>(jb.sub)[e];
+      }
     }
     tile[a * VCOLS + threadIdx.x] = val;
   }
@@ -379,8 +388,37 @@ __global__ void __launch_bounds__(VCOLS)
 }
 
 // ---------------------------------------------------------------------------
-// horizontal t-side sweep + per-point solve
+// horizontal t-side sweep + per-point solve + epilogues
 // ---------------------------------------------------------------------------
+// Optional outputs besides Gamma_hat and status:
+//  y += G Omega   (row x_s of y gets sum_t G(x_s, t) Omega(t, :); EMPTY = 0)
+//  cv terms of one fold f: err = sum (Q_f - 2 G V_f + G^2 W_f) and w_in =
+//  sum W_f over non-EMPTY points, w_out = sum W_f over EMPTY points.
+template <typename T>
+struct Epilogue {
+  const float* omega;  // P x l or NULL
+  int l;
+  float* y;            // P x l (accumulated with atomics)
+  const T* wf;         // held-out fold's bins (P x P) or NULL
+  const T* vf;
+  const T* qf;
+  double* cvacc;       // [3]: err, w_in, w_out
+};
+
+constexpr int MAXL = 64;
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
 // Block: output row x_s (blockIdx.y), t-plane rows [a0, a0 + th) (blockIdx.x).
 // The t-plane of row x_s is R rows x C columns (d = 2: t1 x t2; d = 1: 1 x t1).
 template <int d, typename T, bool COMP, int NT, int PPT>
@@ -388,9 +426,10 @@ __global__ void __launch_bounds__(NT)
     k_hpass_solve(const T* __restrict__ varr, int P, int R, int C, int TH, int Tr, int Tc,
                   const double* __restrict__ tabr, const double* __restrict__ tabc,
                   const double* __restrict__ mu_raw, T* __restrict__ gamma,
-                  uint8_t* __restrict__ status) {
+                  uint8_t* __restrict__ status, Epilogue<T> ep) {
   constexpr int NA = narr(d), NS = nslot(d), D = 2 * d + 1;
   extern __shared__ unsigned char hsm[];
+  __shared__ double red[NT / 32];
   T* wr = reinterpret_cast<T*>(hsm);       // [TROWS][TW]
   T* wc = wr + TROWS * TW;                 // [TROWS][TW]
   const int xs = blockIdx.y;
@@ -468,10 +507,15 @@ __global__ void __launch_bounds__(NT)
     if constexpr (d == 2) __syncthreads();
   }
 
-  // per-point solve and write
+  // per-point solve, write, epilogue terms
+  double gval[PPT];
+  int xts[PPT];
+  double cv_err = 0.0, cv_in = 0.0, cv_out = 0.0;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     const int e = threadIdx.x + j * NT;
+    gval[j] = 0.0;
+    xts[j] = -1;
     if (e >= npts) continue;
     const int xt = a0 * C + e;  // flat t index: (a0 + i) * C + c
     T A[D][D], rv[D];
@@ -490,6 +534,37 @@ __global__ void __launch_bounds__(NT)
     const long long o = (long long)xs * P + xt;
     if (gamma) gamma[o] = (T)g;
     if (status) status[o] = st;
+    xts[j] = xt;
+    gval[j] = st == FPCA_PT_EMPTY ? 0.0 : g;
+    if (ep.cvacc) {
+      const double wf = (double)ep.wf[o];
+      if (st == FPCA_PT_EMPTY) {
+        cv_out += wf;
+      } else {
+        cv_err += (double)ep.qf[o] - 2.0 * g * (double)ep.vf[o] + g * g * wf;
+        cv_in += wf;
+      }
+    }
+  }
+  if (ep.cvacc) {
+    const double s0 = block_sum<NT>(cv_err, red);
+    const double s1 = block_sum<NT>(cv_in, red);
+    const double s2 = block_sum<NT>(cv_out, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(ep.cvacc + 0, s0);
+      atomicAdd(ep.cvacc + 1, s1);
+      atomicAdd(ep.cvacc + 2, s2);
+    }
+  }
+  if (ep.y) {
+    for (int c = 0; c < ep.l; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < PPT; ++j)
+        if (xts[j] >= 0) s += gval[j] * (double)ep.omega[(long long)xts[j] * ep.l + c];
+      s = block_sum<NT>(s, red);
+      if (threadIdx.x == 0) atomicAdd(ep.y + (long long)xs * ep.l + c, (float)s);
+    }
   }
 }
 
@@ -511,15 +586,31 @@ __global__ void k_pool_counts(int F, long long PP, const int32_t* __restrict__ i
   out[e] = s;
 }
 
+// cv[h] = err / w_in over folds; +inf when EMPTY points hold > 1% of the
+// held-out weight or nothing was scored.
+__global__ void k_cv_finish(int nh, int F, const double* __restrict__ acc, double* __restrict__ cv) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nh) return;
+  double err = 0.0, win = 0.0, wout = 0.0;
+  for (int f = 0; f < F; ++f) {
+    err += acc[(h * F + f) * 3 + 0];
+    win += acc[(h * F + f) * 3 + 1];
+    wout += acc[(h * F + f) * 3 + 2];
+  }
+  cv[h] = (wout > 0.01 * (win + wout) || !(win > 0.0)) ? __longlong_as_double(0x7ff0000000000000ll)
+                                                       : err / win;
+}
+
+// One smoothing pass of the P x P bins (optionally train = pooled - sub_*).
 template <typename T, bool COMP>
 fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const T* w,
-                           const T* v, const double* h, const double* tab, T* mids, T* varr,
-                           const double* mu_raw, T* gamma, uint8_t* status) {
+                           const T* v, const int32_t* sub_cnt, const T* sub_w, const T* sub_v,
+                           const double* h, const double* tab, T* mids, T* varr,
+                           const double* mu_raw, T* gamma, uint8_t* status, Epilogue<T> ep) {
   const int d = g->d;
   const int P = grid_P(g);
   const long long PP = (long long)P * P;
   const int Tax[2] = {host_taps(h[0], g->m[0]), d > 1 ? host_taps(h[1], g->m[1]) : 0};
-  const size_t vsmem = sizeof(T) * (TROWS * TW + (size_t)64 * VCOLS);
   static bool vattr = false;
   if (!vattr) {
     cudaFuncSetAttribute(k_vpass<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -532,21 +623,22 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     const int M1 = g->m[0], M2 = g->m[1];
     // pass along s2 (axis 1): rows L*M2 + a
     VJobs j1{};
-    j1.j[0] = VJob{w, 0, 3, {0, 1, 2}, {mids + 0 * PP, mids + 1 * PP, mids + 2 * PP}};
-    j1.j[1] = VJob{v, 0, 2, {0, 1, 0}, {mids + 3 * PP, mids + 4 * PP, nullptr}};
-    j1.j[2] = VJob{cnt, 1, 1, {3, 0, 0}, {mids + 5 * PP, nullptr, nullptr}};
+    j1.j[0] = VJob{w, sub_w, 0, 3, {0, 1, 2}, {mids + 0 * PP, mids + 1 * PP, mids + 2 * PP}};
+    j1.j[1] = VJob{v, sub_v, 0, 2, {0, 1, 0}, {mids + 3 * PP, mids + 4 * PP, nullptr}};
+    j1.j[2] = VJob{cnt, sub_cnt, 1, 1, {3, 0, 0}, {mids + 5 * PP, nullptr, nullptr}};
     k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, M1, 3), vblk,
                        sizeof(T) * (TROWS * TW + (size_t)M2 * VCOLS), ctx->stream>>>(
         j1, P, M2, 1, Tax[1], tabk(1));
     FPCA_LAUNCHED(ctx, "cov_vpass_s2");
     // pass along s1 (axis 0): rows L + a*M2
     VJobs j2{};
-    j2.j[0] = VJob{mids + 0 * PP, 0, 3, {0, 1, 2}, {varr + 0 * PP, varr + 1 * PP, varr + 2 * PP}};
-    j2.j[1] = VJob{mids + 1 * PP, 0, 2, {0, 1, 0}, {varr + 3 * PP, varr + 4 * PP, nullptr}};
-    j2.j[2] = VJob{mids + 2 * PP, 0, 1, {0, 0, 0}, {varr + 5 * PP, nullptr, nullptr}};
-    j2.j[3] = VJob{mids + 3 * PP, 0, 2, {0, 1, 0}, {varr + 6 * PP, varr + 7 * PP, nullptr}};
-    j2.j[4] = VJob{mids + 4 * PP, 0, 1, {0, 0, 0}, {varr + 8 * PP, nullptr, nullptr}};
-    j2.j[5] = VJob{mids + 5 * PP, 0, 1, {3, 0, 0}, {varr + 9 * PP, nullptr, nullptr}};
+    j2.j[0] = VJob{mids + 0 * PP, nullptr, 0, 3, {0, 1, 2},
+                   {varr + 0 * PP, varr + 1 * PP, varr + 2 * PP}};
+    j2.j[1] = VJob{mids + 1 * PP, nullptr, 0, 2, {0, 1, 0}, {varr + 3 * PP, varr + 4 * PP, nullptr}};
+    j2.j[2] = VJob{mids + 2 * PP, nullptr, 0, 1, {0, 0, 0}, {varr + 5 * PP, nullptr, nullptr}};
+    j2.j[3] = VJob{mids + 3 * PP, nullptr, 0, 2, {0, 1, 0}, {varr + 6 * PP, varr + 7 * PP, nullptr}};
+    j2.j[4] = VJob{mids + 4 * PP, nullptr, 0, 1, {0, 0, 0}, {varr + 8 * PP, nullptr, nullptr}};
+    j2.j[5] = VJob{mids + 5 * PP, nullptr, 0, 1, {3, 0, 0}, {varr + 9 * PP, nullptr, nullptr}};
     k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, M2, 6), vblk,
                        sizeof(T) * (TROWS * TW + (size_t)M1 * VCOLS), ctx->stream>>>(
         j2, P, M1, M2, Tax[0], tabk(0));
@@ -564,28 +656,117 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     cudaFuncSetAttribute(k_hpass_solve<2, T, COMP, NT, PPT>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     k_hpass_solve<2, T, COMP, NT, PPT><<<dim3((R + TH - 1) / TH, P), NT, hsmem, ctx->stream>>>(
-        varr, P, R, C, TH, Tax[0], Tax[1], tabk(0), tabk(1), mu_raw, gamma, status);
+        varr, P, R, C, TH, Tax[0], Tax[1], tabk(0), tabk(1), mu_raw, gamma, status, ep);
     FPCA_LAUNCHED(ctx, "cov_hpass_solve");
     return FPCA_OK;
   }
   // d = 1: one vertical pass along s1, then the t pass + solve
   const int M1 = g->m[0];
   VJobs j1{};
-  j1.j[0] = VJob{w, 0, 3, {0, 1, 2}, {varr + 0 * PP, varr + 1 * PP, varr + 2 * PP}};
-  j1.j[1] = VJob{v, 0, 2, {0, 1, 0}, {varr + 3 * PP, varr + 4 * PP, nullptr}};
-  j1.j[2] = VJob{cnt, 1, 1, {3, 0, 0}, {varr + 5 * PP, nullptr, nullptr}};
+  j1.j[0] = VJob{w, sub_w, 0, 3, {0, 1, 2}, {varr + 0 * PP, varr + 1 * PP, varr + 2 * PP}};
+  j1.j[1] = VJob{v, sub_v, 0, 2, {0, 1, 0}, {varr + 3 * PP, varr + 4 * PP, nullptr}};
+  j1.j[2] = VJob{cnt, sub_cnt, 1, 1, {3, 0, 0}, {varr + 5 * PP, nullptr, nullptr}};
   k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, 1, 3), vblk,
                      sizeof(T) * (TROWS * TW + (size_t)M1 * VCOLS), ctx->stream>>>(
       j1, P, M1, 1, Tax[0], tabk(0));
   FPCA_LAUNCHED(ctx, "cov_vpass_s1");
   constexpr int NT = 128, PPT = 1;
+  if (M1 > NT * PPT) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "d = 1 needs m <= 128");
   const size_t hsmem = sizeof(T) * (2 * TROWS * TW + (size_t)narr(1) * M1 + (size_t)3 * M1);
   cudaFuncSetAttribute(k_hpass_solve<1, T, COMP, NT, PPT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-  if (M1 > NT * PPT) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "d = 1 needs m <= 128");
   k_hpass_solve<1, T, COMP, NT, PPT><<<dim3(1, P), NT, hsmem, ctx->stream>>>(
-      varr, P, 1, M1, 1, 0, Tax[0], tabk(0), tabk(0), mu_raw, gamma, status);
+      varr, P, 1, M1, 1, 0, Tax[0], tabk(0), tabk(0), mu_raw, gamma, status, ep);
   FPCA_LAUNCHED(ctx, "cov_hpass_solve");
+  return FPCA_OK;
+}
+
+template <typename T, bool COMP>
+fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins* bins,
+                             const double* h, int nh, const double* mu_raw, const float* omega,
+                             int l, T* gamma, uint8_t* status, float* y, double* cv) {
+  const int d = g->d;
+  const int P = grid_P(g);
+  const long long PP = (long long)P * P;
+  const int F = bins->nfold > 0 ? bins->nfold : 1;
+  const int nmid = d == 2 ? 6 : 0;
+  const size_t need = WsCarve::round(sizeof(double) * 3 * TROWS * TW) +
+                      WsCarve::round(sizeof(T) * PP * (size_t)(nmid + narr(d))) +
+                      (F > 1 ? WsCarve::round(sizeof(T) * PP) * 2 + WsCarve::round(4 * PP) : 0) +
+                      WsCarve::round(sizeof(double) * 3 * (size_t)nh * F) + 4096;
+  void* ws = fpca_workspace(ctx, need);
+  if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
+  WsCarve carve(ws);
+  double* tab = carve.take<double>(3 * TROWS * TW);
+  T* mids = carve.take<T>((size_t)PP * nmid);
+  T* varr = carve.take<T>((size_t)PP * narr(d));
+  double* cvacc = carve.take<double>((size_t)3 * nh * F);
+  const T* w = static_cast<const T*>(bins->w);
+  const T* v = static_cast<const T*>(bins->v);
+  const int32_t* cnt = bins->cnt;
+  if (F > 1) {
+    T* wp = carve.take<T>(PP);
+    T* vp = carve.take<T>(PP);
+    int32_t* cp = carve.take<int32_t>(PP);
+    const int nb = (int)((PP + 255) / 256);
+    k_pool_folds<T><<<nb, 256, 0, ctx->stream>>>(F, PP, w, wp);
+    FPCA_LAUNCHED(ctx, "pool_folds");
+    k_pool_folds<T><<<nb, 256, 0, ctx->stream>>>(F, PP, v, vp);
+    FPCA_LAUNCHED(ctx, "pool_folds");
+    k_pool_counts<<<nb, 256, 0, ctx->stream>>>(F, PP, cnt, cp);
+    FPCA_LAUNCHED(ctx, "pool_counts");
+    w = wp;
+    v = vp;
+    cnt = cp;
+  }
+  if (y) cudaMemsetAsync(y, 0, sizeof(float) * (size_t)nh * P * l, ctx->stream);
+  if (cv) cudaMemsetAsync(cvacc, 0, sizeof(double) * 3 * (size_t)nh * F, ctx->stream);
+  for (int ih = 0; ih < nh; ++ih) {
+    const double* hh = h + (size_t)ih * d;
+    TapParams tp{};
+    tp.d = d;
+    for (int k = 0; k < 3; ++k) {
+      tp.m[k] = k < d ? g->m[k] : 1;
+      tp.h[k] = k < d ? hh[k] : 1.0;
+    }
+    k_taps<<<d, 128, 0, ctx->stream>>>(tp, tab);
+    FPCA_LAUNCHED(ctx, "taps");
+    // the fit on all bins: Gamma_hat, status, projection
+    if (gamma || status || y) {
+      Epilogue<T> ep{};
+      if (y) {
+        ep.omega = omega;
+        ep.l = l;
+        ep.y = y + (size_t)ih * P * l;
+      }
+      fpca_status s = cov_smooth_one<T, COMP>(
+          ctx, g, cnt, w, v, nullptr, nullptr, nullptr, hh, tab, mids, varr, mu_raw,
+          gamma ? gamma + (size_t)ih * PP : nullptr, status ? status + (size_t)ih * PP : nullptr,
+          ep);
+      if (s != FPCA_OK) return s;
+    }
+    // K-fold CV: fit on the other folds, score the held-out fold
+    if (cv) {
+      const T* fw = static_cast<const T*>(bins->w);
+      const T* fv = static_cast<const T*>(bins->v);
+      const T* fq = static_cast<const T*>(bins->q);
+      for (int f = 0; f < F; ++f) {
+        Epilogue<T> ep{};
+        ep.wf = fw + (size_t)f * PP;
+        ep.vf = fv + (size_t)f * PP;
+        ep.qf = fq + (size_t)f * PP;
+        ep.cvacc = cvacc + 3 * ((size_t)ih * F + f);
+        fpca_status s = cov_smooth_one<T, COMP>(
+            ctx, g, cnt, w, v, bins->cnt + (size_t)f * PP, fw + (size_t)f * PP,
+            fv + (size_t)f * PP, hh, tab, mids, varr, mu_raw, nullptr, nullptr, ep);
+        if (s != FPCA_OK) return s;
+      }
+    }
+  }
+  if (cv) {
+    k_cv_finish<<<(nh + 63) / 64, 64, 0, ctx->stream>>>(nh, F, cvacc, cv);
+    FPCA_LAUNCHED(ctx, "cv_finish");
+  }
   return FPCA_OK;
 }
 
@@ -626,85 +807,17 @@ fpca_status smooth_cov_run(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins
                            const double* h, int nh, int prec, const double* mu_raw,
                            const float* omega, int l, void* gamma, uint8_t* status, float* y,
                            double* cv) {
-  if (y || cv)
-    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection and CV outputs are not built yet");
-  const int d = g->d;
-  const int P = grid_P(g);
-  const long long PP = (long long)P * P;
-  const size_t esz = prec == FPCA_F64 ? sizeof(double) : sizeof(float);
-  const int F = bins->nfold > 0 ? bins->nfold : 1;
-  const int nmid = d == 2 ? 6 : 0;
-  const size_t need = WsCarve::round(sizeof(double) * 3 * TROWS * TW) +
-                      WsCarve::round(esz * PP * (size_t)(nmid + narr(d))) +
-                      (F > 1 ? WsCarve::round(esz * PP) * 2 + WsCarve::round(4 * PP) : 0) + 4096;
-  void* ws = fpca_workspace(ctx, need);
-  if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
-  WsCarve carve(ws);
-  double* tab = carve.take<double>(3 * TROWS * TW);
-  unsigned char* mids = carve.take<unsigned char>(esz * PP * nmid);
-  unsigned char* varr = carve.take<unsigned char>(esz * PP * narr(d));
-  const void* w = bins->w;
-  const void* v = bins->v;
-  const int32_t* cnt = bins->cnt;
-  if (F > 1) {
-    void* wp = carve.take<unsigned char>(esz * PP);
-    void* vp = carve.take<unsigned char>(esz * PP);
-    int32_t* cp = carve.take<int32_t>(PP);
-    const int nb = (int)((PP + 255) / 256);
-    if (prec == FPCA_F64) {
-      k_pool_folds<double><<<nb, 256, 0, ctx->stream>>>(F, PP, static_cast<const double*>(w),
-                                                         static_cast<double*>(wp));
-      k_pool_folds<double><<<nb, 256, 0, ctx->stream>>>(F, PP, static_cast<const double*>(v),
-                                                         static_cast<double*>(vp));
-    } else {
-      k_pool_folds<float><<<nb, 256, 0, ctx->stream>>>(F, PP, static_cast<const float*>(w),
-                                                        static_cast<float*>(wp));
-      k_pool_folds<float><<<nb, 256, 0, ctx->stream>>>(F, PP, static_cast<const float*>(v),
-                                                        static_cast<float*>(vp));
-    }
-    k_pool_counts<<<nb, 256, 0, ctx->stream>>>(F, PP, cnt, cp);
-    ctx->launches += 3;
-    fpca_status s = fpca_check_launch(ctx, "pool_folds");
-    if (s != FPCA_OK) return s;
-    w = wp;
-    v = vp;
-    cnt = cp;
-  }
-  for (int ih = 0; ih < nh; ++ih) {
-    const double* hh = h + (size_t)ih * d;
-    for (int k = 0; k < d; ++k)
-      if (host_taps(hh[k], g->m[k]) > TMAX)
+  if (l > MAXL) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection built for l <= %d", MAXL);
+  for (int ih = 0; ih < nh; ++ih)
+    for (int k = 0; k < g->d; ++k)
+      if (host_taps(h[(size_t)ih * g->d + k], g->m[k]) > TMAX)
         return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "bandwidth too wide");
-    TapParams tp{};
-    tp.d = d;
-    for (int k = 0; k < 3; ++k) {
-      tp.m[k] = k < d ? g->m[k] : 1;
-      tp.h[k] = k < d ? hh[k] : 1.0;
-    }
-    k_taps<<<d, 128, 0, ctx->stream>>>(tp, tab);
-    FPCA_LAUNCHED(ctx, "taps");
-    fpca_status s;
-    uint8_t* st = status ? status + (size_t)ih * PP : nullptr;
-    if (prec == FPCA_F64) {
-      double* gm = gamma ? static_cast<double*>(gamma) + (size_t)ih * PP : nullptr;
-      s = cov_smooth_one<double, false>(ctx, g, cnt, static_cast<const double*>(w),
-                                        static_cast<const double*>(v), hh, tab,
-                                        reinterpret_cast<double*>(mids),
-                                        reinterpret_cast<double*>(varr), mu_raw, gm, st);
-    } else {
-      float* gm = gamma ? static_cast<float*>(gamma) + (size_t)ih * PP : nullptr;
-      if (prec == FPCA_F32C)
-        s = cov_smooth_one<float, true>(ctx, g, cnt, static_cast<const float*>(w),
-                                        static_cast<const float*>(v), hh, tab,
-                                        reinterpret_cast<float*>(mids),
-                                        reinterpret_cast<float*>(varr), mu_raw, gm, st);
-      else
-        s = cov_smooth_one<float, false>(ctx, g, cnt, static_cast<const float*>(w),
-                                         static_cast<const float*>(v), hh, tab,
-                                         reinterpret_cast<float*>(mids),
-                                         reinterpret_cast<float*>(varr), mu_raw, gm, st);
-    }
-    if (s != FPCA_OK) return s;
-  }
-  return FPCA_OK;
+  if (prec == FPCA_F64)
+    return smooth_cov_typed<double, false>(ctx, g, bins, h, nh, mu_raw, omega, l,
+                                           static_cast<double*>(gamma), status, y, cv);
+  if (prec == FPCA_F32C)
+    return smooth_cov_typed<float, true>(ctx, g, bins, h, nh, mu_raw, omega, l,
+                                         static_cast<float*>(gamma), status, y, cv);
+  return smooth_cov_typed<float, false>(ctx, g, bins, h, nh, mu_raw, omega, l,
+                                        static_cast<float*>(gamma), status, y, cv);
 }
