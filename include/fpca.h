@@ -214,6 +214,35 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
                            const float* omega, int l, int k, int power_iters, int full,
                            double* evals, double* evecs, double* fve);
 
+/* Mean bins of gridded data without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code whose device memory is owned by another
+ * allocator (a framework's caching pool or a fixed arena), code running
+ * where allocation is not allowed, or hosts that forbid libraries from
+ * allocating behind their back.  It needs no fpca_ctx (creating one
+ * allocates) and computes exactly what fpca_bin_mean computes for
+ * FPCA_DENSE data, on the given stream (NULL = legacy default stream) of the
+ * current device.
+ *
+ *  y: n x P row-major, FP64 (y_prec FPCA_F64) or FP32 (FPCA_F32); mask: n x P
+ *  uint8 or NULL; outputs cnt, w, v (and v2 unless NULL) of length P.  All
+ *  are caller-owned device pointers.
+ *
+ * Scratch: the per-subject counts N_i live in a file-scope __device__ array
+ * of 2^20 int32 (4 MiB) that every GPU loading the library holds until the
+ * process exits.  n > 2^20 returns FPCA_E_UNSUPPORTED without launching.
+ * Each call overwrites entries 0..n-1 before reading them, so nothing needs
+ * to start at zero; all calls share the array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * with that device current (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Errors: FPCA_E_INVALID_ARG for bad
+ * arguments, FPCA_E_CUDA for a failed lookup or launch. */
+fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, const void* y, int y_prec,
+                                 const uint8_t* mask, int32_t* cnt, double* w, double* v,
+                                 double* v2);
+
 #ifdef __cplusplus
 }
 #endif

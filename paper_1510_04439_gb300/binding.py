@@ -27,7 +27,7 @@ SYMBOLS = (
     "fpca_create", "fpca_destroy", "fpca_set_stream", "fpca_last_error", "fpca_sync",
     "fpca_launch_count", "fpca_bin_mean", "fpca_smooth_mean", "fpca_bin_cov",
     "fpca_smooth_cov_project", "fpca_rproj_eig", "fpca_profile_enable", "fpca_profile_count",
-    "fpca_profile_entry",
+    "fpca_profile_entry", "fpca_bin_mean_static",
 )
 
 
@@ -102,6 +102,7 @@ def load(path=LIB_PATH):
                                             dbl_p, i32, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.fpca_rproj_eig.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, vp, vp, i32, i32, i32, i32,
                                    vp, vp, vp]
+    lib.fpca_bin_mean_static.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
     lib.fpca_profile_count.argtypes = [vp]
     lib.fpca_profile_entry.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
