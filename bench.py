@@ -251,9 +251,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = B.Context(local_rank, stream)
 
-    def step(yy, mm):
+    def step(yy, mm, smooth_prec=B.F32C):
         pipeline.run_dense(ctx, D.m, yy, mm, H, H, K_EIG, bufs, bin_prec=B.BF16,
-                           smooth_prec=B.F32C, omega=omega, power_iters=Q_POWER)
+                           smooth_prec=smooth_prec, omega=omega, power_iters=Q_POWER)
 
     def barrier():
         if world > 1:
@@ -329,10 +329,30 @@ def main():
     h2d = y_host.numel() * y_host.element_size() + m_host.numel() * m_host.element_size()
     d2h = (ev_h.numel() + vec_h.numel() + fve_h.numel()) * 8
 
+    # ---- the same step with uncompensated FP32 moment sums (reported beside) ----
+    for _ in range(3):
+        step(y, mask, B.F32)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(y, mask, B.F32)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    prof_u = ctx.profile_read()
+    ctx.profile(False)
+    ms_u = maxreduce(sum(a.elapsed_time(b) for a, b in evs) / args.steps)
+
     # ---- roofline of the dominant kernel (t-side sweep + per-point solve) ----
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     hp = prof.get("cov_hpass_solve")
     roof = None
+    variant = None
     if hp:
         M0, M1 = D.m
         T0, T1 = taps(H[0], M0), taps(H[1], M1)
@@ -349,6 +369,14 @@ def main():
                 "ms_per_launch": per_launch_ms, "flops_per_point": flops_pt,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "dominant_kernel_by_time": dom}
+        hu = prof_u.get("cov_hpass_solve")
+        if hu:
+            ach_u = flops_pt * units / (hu[0] / hu[1] * 1e-3) / 1e12
+            variant = {"precision": "FP32 moments without compensation",
+                       "ms_per_step": ms_u, "value": world * units / (ms_u * 1e-3),
+                       "roofline": {"kernel": "cov_hpass_solve", "bound": "alu",
+                                    "achieved": ach_u, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": ach_u / peak, "ms_per_launch": hu[0] / hu[1]}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,6 +405,7 @@ def main():
                     "ms_per_step": ms_e2e},
             "gpu_launches": launches,
             "roofline": roof,
+            "variant_uncompensated": variant,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernels": kernels,

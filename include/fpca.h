@@ -214,6 +214,48 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
                            const float* omega, int l, int k, int power_iters, int full,
                            double* evals, double* evecs, double* fve);
 
+/* Learned bandwidth proposal.  Section 3.3 selects bandwidths by
+ * cross-validation over candidates and calls grid search expensive; this
+ * network maps a 32-number summary of a dataset's bins (fpca_bw_features)
+ * to the CV-optimal log bandwidths [log h_mu (3), log h_Gamma (3)], so that
+ * one smoothing pass plus a CV check can replace the grid.
+ * Architecture 32 -> 256 -> 256 -> 256 -> 6, exact GELU after each hidden
+ * layer; weights used in FP16 (rounded from the FP32 master copy), FP32
+ * accumulation.  Parameter vector (device float, fpca_bw_param_count()
+ * entries): for each layer W (fan_in x fan_out, row-major) then b. */
+int64_t fpca_bw_param_count(void);
+/* out (B x 6) = network(feat (B x 32)); all device float. */
+fpca_status fpca_bw_predict(fpca_ctx* ctx, const float* params, const float* feat, int B,
+                            float* out);
+/* One training step on a batch: loss = sum m (out - target)^2 / sum m over
+ * the B x 6 entries with tmask (uint8) set; the gradient of the loss by
+ * manual backward; if step >= 1, one AdamW update (beta 0.9/0.999, eps
+ * 1e-8, bias correction for update number `step`, decoupled weight decay wd)
+ * of params with moments adam_m, adam_v (device float, zero initially).
+ * step = 0 computes loss and gradient only.  loss (device float) and
+ * grad_out (param_count floats) may be NULL. */
+fpca_status fpca_bw_train_step(fpca_ctx* ctx, float* params, float* adam_m, float* adam_v,
+                               int step, const float* feat, const float* target,
+                               const uint8_t* tmask, int B, float lr, float wd, float* loss,
+                               float* grad_out);
+
+/* The network's input: 32 summary numbers of one dataset (device float
+ * feat[32]) from its observations (for the per-subject counts N_i), its mean
+ * bins (cnt, w, v, v2 as produced by fpca_bin_mean; v2 may be NULL) and its
+ * pooled covariance bins (nfold <= 1).  Features, in order: d; log n; log
+ * mean N_i; std/mean N_i; log min N_i; log max N_i; log(1 + mean bin count);
+ * var/mean^2 and skewness of bin counts; fraction of empty bins; log mean
+ * within-bin variance v2/w - (v/w)^2; log variance of the binned mean v/w;
+ * log mean squared 2nd difference of v/w along axes 0..2 and 1st difference
+ * along axes 0..1, relative to that variance; 0; log roughness of the
+ * covariance raw means V/W along s_1 and along the (s_1, t_1) diagonal,
+ * relative to their variance; log(1 + mean pair count); fraction of
+ * covariance bins with a pair; log 1/M_k (k < d); zeros.  Non-empty means
+ * w > 0; sums in FP64. */
+fpca_status fpca_bw_features(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                             const int32_t* cnt, const double* w, const double* v,
+                             const double* v2, const fpca_covbins* bins, float* feat);
+
 /* Mean bins of gridded data without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

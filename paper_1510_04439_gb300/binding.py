@@ -27,7 +27,8 @@ SYMBOLS = (
     "fpca_create", "fpca_destroy", "fpca_set_stream", "fpca_last_error", "fpca_sync",
     "fpca_launch_count", "fpca_bin_mean", "fpca_smooth_mean", "fpca_bin_cov",
     "fpca_smooth_cov_project", "fpca_rproj_eig", "fpca_profile_enable", "fpca_profile_count",
-    "fpca_profile_entry", "fpca_bin_mean_static",
+    "fpca_profile_entry", "fpca_bin_mean_static", "fpca_bw_param_count", "fpca_bw_predict",
+    "fpca_bw_train_step", "fpca_bw_features",
 )
 
 
@@ -102,6 +103,13 @@ def load(path=LIB_PATH):
                                             dbl_p, i32, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.fpca_rproj_eig.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, vp, vp, i32, i32, i32, i32,
                                    vp, vp, vp]
+    lib.fpca_bw_features.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp, vp,
+                                     ctypes.POINTER(CovBins), vp]
+    lib.fpca_bw_param_count.argtypes = []
+    lib.fpca_bw_param_count.restype = ctypes.c_int64
+    lib.fpca_bw_predict.argtypes = [vp, vp, vp, i32, vp]
+    lib.fpca_bw_train_step.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, ctypes.c_float,
+                                       ctypes.c_float, vp, vp]
     lib.fpca_bin_mean_static.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
     lib.fpca_profile_count.argtypes = [vp]
@@ -109,7 +117,8 @@ def load(path=LIB_PATH):
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
     for name in SYMBOLS:
         f = getattr(lib, name)
-        if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count"):
+        if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count",
+                        "fpca_bw_param_count"):
             f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -180,6 +189,30 @@ class Context:
                                                     ctypes.byref(cnt)))
             out[name.value.decode()] = (ms.value, int(cnt.value))
         return out
+
+    # ---- bandwidth network ---------------------------------------------------
+    def bw_param_count(self):
+        return int(self.lib.fpca_bw_param_count())
+
+    def bw_features(self, data, m, cnt, w, v, v2, ccnt, cw, cv, feat):
+        bins = CovBins()
+        bins.nfold = 0
+        bins.prec = F64 if cw.dtype.itemsize == 8 else F32
+        bins.cnt, bins.w, bins.v = ccnt.data_ptr(), cw.data_ptr(), cv.data_ptr()
+        bins.q = None
+        self._check(self.lib.fpca_bw_features(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                              _ptr(cnt), _ptr(w), _ptr(v), _ptr(v2),
+                                              ctypes.byref(bins), _ptr(feat)))
+
+    def bw_predict(self, params, feat, out):
+        self._check(self.lib.fpca_bw_predict(self.h, _ptr(params), _ptr(feat), int(feat.shape[0]),
+                                             _ptr(out)))
+
+    def bw_train_step(self, params, m, v, step, feat, target, tmask, lr=1e-3, wd=1e-4,
+                      loss=None, grad=None):
+        self._check(self.lib.fpca_bw_train_step(
+            self.h, _ptr(params), _ptr(m), _ptr(v), int(step), _ptr(feat), _ptr(target),
+            _ptr(tmask), int(feat.shape[0]), float(lr), float(wd), _ptr(loss), _ptr(grad)))
 
     # ---- data descriptors --------------------------------------------------
     @staticmethod

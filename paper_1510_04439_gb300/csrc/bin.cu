@@ -47,32 +47,65 @@ __global__ void k_subject_counts(int n, int P, const uint8_t* __restrict__ mask,
   }
 }
 
-// Dense mean bins: one thread per node, subjects in order (weights 1/N_i).
-__global__ void k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y_prec,
-                                 const uint8_t* __restrict__ mask,
-                                 const int32_t* __restrict__ Ni, int32_t* __restrict__ cnt,
-                                 double* __restrict__ w, double* __restrict__ v,
-                                 double* __restrict__ v2) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+// Dense mean bins: a block covers 32 nodes; its 8 thread rows take every
+// 8th subject, and the 8 partial sums are added in a fixed order
+// (deterministic).  Weights 1/N_i.
+constexpr int MB_SLICES = 8;
+__global__ void __launch_bounds__(32 * MB_SLICES)
+    k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y_prec,
+                     const uint8_t* __restrict__ mask, const int32_t* __restrict__ Ni,
+                     int32_t* __restrict__ cnt, double* __restrict__ w, double* __restrict__ v,
+                     double* __restrict__ v2) {
+  __shared__ double ps[3][MB_SLICES][32];
+  __shared__ int pc[MB_SLICES][32];
+  __shared__ double winv[256];
+  const int p = blockIdx.x * 32 + threadIdx.x;
   int c = 0;
   double sw = 0.0, sv = 0.0, sv2 = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const size_t idx = (size_t)i * P + p;
-    if (mask && !mask[idx]) continue;
-    const int N = Ni[i];
-    if (N <= 0) continue;
-    const double wi = 1.0 / (double)N;
-    const double yy = load_y(y, y_prec, idx);
-    c += 1;
-    sw = __dadd_rn(sw, wi);
-    sv = __dadd_rn(sv, __dmul_rn(wi, yy));
-    sv2 = __dadd_rn(sv2, __dmul_rn(wi, __dmul_rn(yy, yy)));
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int i0 = 0; i0 < n; i0 += 256) {
+    // 1/N_i for the next 256 subjects, one division per subject
+    __syncthreads();
+    {
+      const int i = i0 + tid;
+      const int N = i < n ? Ni[i] : 0;
+      winv[tid] = N > 0 ? 1.0 / (double)N : 0.0;
+    }
+    __syncthreads();
+    if (p < P) {
+      const int iend = min(n, i0 + 256);
+      for (int i = i0 + threadIdx.y; i < iend; i += MB_SLICES) {
+        const size_t idx = (size_t)i * P + p;
+        if (mask && !mask[idx]) continue;
+        const double wi = winv[i - i0];
+        if (wi == 0.0) continue;
+        const double yy = load_y(y, y_prec, idx);
+        c += 1;
+        sw = __dadd_rn(sw, wi);
+        sv = __dadd_rn(sv, __dmul_rn(wi, yy));
+        sv2 = __dadd_rn(sv2, __dmul_rn(wi, __dmul_rn(yy, yy)));
+      }
+    }
   }
-  cnt[p] = c;
-  w[p] = sw;
-  v[p] = sv;
-  if (v2) v2[p] = sv2;
+  ps[0][threadIdx.y][threadIdx.x] = sw;
+  ps[1][threadIdx.y][threadIdx.x] = sv;
+  ps[2][threadIdx.y][threadIdx.x] = sv2;
+  pc[threadIdx.y][threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.y == 0 && p < P) {
+    int ct = 0;
+    double tw = 0.0, tv = 0.0, tv2 = 0.0;
+    for (int k = 0; k < MB_SLICES; ++k) {
+      ct += pc[k][threadIdx.x];
+      tw += ps[0][k][threadIdx.x];
+      tv += ps[1][k][threadIdx.x];
+      tv2 += ps[2][k][threadIdx.x];
+    }
+    cnt[p] = ct;
+    w[p] = tw;
+    v[p] = tv;
+    if (v2) v2[p] = tv2;
+  }
 }
 
 // Sparse mean bins: one thread per subject, atomic scatter into the bins.
@@ -111,21 +144,35 @@ __global__ void k_cov_operands_bf16(int n, int P, int Kpad, const void* __restri
                                     const int32_t* __restrict__ Ni, const double* __restrict__ mu,
                                     int mode, __nv_bfloat16* __restrict__ ops) {
   __shared__ float tm[32][33], tw[32][33], tr[32][33];
+  __shared__ float wsub[32], swsub[32];
   const int i0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+  // per-subject weights w_i = 1/(N_i (N_i - 1)) and sqrt(w_i), once per subject
+  if (threadIdx.y == 0) {
+    const int i = i0 + threadIdx.x;
+    const int N = i < n ? Ni[i] : 0;
+    const double wi = N >= 2 ? 1.0 / ((double)N * (double)(N - 1)) : 0.0;
+    wsub[threadIdx.x] = (float)wi;
+    swsub[threadIdx.x] = (float)sqrt(wi);
+  }
+  __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int i = i0 + r, p = p0 + threadIdx.x;
     float fm = 0.f, fw = 0.f, fr = 0.f;
     if (i < n && p < P) {
       const size_t idx = (size_t)i * P + p;
       const bool obs = mask ? mask[idx] != 0 : true;
-      const int N = Ni[i];
       if (obs) {
-        const double wi = N >= 2 ? 1.0 / ((double)N * (double)(N - 1)) : 0.0;
-        const double yy = load_y(y, y_prec, idx);
-        const double rr = mode == FPCA_COV_RESIDUAL ? yy - mu[p] : yy;
+        float rr;
+        if (y_prec == FPCA_F64) {
+          const double yy = static_cast<const double*>(y)[idx];
+          rr = (float)(mode == FPCA_COV_RESIDUAL ? yy - mu[p] : yy);
+        } else {
+          const float yy = static_cast<const float*>(y)[idx];
+          rr = mode == FPCA_COV_RESIDUAL ? (float)((double)yy - mu[p]) : yy;
+        }
         fm = 1.f;
-        fw = (float)wi;
-        fr = (float)(sqrt(wi) * rr);
+        fw = wsub[r];
+        fr = swsub[r] * rr;
       }
     }
     tm[r][threadIdx.x] = fm;
@@ -281,8 +328,8 @@ fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8
 fpca_status launch_bin_mean_dense(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
                                   const uint8_t* mask, const int32_t* Ni, int32_t* cnt,
                                   double* w, double* v, double* v2) {
-  k_bin_mean_dense<<<(P + 127) / 128, 128, 0, ctx->stream>>>(n, P, y, y_prec, mask, Ni, cnt, w,
-                                                              v, v2);
+  k_bin_mean_dense<<<(P + 31) / 32, dim3(32, MB_SLICES), 0, ctx->stream>>>(n, P, y, y_prec, mask,
+                                                                          Ni, cnt, w, v, v2);
   FPCA_LAUNCHED(ctx, "bin_mean_dense");
   return FPCA_OK;
 }

@@ -20,30 +20,40 @@ __device__ __forceinline__ double gval(const TG* G, long long idx) {
 }
 
 // Sigma = sym(G) with NaN and out-of-domain entries zeroed; trace accumulated.
+// The arithmetic is done in the type of Sigma (FP32 for the projected path).
 template <typename TG, typename TS>
 __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __restrict__ dom,
                             TS* __restrict__ S, double* __restrict__ trace) {
-  __shared__ double tile[32][33];
+  __shared__ TS tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   // transposed tile: rows q in [bx, bx+32), columns p in [by, by+32)
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int q = bx + r, p = by + threadIdx.x;
-    tile[r][threadIdx.x] = (q < P && p < P) ? gval(G, (long long)q * P + p) : 0.0;
+    TS v = TS(0);
+    if (q < P && p < P) {
+      v = (TS)G[(long long)q * P + p];
+      if (isnan(v)) v = TS(0);
+    }
+    tile[r][threadIdx.x] = v;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int p = by + r, q = bx + threadIdx.x;
     if (p < P && q < P) {
-      double s = 0.5 * (gval(G, (long long)p * P + q) + tile[threadIdx.x][r]);
-      if (dom && (dom[p] <= 0 || dom[q] <= 0)) s = 0.0;
-      S[(long long)p * P + q] = (TS)s;
-      if (p == q) atomicAdd(trace, s);
+      TS g = (TS)G[(long long)p * P + q];
+      if (isnan(g)) g = TS(0);
+      TS sv = TS(0.5) * (g + tile[threadIdx.x][r]);
+      if (dom && (dom[p] <= 0 || dom[q] <= 0)) sv = TS(0);
+      S[(long long)p * P + q] = sv;
+      if (p == q) atomicAdd(trace, (double)sv);
     }
   }
 }
 
 // Y (P x l) = S (P x P) X (P x l): a warp per RPW rows, lanes stride over the
 // columns of S, X staged in shared memory in chunks of QCH rows.
+// The column range is split over gridDim.y blocks (split-K); partial sums
+// are added to Y (zeroed beforehand) with atomics.
 template <typename TS, typename TX, int LM, int RPW>
 __global__ void __launch_bounds__(256)
     k_proj(int P, int l, const TS* __restrict__ S, const TX* __restrict__ X,
@@ -58,26 +68,33 @@ __global__ void __launch_bounds__(256)
   for (int r = 0; r < RPW; ++r)
 #pragma unroll
     for (int c = 0; c < LM; ++c) acc[r][c] = TX(0);
-  for (int q0 = 0; q0 < P; q0 += QCH) {
+  const int span = (P + gridDim.y - 1) / gridDim.y;
+  const int qbeg = blockIdx.y * span, qend = min(P, qbeg + span);
+  for (int q0 = qbeg; q0 < qend; q0 += QCH) {
     __syncthreads();
     for (int e = threadIdx.x; e < QCH * LM; e += 256) {
       const int qq = e / LM, c = e - qq * LM;
-      xs[qq * LP + c] = (q0 + qq < P && c < l) ? X[(long long)(q0 + qq) * l + c] : TX(0);
+      xs[qq * LP + c] = (q0 + qq < qend && c < l) ? X[(long long)(q0 + qq) * l + c] : TX(0);
     }
     __syncthreads();
-#pragma unroll 2
-    for (int t = lane; t < QCH; t += 32) {
-      const int q = q0 + t;
-      if (q >= P) break;
-      TX sv[RPW];
+    // all of this chunk's Sigma loads are issued before the FMAs
+    constexpr int NQ = QCH / 32;
+    TX sv[NQ][RPW];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int q = q0 + lane + 32 * u;
 #pragma unroll
       for (int r = 0; r < RPW; ++r)
-        sv[r] = (row0 + r < P) ? (TX)S[(long long)(row0 + r) * P + q] : TX(0);
+        sv[u][r] = (q < qend && row0 + r < P) ? (TX)S[(long long)(row0 + r) * P + q] : TX(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int t = lane + 32 * u;
 #pragma unroll
       for (int c = 0; c < LM; ++c) {
         const TX xv = xs[t * LP + c];
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) acc[r][c] = fma(sv[r], xv, acc[r][c]);
+        for (int r = 0; r < RPW; ++r) acc[r][c] = fma(sv[u][r], xv, acc[r][c]);
       }
     }
   }
@@ -95,7 +112,7 @@ __global__ void __launch_bounds__(256)
       if (row0 + r < P) {
 #pragma unroll
         for (int c = 0; c < LM; ++c)
-          if (c < l) Y[(long long)(row0 + r) * l + c] = acc[r][c];
+          if (c < l) atomicAdd(Y + (long long)(row0 + r) * l + c, acc[r][c]);
       }
   }
 }
@@ -115,42 +132,110 @@ __global__ void k_cross_gram(int P, int l, const TX* __restrict__ A, const TX* _
   }
 }
 
-// Upper Cholesky G = R'R (one thread; l <= 128) and Rinv; rank-deficient
-// directions (pivot <= 1e-13 of the largest diagonal) get a zero column.
+// Upper Cholesky G = R'R and Rinv (one block, l <= 64, shared memory).
+// Column j: the pivot by thread 0, the rest of row j of R in parallel; then
+// each thread back-substitutes one column of Rinv.  Rank-deficient
+// directions (pivot <= 1e-13 of the largest diagonal) get a zero row/column.
 __global__ void k_chol_inv(int l, const double* __restrict__ G, double* __restrict__ Rinv,
                            double* __restrict__ work) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* R = work;  // l x l
-  double dmax = 0.0;
-  for (int i = 0; i < l; ++i) dmax = fmax(dmax, G[i * l + i]);
-  for (int i = 0; i < l * l; ++i) R[i] = 0.0;
-  for (int j = 0; j < l; ++j) {
-    double s = G[j * l + j];
-    for (int k = 0; k < j; ++k) s -= R[k * l + j] * R[k * l + j];
-    if (!(s > 1e-13 * dmax)) {
-      R[j * l + j] = 0.0;  // dropped direction
-      continue;
-    }
-    const double rjj = sqrt(s);
-    R[j * l + j] = rjj;
-    for (int i = j + 1; i < l; ++i) {
-      double t = G[j * l + i];
-      for (int k = 0; k < j; ++k) t -= R[k * l + j] * R[k * l + i];
-      R[j * l + i] = t / rjj;
-    }
+  (void)work;
+  __shared__ double R[64 * 64];
+  __shared__ double dmax_s;
+  const int t = threadIdx.x;
+  for (int e = t; e < l * l; e += blockDim.x) R[e] = G[e];
+  __syncthreads();
+  if (t == 0) {
+    double dm = 0.0;
+    for (int i = 0; i < l; ++i) dm = fmax(dm, R[i * l + i]);
+    dmax_s = dm;
   }
-  // Rinv: upper triangular inverse, zero rows/columns for dropped directions
-  for (int i = 0; i < l * l; ++i) Rinv[i] = 0.0;
+  __syncthreads();
+  // in place: R[j][i] (i >= j) becomes the Cholesky factor; the strict lower part is zeroed
   for (int j = 0; j < l; ++j) {
+    if (t == 0) {
+      double sdiag = R[j * l + j];
+      for (int k = 0; k < j; ++k) sdiag -= R[k * l + j] * R[k * l + j];
+      R[j * l + j] = sdiag > 1e-13 * dmax_s ? sqrt(sdiag) : 0.0;
+    }
+    __syncthreads();
+    const double rjj = R[j * l + j];
+    for (int i = j + 1 + t; i < l; i += blockDim.x) {
+      double v = R[j * l + i];
+      for (int k = 0; k < j; ++k) v -= R[k * l + j] * R[k * l + i];
+      R[j * l + i] = rjj > 0.0 ? v / rjj : 0.0;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e - (e / l) * l;
+    if (i > j) R[e] = 0.0;
+  }
+  __syncthreads();
+  for (int j = t; j < l; j += blockDim.x) {
+    for (int i = 0; i < l; ++i) Rinv[i * l + j] = 0.0;
     if (R[j * l + j] == 0.0) continue;
     Rinv[j * l + j] = 1.0 / R[j * l + j];
     for (int i = j - 1; i >= 0; --i) {
       if (R[i * l + i] == 0.0) continue;
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s += R[i * l + k] * Rinv[k * l + j];
-      Rinv[i * l + j] = -s / R[i * l + i];
+      double acc = 0.0;
+      for (int k = i + 1; k <= j; ++k) acc += R[i * l + k] * Rinv[k * l + j];
+      Rinv[i * l + j] = -acc / R[i * l + i];
     }
   }
+}
+
+// Upper Cholesky G = R'R and Rinv by one warp (l <= 32): lane i holds column
+// i of R and of Rinv in registers; column j of the factor needs only
+// shuffles of row j.  Rank-deficient directions (pivot <= 1e-13 of the
+// largest diagonal) get a zero row/column.
+__global__ void __launch_bounds__(32) k_chol_inv_warp(int l, const double* __restrict__ G,
+                                                      double* __restrict__ Rinv) {
+  const int i = threadIdx.x;
+  double Rc[32];  // Rc[k] = R[k][i] (column i of the upper factor)
+#pragma unroll
+  for (int k = 0; k < 32; ++k) Rc[k] = 0.0;
+  double gcol[32];  // G[k][i]
+#pragma unroll
+  for (int k = 0; k < 32; ++k) gcol[k] = (k < l && i < l) ? G[k * l + i] : 0.0;
+  double dmax = (i < l) ? G[i * l + i] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j >= l) break;
+    // R[j][i] = (G[j][i] - sum_{k<j} R[k][j] R[k][i]) / R[j][j]  for i >= j
+    double v = gcol[j];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k >= j) break;
+      v -= __shfl_sync(0xffffffffu, Rc[k], j) * Rc[k];
+    }
+    // lane j's v is the pivot
+    const double piv = __shfl_sync(0xffffffffu, v, j);
+    const double rjj = piv > 1e-13 * dmax ? sqrt(piv) : 0.0;
+    if (i == j) Rc[j] = rjj;
+    else if (i > j) Rc[j] = rjj > 0.0 ? v / rjj : 0.0;
+  }
+  // Rinv column i: back substitution  R Rinv[:, i] = e_i
+  double x[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) x[k] = 0.0;
+  // need R[k][m] for all k, m: R[k][m] = Rc[k] of lane m
+#pragma unroll
+  for (int k = 31; k >= 0; --k) {
+    if (k >= l) continue;
+    const double rkk = __shfl_sync(0xffffffffu, Rc[k], k);
+    double acc = (k == i) ? 1.0 : 0.0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+      if (m <= k || m >= l) continue;
+      acc -= __shfl_sync(0xffffffffu, Rc[k], m) * x[m];
+    }
+    x[k] = (rkk > 0.0 && k <= i) ? acc / rkk : 0.0;
+  }
+  if (i < l)
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < l) Rinv[k * l + i] = x[k];
 }
 
 // Q = Y Rinv (row-wise).
@@ -212,7 +297,7 @@ __global__ void __launch_bounds__(1024)
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < (nt + 31) / 32; ++w) s += red[w];
-      done = (off_tot <= 1e-30 * s) || off_tot == 0.0;
+      done = (off_tot <= 1e-26 * s) || off_tot == 0.0;
     }
     __syncthreads();
     if (done) break;
@@ -275,6 +360,209 @@ __global__ void __launch_bounds__(1024)
       }
       __syncthreads();
     }
+  }
+}
+
+// The same cyclic parallel Jacobi for n <= 64 with A and V in shared memory;
+// results are copied back to A and V in global memory.
+__global__ void __launch_bounds__(256)
+    k_jacobi_small(int n, double* __restrict__ Ag, double* __restrict__ Vg, int max_sweeps) {
+  extern __shared__ double jsm[];
+  double* A = jsm;          // n x n
+  double* V = jsm + n * n;  // n x n
+  __shared__ double cs[64];
+  __shared__ int pr[64];
+  __shared__ double red[8];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ne = (n + 1) & ~1;
+  const int np = ne / 2;
+  // (A + A')/2: a Rayleigh-Ritz matrix formed as Q'(Sigma Q) is symmetric
+  // only to rounding, and the rotations zero one triangle
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    A[e] = 0.5 * (Ag[e] + Ag[j * n + i]);
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      const double a = A[e];
+      if (e / n == e % n) dia += a * a;
+      else off += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    double offt = 0.0;
+    for (int w = 0; w < nt / 32; ++w) offt += red[w];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dia;
+    __syncthreads();
+    if (tid == 0) {
+      double diat = 0.0;
+      for (int w = 0; w < nt / 32; ++w) diat += red[w];
+      done = (offt <= 1e-26 * diat) || offt == 0.0;
+    }
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < ne - 1; ++step) {
+      if (tid < np) {
+        const int i = tid;
+        int p, q;
+        if (i == 0) {
+          p = ne - 1;
+          q = step;
+        } else {
+          p = (step + i) % (ne - 1);
+          q = (step - i + (ne - 1)) % (ne - 1);
+        }
+        if (p > q) {
+          const int tt = p;
+          p = q;
+          q = tt;
+        }
+        double c = 1.0, sn = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            sn = tt * c;
+          }
+        }
+        pr[2 * i] = p;
+        pr[2 * i + 1] = q;
+        cs[2 * i] = c;
+        cs[2 * i + 1] = sn;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * n; e += nt) {
+        const int i = e / n, k = e - (e / n) * n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double akp = A[k * n + p], akq = A[k * n + q];
+        A[k * n + p] = c * akp - sn * akq;
+        A[k * n + q] = sn * akp + c * akq;
+        const double vkp = V[k * n + p], vkq = V[k * n + q];
+        V[k * n + p] = c * vkp - sn * vkq;
+        V[k * n + q] = sn * vkp + c * vkq;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * n; e += nt) {
+        const int i = e / n, k = e - (e / n) * n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double apk = A[p * n + k], aqk = A[q * n + k];
+        A[p * n + k] = c * apk - sn * aqk;
+        A[q * n + k] = sn * apk + c * aqk;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < n * n; e += nt) {
+    Ag[e] = A[e];
+    Vg[e] = V[e];
+  }
+}
+
+// Cyclic parallel Jacobi by one warp for n <= 32 (A, V in shared memory,
+// warp-synchronous: no block barriers).  Same rotations and pair schedule as
+// the block version.
+__global__ void __launch_bounds__(32)
+    k_jacobi_warp(int n, double* __restrict__ Ag, double* __restrict__ Vg, int max_sweeps) {
+  __shared__ double A[32 * 32];
+  __shared__ double V[32 * 32];
+  __shared__ double cs[32];
+  __shared__ int pr[32];
+  const int lane = threadIdx.x;
+  const int ne = (n + 1) & ~1;
+  const int np = ne / 2;
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e - (e / n) * n;
+    A[e] = 0.5 * (Ag[e] + Ag[j * n + i]);
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = lane; e < n * n; e += 32) {
+      const double a = A[e];
+      if (e / n == e % n) dia += a * a;
+      else off += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off <= 1e-26 * dia || off == 0.0) break;
+    for (int step = 0; step < ne - 1; ++step) {
+      if (lane < np) {
+        const int i = lane;
+        int p, q;
+        if (i == 0) {
+          p = ne - 1;
+          q = step;
+        } else {
+          p = (step + i) % (ne - 1);
+          q = (step - i + (ne - 1)) % (ne - 1);
+        }
+        if (p > q) {
+          const int tt = p;
+          p = q;
+          q = tt;
+        }
+        double c = 1.0, sn = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            sn = tt * c;
+          }
+        }
+        pr[2 * i] = p;
+        pr[2 * i + 1] = q;
+        cs[2 * i] = c;
+        cs[2 * i + 1] = sn;
+      }
+      __syncwarp();
+      for (int e = lane; e < np * n; e += 32) {
+        const int i = e / n, k = e - (e / n) * n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double akp = A[k * n + p], akq = A[k * n + q];
+        A[k * n + p] = c * akp - sn * akq;
+        A[k * n + q] = sn * akp + c * akq;
+        const double vkp = V[k * n + p], vkq = V[k * n + q];
+        V[k * n + p] = c * vkp - sn * vkq;
+        V[k * n + q] = sn * vkp + c * vkq;
+      }
+      __syncwarp();
+      for (int e = lane; e < np * n; e += 32) {
+        const int i = e / n, k = e - (e / n) * n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double apk = A[p * n + k], aqk = A[q * n + k];
+        A[p * n + k] = c * apk - sn * aqk;
+        A[q * n + k] = sn * apk + c * aqk;
+      }
+      __syncwarp();
+    }
+  }
+  for (int e = lane; e < n * n; e += 32) {
+    Ag[e] = A[e];
+    Vg[e] = V[e];
   }
 }
 
@@ -366,12 +654,14 @@ __global__ void k_finish(int P, int n, int k, double dv, const double* __restric
 template <typename TS>
 fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, TS* Y) {
   const int nb8 = (P + 7) / 8;
+  const int ksplit = P >= 2048 ? 8 : 1;
+  cudaMemsetAsync(Y, 0, sizeof(TS) * (size_t)P * l, ctx->stream);
   if (l <= 8) {
-    k_proj<TS, TS, 8, 4><<<(nb8 + 3) / 4, 256, 0, ctx->stream>>>(P, l, S, X, Y);
+    k_proj<TS, TS, 8, 4><<<dim3((nb8 + 3) / 4, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else if (l <= 24) {
-    k_proj<TS, TS, 24, 2><<<(nb8 + 1) / 2, 256, 0, ctx->stream>>>(P, l, S, X, Y);
+    k_proj<TS, TS, 24, 2><<<dim3((nb8 + 1) / 2, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else if (l <= 64) {
-    k_proj<TS, TS, 64, 1><<<nb8, 256, 0, ctx->stream>>>(P, l, S, X, Y);
+    k_proj<TS, TS, 64, 1><<<dim3(nb8, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else {
     return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection built for l <= 64");
   }
@@ -387,7 +677,10 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, doub
     cudaMemsetAsync(G, 0, sizeof(double) * l * l, ctx->stream);
     k_cross_gram<TS><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, src, src, G);
     FPCA_LAUNCHED(ctx, "gram");
-    k_chol_inv<<<1, 32, 0, ctx->stream>>>(l, G, Rinv, work);
+    if (l <= 32)
+      k_chol_inv_warp<<<1, 32, 0, ctx->stream>>>(l, G, Rinv);
+    else
+      k_chol_inv<<<1, 64, 0, ctx->stream>>>(l, G, Rinv, work);
     FPCA_LAUNCHED(ctx, "chol_inv");
     k_apply_rinv<TS><<<(P + 127) / 128, 128, sizeof(double) * l * l, ctx->stream>>>(P, l, src, Rinv, Q);
     FPCA_LAUNCHED(ctx, "apply_rinv");
@@ -470,7 +763,17 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   cudaMemsetAsync(A, 0, sizeof(double) * l * l, ctx->stream);
   k_cross_gram<TS><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, Q, Z, A);
   FPCA_LAUNCHED(ctx, "ritz_gram");
-  k_jacobi<<<1, 1024, 0, ctx->stream>>>(l, A, V, cs, pairs, 60);
+  if (l <= 32) {
+    k_jacobi_warp<<<1, 32, 0, ctx->stream>>>(l, A, V, 60);
+  } else {
+    static bool jattr = false;
+    if (!jattr) {
+      cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(2 * 64 * 64 * sizeof(double)));
+      jattr = true;
+    }
+    k_jacobi_small<<<1, 256, 2 * (size_t)l * l * sizeof(double), ctx->stream>>>(l, A, V, 60);
+  }
   FPCA_LAUNCHED(ctx, "jacobi");
   k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, A, order);
   FPCA_LAUNCHED(ctx, "eig_order");

@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "fpca_internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -129,18 +130,25 @@ __device__ __forceinline__ double fit_point(T (&A)[D][D], T (&r)[D], double none
     st = FPCA_PT_OK;
     return b;
   } else {
-    double Ad[D][D], rd[D];
+    T Ac[D][D], rc[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      rd[i] = (double)r[i];
+      rc[i] = r[i];
 #pragma unroll
-      for (int j = 0; j < D; ++j) Ad[i][j] = (double)A[i][j];
+      for (int j = 0; j < D; ++j) Ac[i][j] = A[i][j];
     }
     double ratio;
     const T b = elim_solve<D, T>(A, r, ratio);
     if (ratio >= ESCALATE_F32) {
       st = FPCA_PT_OK;
       return (double)b;
+    }
+    double Ad[D][D], rd[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      rd[i] = (double)rc[i];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Ad[i][j] = (double)Ac[i][j];
     }
     const double bd = elim_solve<D, double>(Ad, rd, ratio);
     if (ratio <= PIVOT_RTOL_F32) {
@@ -152,16 +160,95 @@ __device__ __forceinline__ double fit_point(T (&A)[D][D], T (&r)[D], double none
   }
 }
 
+// FP32 fit without FP64 arithmetic on the common path: pivot tests by
+// multiplication (pivot < thr * diagonal) and FP32 divisions; the FP64
+// elimination runs only for the rare escalated systems.
+// Status code returned when the system must be re-solved in FP64.
+constexpr uint8_t PT_ESCALATE = 255;
+
+template <int D, bool INLINE_FP64 = true>
+__device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], float nonempty,
+                                               uint8_t& st) {
+  if (!(A[0][0] > 0.f)) {
+    st = FPCA_PT_EMPTY;
+    return __int_as_float(0x7fc00000);
+  }
+  if (nonempty < (float)D) {
+    st = FPCA_PT_FALLBACK;
+    return r[0] / A[0][0];
+  }
+  float Ac[D][D], rc[D], diag[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    rc[i] = r[i];
+    diag[i] = A[i][i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Ac[i][j] = A[i][j];
+  }
+  bool escalate = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float piv = A[k][k];
+    if (!(piv >= (float)ESCALATE_F32 * diag[k])) escalate = true;
+    const float inv = piv > 0.f ? 1.f / piv : 0.f;
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const float l = A[k][i] * inv;
+#pragma unroll
+      for (int j = i; j < D; ++j) A[i][j] = fmaf(-l, A[k][j], A[i][j]);
+      r[i] = fmaf(-l, r[k], r[i]);
+    }
+  }
+  if (!escalate) {
+    float x[D];
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+      float sacc = r[k];
+#pragma unroll
+      for (int j = k + 1; j < D; ++j) sacc = fmaf(-A[k][j], x[j], sacc);
+      x[k] = sacc / A[k][k];
+    }
+    st = FPCA_PT_OK;
+    return x[0];
+  }
+  if constexpr (!INLINE_FP64) {
+    st = PT_ESCALATE;
+    return 0.f;
+  }
+  double Ad[D][D], rd[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    rd[i] = (double)rc[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Ad[i][j] = (double)Ac[i][j];
+  }
+  double ratio;
+  const double bd = elim_solve<D, double>(Ad, rd, ratio);
+  if (ratio <= PIVOT_RTOL_F32) {
+    st = FPCA_PT_FALLBACK;
+    return rc[0] / Ac[0][0];
+  }
+  st = FPCA_PT_OK;
+  return (float)bd;
+}
+
 // ---------------------------------------------------------------------------
-// mean smoother, Eq. (2.3): one thread per output node, FP64 window sums
+// mean smoother, Eq. (2.3): one warp per output node, FP64 window sums
 // ---------------------------------------------------------------------------
+// Lanes stride over the window's bins; the (d+1)(d+2)/2 entries of A, the
+// d+1 entries of r and the non-empty count are reduced across the warp and
+// lane 0 solves.
 template <int DIM>
-__global__ void k_smooth_mean(int P, TapParams tp, const double* __restrict__ tab,
-                              const int32_t* __restrict__ cnt, const double* __restrict__ w,
-                              const double* __restrict__ v, double* __restrict__ mu,
-                              uint8_t* __restrict__ status, int T0, int T1, int T2) {
+__global__ void __launch_bounds__(128)
+    k_smooth_mean(int P, TapParams tp, const double* __restrict__ tab,
+                  const int32_t* __restrict__ cnt, const double* __restrict__ w,
+                  const double* __restrict__ v, double* __restrict__ mu,
+                  uint8_t* __restrict__ status, int T0, int T1, int T2) {
   constexpr int D = DIM + 1;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int NA = D * (D + 1) / 2;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int p = warp;
   if (p >= P) return;
   int j[3] = {0, 0, 0};
   {
@@ -172,57 +259,61 @@ __global__ void k_smooth_mean(int P, TapParams tp, const double* __restrict__ ta
     }
   }
   const int taps[3] = {T0, T1, T2};
-  double A[D][D], r[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    r[a] = 0.0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) A[a][b] = 0.0;
-  }
-  double nonempty = 0.0;
-  int lo[3], hi[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = 0;
-    hi[k] = 0;
-  }
+  int lo[3] = {0, 0, 0}, len[3] = {1, 1, 1};
   for (int k = 0; k < DIM; ++k) {
     lo[k] = max(-taps[k], -j[k]);
-    hi[k] = min(taps[k], tp.m[k] - 1 - j[k]);
+    len[k] = min(taps[k], tp.m[k] - 1 - j[k]) - lo[k] + 1;
   }
-  for (int o0 = lo[0]; o0 <= hi[0]; ++o0)
-    for (int o1 = lo[1]; o1 <= hi[1]; ++o1)
-      for (int o2 = lo[2]; o2 <= hi[2]; ++o2) {
-        const int off[3] = {o0, o1, o2};
-        int b = 0;
-        double K = 1.0;
-        double u[3];
+  const int nwin = len[0] * len[1] * len[2];
+  double acc[NA + D + 1];
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-          b = b * tp.m[k] + (j[k] + off[k]);
-          const double* tk = tab + (size_t)k * TROWS * TW;
-          K *= tk[off[k] + TMAX];
-          u[k] = __ddiv_rn((double)off[k], __dmul_rn(tp.h[k], (double)tp.m[k]));
-        }
-        if (K == 0.0) continue;
-        const double kw = K * w[b], kv = K * v[b];
-        nonempty += cnt[b] > 0 ? 1.0 : 0.0;
-        double z[D];
-        z[0] = 1.0;
+  for (int a = 0; a < NA + D + 1; ++a) acc[a] = 0.0;
+  for (int e = lane; e < nwin; e += 32) {
+    int off[3];
+    off[2] = lo[2] + e % len[2];
+    off[1] = lo[1] + (e / len[2]) % len[1];
+    off[0] = lo[0] + e / (len[2] * len[1]);
+    int b = 0;
+    double K = 1.0;
+    double z[D];
+    z[0] = 1.0;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) z[k + 1] = u[k];
+    for (int k = 0; k < DIM; ++k) {
+      b = b * tp.m[k] + (j[k] + off[k]);
+      K *= tab[(size_t)k * TROWS * TW + off[k] + TMAX];
+      z[k + 1] = __ddiv_rn((double)off[k], __dmul_rn(tp.h[k], (double)tp.m[k]));
+    }
+    if (K == 0.0) continue;
+    const double kw = K * w[b], kv = K * v[b];
+    int a = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          r[a] += kv * z[a];
+    for (int r = 0; r < D; ++r)
 #pragma unroll
-          for (int c = a; c < D; ++c) A[a][c] += kw * z[a] * z[c];
-        }
+      for (int c = r; c < D; ++c) acc[a++] += kw * z[r] * z[c];
+#pragma unroll
+    for (int r = 0; r < D; ++r) acc[NA + r] += kv * z[r];
+    acc[NA + D] += cnt[b] > 0 ? 1.0 : 0.0;
+  }
+#pragma unroll
+  for (int a = 0; a < NA + D + 1; ++a)
+    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+  if (lane != 0) return;
+  double A[D][D], r[D];
+  {
+    int a = 0;
+#pragma unroll
+    for (int rr = 0; rr < D; ++rr)
+#pragma unroll
+      for (int c = rr; c < D; ++c) {
+        A[rr][c] = acc[a];
+        A[c][rr] = acc[a];
+        ++a;
       }
 #pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int c = 0; c < a; ++c) A[a][c] = A[c][a];
+    for (int rr = 0; rr < D; ++rr) r[rr] = acc[NA + rr];
+  }
   uint8_t st;
-  mu[p] = fit_point<D, double>(A, r, nonempty, st);
+  mu[p] = fit_point<D, double>(A, r, acc[NA + D], st);
   if (status) status[p] = st;
 }
 
@@ -403,6 +494,13 @@ struct Epilogue {
   const T* vf;
   const T* qf;
   double* cvacc;       // [3]: err, w_in, w_out
+  // Escalated fits (FP32 pivots below the escalation threshold) are queued
+  // here and solved in FP64 by a separate kernel: entry e holds the 21
+  // moment slots of the point in esc_slots[e*21 ..] and its (xs, xt).
+  float* esc_slots;
+  int2* esc_idx;
+  unsigned* esc_count;
+  int esc_cap;
 };
 
 constexpr int MAXL = 64;
@@ -568,6 +666,558 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// ---------------------------------------------------------------------------
+// t-side sweep + solve, register-blocked (d = 2, FP32)
+// ---------------------------------------------------------------------------
+// The 10 s-side arrays of row x_s are summed along t1 into 15 "mid" arrays
+// (array a, t1-power a1) and along t2 into the 21 moment slots; the slots
+// then feed the per-point solve.  One block handles HT rows of the t-plane:
+//   phase 1  item = (mid array, column): HT outputs down one column from a
+//            sliding window of input rows; tap weights read 4 at a time;
+//   phase 2  item = (slot, row, SEG-column segment): SEG outputs along a row
+//            of a mid array from a sliding window;
+//   phase 3  one point per thread at a time: 21 slots -> A, r -> solve.
+// Tap lists are zero-padded to a multiple of 4 (out-of-grid rows and
+// columns are zero in shared memory), so the inner loops carry no bounds
+// checks.  With COMP, every 4-tap partial is added to the running sum with
+// Kahan compensation.
+constexpr int HT = 8;     // t-plane rows per block
+constexpr int SEG = 8;    // columns per phase-2 item
+constexpr int NT2 = 256;  // threads per block
+constexpr int NMID = 15;  // mid arrays (d = 2)
+constexpr int NSL = 21;   // moment slots (d = 2)
+
+// mid array m -> (s-side array a, t1 power a1; 3 = box weights);
+// slot s -> (mid array, t2 power; 3 = box weights).  Items of one warp share
+// m (phase 1) or s (phase 2), so the constant-cache reads broadcast.
+__constant__ int8_t c_mid_array[NMID] = {0, 0, 0, 1, 1, 2, 3, 3, 4, 5, 6, 6, 7, 8, 9};
+__constant__ int8_t c_mid_pow[NMID] = {0, 1, 2, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 3};
+__constant__ int8_t c_slot_mid[NSL] = {0, 3, 6, 1, 0, 5, 8, 4, 3, 9, 7,
+                                       6, 2, 1, 0, 10, 12, 13, 11, 10, 14};
+__constant__ int8_t c_slot_pow[NSL] = {0, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0,
+                                       1, 0, 1, 2, 0, 0, 0, 0, 1, 3};
+
+struct Hs2Geom {
+  int P, R, C;
+  int Tr, Tc;        // tap half-widths (t1, t2)
+  int ntr, ntc;      // padded tap counts (multiples of 4)
+  int nrp;           // input rows held per block: HT + ntr (the window preloads one spare row)
+  int RS;            // mid row stride (odd, >= C + ntc)
+  int SC;            // slot row stride (odd, >= C)
+};
+
+template <bool COMP>
+__device__ __forceinline__ void chunk_add(float& s, float& c, float p) {
+  if constexpr (COMP) {
+    const float y = p - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  } else {
+    s += p;
+  }
+}
+
+// NO outputs along a line: out[j] = sum_{k < nt} w[k] * x[(j + k) * stride].
+// The next 4-tap chunk (inputs and weights) is loaded before the current one
+// is summed, so shared-memory latency overlaps the FMAs.
+template <int NO, bool COMP>
+__device__ __forceinline__ void slide_sum(const float* __restrict__ x, int stride,
+                                          const float4* __restrict__ w4, int nt, float (&out)[NO]) {
+  float win[NO + 4];
+#pragma unroll
+  for (int j = 0; j < NO; ++j) win[j] = x[j * stride];
+  float nxt[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) nxt[u] = x[(NO + u) * stride];
+  float4 wn = w4[0];
+  float sum[NO], cmp[NO];
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    sum[j] = 0.f;
+    cmp[j] = 0.f;
+  }
+#pragma unroll 2
+  for (int kc = 0; kc < nt; kc += 4) {
+    const float4 w = wn;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) win[NO + u] = nxt[u];
+    if (kc + 4 < nt) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) nxt[u] = x[(NO + kc + 4 + u) * stride];
+      wn = w4[(kc >> 2) + 1];
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        float p = w.x * win[j];
+        p = fmaf(w.y, win[j + 1], p);
+        p = fmaf(w.z, win[j + 2], p);
+        p = fmaf(w.w, win[j + 3], p);
+        chunk_add<true>(sum[j], cmp[j], p);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        sum[j] = fmaf(w.x, win[j], sum[j]);
+        sum[j] = fmaf(w.y, win[j + 1], sum[j]);
+        sum[j] = fmaf(w.z, win[j + 2], sum[j]);
+        sum[j] = fmaf(w.w, win[j + 3], sum[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NO; ++j) win[j] = win[j + 4];
+  }
+#pragma unroll
+  for (int j = 0; j < NO; ++j) out[j] = sum[j];
+}
+
+// weights in padded form: wp[row][k], k = 0..nt-1 <-> offset k - T (zero beyond 2T)
+__device__ __forceinline__ void load_padded_weights(const double* __restrict__ tab, int T, int nt,
+                                                    float* __restrict__ wp) {
+  for (int e = threadIdx.x; e < TROWS * nt; e += blockDim.x) {
+    const int row = e / nt, k = e - (e / nt) * nt;
+    wp[e] = k <= 2 * T ? (float)tab[row * TW + TMAX + (k - T)] : 0.f;
+  }
+}
+
+template <bool COMP, int C>
+__global__ void __launch_bounds__(NT2, 2)
+    k_hsolve2(const float* __restrict__ varr, Hs2Geom g, const double* __restrict__ tabr,
+              const double* __restrict__ tabc, const double* __restrict__ mu_raw,
+              float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep,
+              int* __restrict__ err) {
+  static_assert(C % SEG == 0 && C <= 64, "t-plane width");
+  extern __shared__ __align__(128) unsigned char hs2[];
+  __shared__ double red[NT2 / 32];
+  __shared__ __align__(8) uint64_t tile_bar;
+  const int P = g.P, R = g.R;
+  float* wr = reinterpret_cast<float*>(hs2);          // [TROWS][ntr]
+  float* wc = wr + TROWS * g.ntr;                       // [TROWS][ntc]
+  float* mid = wc + TROWS * g.ntc;                      // [NMID][HT][RS]
+  float* in = mid + (size_t)NMID * HT * g.RS;           // [10][nrp][C]; later the slots
+  // (the sliding windows read input rows < HT + ntr = nrp and mid columns
+  //  < C + ntc <= RS, so every load stays inside these arrays)
+  float* slots = in;                                    // [NSL][HT][SC]
+  const int xs = blockIdx.y;
+  const int a0 = blockIdx.x * HT;
+  const int th = min(HT, R - a0);
+  const long long PP = (long long)P * P;
+
+  // input rows a0 - Tr .. a0 - Tr + nrp - 1 of the t-plane, zero outside [0, R):
+  // the in-grid rows of each array are one contiguous run in global memory,
+  // fetched by the TMA engine (one bulk copy per array) while the threads
+  // fill the padding rows and the weight tables.
+  const int rlo = max(0, a0 - g.Tr), rhi = min(R, a0 - g.Tr + g.nrp);
+  const int skip = rlo - (a0 - g.Tr);  // padding rows above the grid
+  const uint32_t bytes = (uint32_t)((rhi - rlo) * C * sizeof(float));
+  const uint32_t bar = ptx::smem_u32(&tile_bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(bar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && bytes > 0) {
+    ptx::mbar_arrive_expect_tx(bar, 10 * bytes);
+    for (int a = 0; a < 10; ++a)
+      ptx::bulk_load(ptx::smem_u32(in + ((size_t)a * g.nrp + skip) * C),
+                     varr + a * PP + (long long)xs * P + (long long)rlo * C, bytes, bar);
+  }
+  load_padded_weights(tabr, g.Tr, g.ntr, wr);
+  load_padded_weights(tabc, g.Tc, g.ntc, wc);
+  {
+    constexpr int C4 = C / 4;
+    const int padrows = g.nrp - (rhi - rlo);
+    for (int e = threadIdx.x; e < 10 * padrows * C4; e += NT2) {
+      const int a = e / (padrows * C4);
+      const int rem = e - a * padrows * C4;
+      const int pr = rem / C4, c4 = rem % C4;
+      const int r = pr < skip ? pr : (rhi - rlo) + pr;  // above, then below the copied rows
+      *reinterpret_cast<float4*>(in + ((size_t)a * g.nrp + r) * C + 4 * c4) =
+          make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // zero the column padding of the mid rows
+    const int padw = g.RS - C;
+    for (int e = threadIdx.x; e < NMID * HT * padw; e += NT2) {
+      const int line = e / padw, k = e - (e / padw) * padw;
+      const int cp = k < g.Tc ? k : C + k;
+      mid[(size_t)line * g.RS + cp] = 0.f;
+    }
+  }
+  // bounded wait for the copies; the block leaves together if any thread gave up
+  const bool landed = bytes == 0 || ptx::mbar_wait(bar, 0, err);
+  if (__syncthreads_or(!landed)) return;
+
+  // phase 1: sums across t-plane rows
+  for (int it = threadIdx.x; it < NMID * C; it += NT2) {
+    const int m = it / C, c = it - (it / C) * C;
+    const int a = c_mid_array[m], pw = c_mid_pow[m];
+    float out[HT];
+    slide_sum<HT, COMP>(in + (size_t)a * g.nrp * C + c, C,
+                        reinterpret_cast<const float4*>(wr + pw * g.ntr), g.ntr, out);
+    float* dst = mid + (size_t)m * HT * g.RS + g.Tc + c;
+#pragma unroll
+    for (int j = 0; j < HT; ++j) dst[j * g.RS] = out[j];
+  }
+  __syncthreads();
+
+  // phase 2: sums along t-plane rows into the moment slots (aliasing `in`).
+  // A warp covers 8 rows x 4 segments of one slot: with odd row strides its
+  // loads and stores fall in 32 distinct banks.
+  constexpr int NSEG = C / SEG;
+  constexpr int SLO = NSEG < 4 ? NSEG : 4;
+  for (int it = threadIdx.x; it < NSL * HT * NSEG; it += NT2) {
+    const int s = it / (HT * NSEG);
+    const int rem = it % (HT * NSEG);
+    const int sg = (rem % SLO) + SLO * (rem / (SLO * HT));
+    const int i = (rem / SLO) % HT;
+    const int m = c_slot_mid[s], pw = c_slot_pow[s];
+    float out[SEG];
+    slide_sum<SEG, COMP>(mid + ((size_t)m * HT + i) * g.RS + sg * SEG, 1,
+                         reinterpret_cast<const float4*>(wc + pw * g.ntc), g.ntc, out);
+    float* dst = slots + ((size_t)s * HT + i) * g.SC + sg * SEG;
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) dst[j] = out[j];
+  }
+  __syncthreads();
+
+  // phase 3: per-point solve, write, epilogue terms (FP32; FP64 only for
+  // escalated systems and for the block sums of the CV terms)
+  float cv_err = 0.f, cv_in = 0.f, cv_out = 0.f;
+  constexpr int PPT3 = (HT * C + NT2 - 1) / NT2;
+  float gval[PPT3];
+  int xts[PPT3];
+#pragma unroll
+  for (int j = 0; j < PPT3; ++j) {
+    const int e = threadIdx.x + j * NT2;
+    gval[j] = 0.f;
+    xts[j] = -1;
+    if (e >= th * C) continue;
+    const int i = e / C, c = e % C;
+    const float* sl = slots + (size_t)i * g.SC + c;
+    float A[5][5], rv[5];
+#pragma unroll
+    for (int i2 = 0; i2 < 5; ++i2) {
+      rv[i2] = sl[(size_t)rslot(2, i2) * HT * g.SC];
+#pragma unroll
+      for (int j2 = i2; j2 < 5; ++j2) {
+        A[i2][j2] = sl[(size_t)aslot(2, i2, j2) * HT * g.SC];
+        A[j2][i2] = A[i2][j2];
+      }
+    }
+    const float cnt = sl[(size_t)(NSL - 1) * HT * g.SC];
+    uint8_t st;
+    float gv = fit_point_f32<5, false>(A, rv, cnt + 0.25f, st);
+    const int xt = (a0 + i) * C + c;
+    if (st == PT_ESCALATE) {
+      const unsigned slot = ep.esc_count ? atomicAdd(ep.esc_count, 1u) : 0xffffffffu;
+      if (slot < (unsigned)ep.esc_cap) {
+        float* dst = ep.esc_slots + (size_t)slot * NSL;
+        for (int q = 0; q < NSL; ++q) dst[q] = sl[(size_t)q * HT * g.SC];
+        ep.esc_idx[slot] = make_int2(xs, xt);
+        continue;  // the FP64 kernel writes this point and its epilogue terms
+      }
+      // queue full: solve here
+      float A2[5][5], r2[5];
+#pragma unroll
+      for (int i2 = 0; i2 < 5; ++i2) {
+        r2[i2] = sl[(size_t)rslot(2, i2) * HT * g.SC];
+#pragma unroll
+        for (int j2 = i2; j2 < 5; ++j2) {
+          A2[i2][j2] = sl[(size_t)aslot(2, i2, j2) * HT * g.SC];
+          A2[j2][i2] = A2[i2][j2];
+        }
+      }
+      gv = fit_point_f32<5, true>(A2, r2, cnt + 0.25f, st);
+    }
+    if (mu_raw && st != FPCA_PT_EMPTY) gv -= (float)(mu_raw[xs] * mu_raw[xt]);
+    const long long o = (long long)xs * P + xt;
+    if (gamma) gamma[o] = gv;
+    if (status) status[o] = st;
+    xts[j] = xt;
+    gval[j] = st == FPCA_PT_EMPTY ? 0.f : gv;
+    if (ep.cvacc) {
+      const float wf = ep.wf[o];
+      if (st == FPCA_PT_EMPTY) {
+        cv_out += wf;
+      } else {
+        cv_err += ep.qf[o] - 2.f * gv * ep.vf[o] + gv * gv * wf;
+        cv_in += wf;
+      }
+    }
+  }
+  if (ep.cvacc) {
+    const double s0 = block_sum<NT2>((double)cv_err, red);
+    const double s1 = block_sum<NT2>((double)cv_in, red);
+    const double s2 = block_sum<NT2>((double)cv_out, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(ep.cvacc + 0, s0);
+      atomicAdd(ep.cvacc + 1, s1);
+      atomicAdd(ep.cvacc + 2, s2);
+    }
+  }
+  if (ep.y) {
+    for (int c = 0; c < ep.l; ++c) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int j = 0; j < PPT3; ++j)
+        if (xts[j] >= 0) sacc = fmaf(gval[j], ep.omega[(long long)xts[j] * ep.l + c], sacc);
+      const double tot = block_sum<NT2>((double)sacc, red);
+      if (threadIdx.x == 0) atomicAdd(ep.y + (long long)xs * ep.l + c, (float)tot);
+    }
+  }
+}
+
+// NO outputs x NP powers along a line from one sliding window:
+// out[p][j] = sum_{k < nt} w_p[k] * x[(j + k) * stride].
+template <int NO, int NP, bool COMP>
+__device__ __forceinline__ void slide_sum_multi(const float* __restrict__ x, int stride,
+                                                const float4* const (&w4)[NP], int nt,
+                                                float (&out)[NP][NO]) {
+  float win[NO + 4];
+#pragma unroll
+  for (int j = 0; j < NO; ++j) win[j] = x[j * stride];
+  float nxt[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) nxt[u] = x[(NO + u) * stride];
+  float sum[NP][NO], cmp[NP][NO];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      sum[q][j] = 0.f;
+      cmp[q][j] = 0.f;
+    }
+#pragma unroll 2
+  for (int kc = 0; kc < nt; kc += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) win[NO + u] = nxt[u];
+    if (kc + 4 < nt) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) nxt[u] = x[(NO + kc + 4 + u) * stride];
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float4 w = w4[q][kc >> 2];
+      if constexpr (COMP) {
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          float pp = w.x * win[j];
+          pp = fmaf(w.y, win[j + 1], pp);
+          pp = fmaf(w.z, win[j + 2], pp);
+          pp = fmaf(w.w, win[j + 3], pp);
+          chunk_add<true>(sum[q][j], cmp[q][j], pp);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          sum[q][j] = fmaf(w.x, win[j], sum[q][j]);
+          sum[q][j] = fmaf(w.y, win[j + 1], sum[q][j]);
+          sum[q][j] = fmaf(w.z, win[j + 2], sum[q][j]);
+          sum[q][j] = fmaf(w.w, win[j + 3], sum[q][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NO; ++j) win[j] = win[j + 4];
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) out[q][j] = sum[q][j];
+}
+
+// s-side pass (FP32): one block = one line (Ma rows along the pass axis) x
+// 128 columns of one input array; rows padded with zeros above and below.
+constexpr int VROWS = 8;  // outputs per sliding window
+template <int NP, bool COMP>
+__device__ __forceinline__ void vpass2_line(const VJob& jb, const float* tile, const float* wp,
+                                            int ntp, int Ma, int stride, long long base, int P,
+                                            int col) {
+  const float4* w4[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) w4[q] = reinterpret_cast<const float4*>(wp + jb.row[q] * ntp);
+  for (int x0 = 0; x0 < Ma; x0 += VROWS) {
+    float out[NP][VROWS];
+    slide_sum_multi<VROWS, NP, COMP>(tile + (size_t)x0 * VCOLS + threadIdx.x, VCOLS, w4, ntp, out);
+#pragma unroll
+    for (int j = 0; j < VROWS; ++j) {
+      const int x = x0 + j;
+      if (x < Ma) {
+        const long long o = (base + (long long)x * stride) * P + col;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) static_cast<float*>(jb.out[q])[o] = out[q][j];
+      }
+    }
+  }
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(VCOLS)
+    k_vpass2(VJobs jobs, int P, int Ma, int stride, int taps, int ntp,
+             const double* __restrict__ tab, int bulk, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char vsm2[];
+  __shared__ __align__(8) uint64_t vbar;
+  float* wp = reinterpret_cast<float*>(vsm2);  // [TROWS][ntp]
+  float* tile = wp + TROWS * ntp;              // [Ma + ntp + VROWS][VCOLS], row r <-> x = r - taps
+  const int nrow = ((Ma + VROWS - 1) / VROWS) * VROWS + ntp;
+  float* subt = tile + (size_t)nrow * VCOLS;   // [Ma][VCOLS] when a job subtracts a fold
+  const VJob& jb = jobs.j[blockIdx.z];
+  const int col0 = blockIdx.x * VCOLS;
+  const int col = col0 + threadIdx.x;
+  const int L = blockIdx.y;
+  const long long base = (long long)(L / stride) * Ma * stride + (L % stride);
+  if (bulk) {
+    // one bulk copy per tile row (and per fold row), all on one mbarrier
+    const int ncols = min(VCOLS, P - col0);
+    const uint32_t rbytes = (uint32_t)ncols * 4u;
+    const uint32_t bar = ptx::smem_u32(&vbar);
+    if (threadIdx.x == 0) {
+      ptx::mbar_init(bar, 1);
+      ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const int nsrc = jb.sub ? 2 : 1;
+    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(bar, rbytes * (uint32_t)(Ma * nsrc));
+    __syncwarp();
+    if (threadIdx.x < 32) {
+      for (int x = threadIdx.x; x < Ma; x += 32) {
+        const long long e = (base + (long long)x * stride) * P + col0;
+        ptx::bulk_load(ptx::smem_u32(tile + (size_t)(x + taps) * VCOLS),
+                       static_cast<const float*>(jb.in) + e, rbytes, bar);
+        if (jb.sub)
+          ptx::bulk_load(ptx::smem_u32(subt + (size_t)x * VCOLS),
+                         static_cast<const float*>(jb.sub) + e, rbytes, bar);
+      }
+    }
+    load_padded_weights(tab, taps, ntp, wp);
+    for (int r = 0; r < nrow; ++r)
+      if (r < taps || r >= taps + Ma) tile[(size_t)r * VCOLS + threadIdx.x] = 0.f;
+    const bool landed = ptx::mbar_wait(bar, 0, err);
+    if (__syncthreads_or(!landed)) return;
+    if (jb.in_int || jb.sub) {
+      for (int x = 0; x < Ma; ++x) {
+        float* tv = tile + (size_t)(x + taps) * VCOLS + threadIdx.x;
+        if (jb.in_int) {
+          int c = __float_as_int(*tv);
+          if (jb.sub) c -= __float_as_int(subt[(size_t)x * VCOLS + threadIdx.x]);
+          *tv = c > 0 ? 1.f : 0.f;
+        } else {
+          *tv -= subt[(size_t)x * VCOLS + threadIdx.x];
+        }
+      }
+    }
+  } else {
+    load_padded_weights(tab, taps, ntp, wp);
+    // rows in batches of 8 so that eight global loads are in flight per thread
+    for (int r0 = 0; r0 < nrow; r0 += 8) {
+      float vals[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int x = r0 + u - taps;
+        float val = 0.f;
+        if (col < P && x >= 0 && x < Ma && r0 + u < nrow) {
+          const long long e = (base + (long long)x * stride) * P + col;
+          if (jb.in_int) {
+            int c = __ldg(static_cast<const int32_t*>(jb.in) + e);
+            if (jb.sub) c -= __ldg(static_cast<const int32_t*>(jb.sub) + e);
+            val = c > 0 ? 1.f : 0.f;
+          } else {
+            val = __ldg(static_cast<const float*>(jb.in) + e);
+            if (jb.sub) val -= __ldg(static_cast<const float*>(jb.sub) + e);
+          }
+        }
+        vals[u] = val;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (r0 + u < nrow) tile[(size_t)(r0 + u) * VCOLS + threadIdx.x] = vals[u];
+    }
+  }
+  __syncthreads();
+  if (col >= P) return;
+  if (jb.npow == 3)
+    vpass2_line<3, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+  else if (jb.npow == 2)
+    vpass2_line<2, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+  else
+    vpass2_line<1, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+}
+
+size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
+  const int nrow = ((Ma + VROWS - 1) / VROWS) * VROWS + ntp;
+  return sizeof(float) * ((size_t)TROWS * ntp + (size_t)nrow * VCOLS +
+                          (with_sub ? (size_t)Ma * VCOLS : 0));
+}
+
+// FP64 fits of the queued (escalated) points: one thread per point, so the
+// slow FP64 pipe runs full warps; writes Gamma_hat, status and the epilogue
+// terms the t-side kernel skipped.
+__global__ void __launch_bounds__(256)
+    k_escalated_f64(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
+                    const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,
+                    float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep) {
+  const unsigned n = min(*esc_count, (unsigned)cap);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const float* sl = esc_slots + (size_t)e * NSL;
+    const int2 id = esc_idx[e];
+    double A[5][5], r[5];
+#pragma unroll
+    for (int i2 = 0; i2 < 5; ++i2) {
+      r[i2] = (double)sl[rslot(2, i2)];
+#pragma unroll
+      for (int j2 = i2; j2 < 5; ++j2) {
+        A[i2][j2] = (double)sl[aslot(2, i2, j2)];
+        A[j2][i2] = A[i2][j2];
+      }
+    }
+    const double lc = r[0] / A[0][0];
+    double ratio;
+    double g = elim_solve<5, double>(A, r, ratio);
+    uint8_t st = FPCA_PT_OK;
+    if (ratio <= PIVOT_RTOL_F32) {
+      st = FPCA_PT_FALLBACK;
+      g = lc;
+    }
+    if (mu_raw) g -= mu_raw[id.x] * mu_raw[id.y];
+    const long long o = (long long)id.x * P + id.y;
+    const float gv = (float)g;
+    if (gamma) gamma[o] = gv;
+    if (status) status[o] = st;
+    if (ep.cvacc) {
+      const double wf = (double)ep.wf[o];
+      atomicAdd(ep.cvacc + 0, (double)ep.qf[o] - 2.0 * g * (double)ep.vf[o] + g * g * wf);
+      atomicAdd(ep.cvacc + 1, wf);
+    }
+    if (ep.y)
+      for (int c = 0; c < ep.l; ++c)
+        atomicAdd(ep.y + (long long)id.x * ep.l + c, gv * ep.omega[(long long)id.y * ep.l + c]);
+  }
+}
+
+// Geometry of k_hsolve2 for a d = 2 grid and tap half-widths (Tr on t1, Tc on t2).
+Hs2Geom hs2_geometry(int P, int M1, int M2, int Tr, int Tc) {
+  Hs2Geom g{};
+  g.P = P;
+  g.R = M1;
+  g.C = M2;
+  g.Tr = Tr;
+  g.Tc = Tc;
+  g.ntr = ((2 * Tr + 1) + 3) / 4 * 4;
+  g.ntc = ((2 * Tc + 1) + 3) / 4 * 4;
+  g.nrp = HT + g.ntr;
+  g.RS = (M2 + g.ntc) | 1;
+  g.SC = M2 | 1;
+  return g;
+}
+
+size_t hs2_smem(const Hs2Geom& g) {
+  const size_t in_f = (size_t)10 * g.nrp * g.C;
+  const size_t slot_f = (size_t)NSL * HT * g.SC;
+  return sizeof(float) * ((size_t)TROWS * (g.ntr + g.ntc) + (size_t)NMID * HT * g.RS +
+                          (in_f > slot_f ? in_f : slot_f));
+}
+
 // sum of fold slices: out[e] = sum_f in[f][e]
 template <typename T>
 __global__ void k_pool_folds(int F, long long PP, const T* __restrict__ in, T* __restrict__ out) {
@@ -601,6 +1251,49 @@ __global__ void k_cv_finish(int nh, int F, const double* __restrict__ acc, doubl
                                                        : err / win;
 }
 
+template <bool COMP, int C>
+void launch_hsolve2(fpca_ctx* ctx, dim3 grid, size_t smem, const float* varr, const Hs2Geom& g,
+                    const double* tabr, const double* tabc, const double* mu_raw, float* gamma,
+                    uint8_t* status, const Epilogue<float>& ep) {
+  cudaFuncSetAttribute(k_hsolve2<COMP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_hsolve2<COMP, C><<<grid, NT2, smem, ctx->stream>>>(varr, g, tabr, tabc, mu_raw, gamma, status,
+                                                       ep, ctx->d_err);
+}
+
+// Launches one s-side pass: njobs input arrays, lines of Ma rows at row
+// stride `stride`, `lines` lines.  FP32 uses the sliding-window kernel.
+template <typename T, bool COMP>
+bool launch_vpass(fpca_ctx* ctx, const VJobs& jobs, int njobs, int P, int Ma, int stride, int lines,
+                  int taps, const double* tab) {
+  const dim3 grid((P + VCOLS - 1) / VCOLS, lines, njobs);
+  if constexpr (sizeof(T) == 4) {
+    const int ntp = ((2 * taps + 1) + 3) / 4 * 4;
+    bool with_sub = false;
+    for (int j = 0; j < njobs; ++j) with_sub = with_sub || jobs.j[j].sub != nullptr;
+    const size_t sm = vpass2_smem(Ma, ntp, with_sub);
+    // bulk row copies need 16-byte aligned rows: P a multiple of 4
+    const int bulk = (P % 4 == 0) ? 1 : 0;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_vpass2<COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vpass2_smem(64, 128, true));
+      attr = true;
+    }
+    k_vpass2<COMP><<<grid, VCOLS, sm, ctx->stream>>>(jobs, P, Ma, stride, taps, ntp, tab, bulk,
+                                                     ctx->d_err);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_vpass<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(T) * (TROWS * TW + (size_t)64 * VCOLS)));
+      attr = true;
+    }
+    k_vpass<T, COMP><<<grid, VCOLS, sizeof(T) * (TROWS * TW + (size_t)Ma * VCOLS), ctx->stream>>>(
+        jobs, P, Ma, stride, taps, tab);
+  }
+  return true;
+}
+
 // One smoothing pass of the P x P bins (optionally train = pooled - sub_*).
 template <typename T, bool COMP>
 fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const T* w,
@@ -611,13 +1304,6 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
   const int P = grid_P(g);
   const long long PP = (long long)P * P;
   const int Tax[2] = {host_taps(h[0], g->m[0]), d > 1 ? host_taps(h[1], g->m[1]) : 0};
-  static bool vattr = false;
-  if (!vattr) {
-    cudaFuncSetAttribute(k_vpass<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (TROWS * TW + (size_t)64 * VCOLS)));
-    vattr = true;
-  }
-  const dim3 vblk(VCOLS);
   auto tabk = [&](int k) { return tab + (size_t)k * TROWS * TW; };
   if (d == 2) {
     const int M1 = g->m[0], M2 = g->m[1];
@@ -626,9 +1312,8 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     j1.j[0] = VJob{w, sub_w, 0, 3, {0, 1, 2}, {mids + 0 * PP, mids + 1 * PP, mids + 2 * PP}};
     j1.j[1] = VJob{v, sub_v, 0, 2, {0, 1, 0}, {mids + 3 * PP, mids + 4 * PP, nullptr}};
     j1.j[2] = VJob{cnt, sub_cnt, 1, 1, {3, 0, 0}, {mids + 5 * PP, nullptr, nullptr}};
-    k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, M1, 3), vblk,
-                       sizeof(T) * (TROWS * TW + (size_t)M2 * VCOLS), ctx->stream>>>(
-        j1, P, M2, 1, Tax[1], tabk(1));
+    if (!launch_vpass<T, COMP>(ctx, j1, 3, P, M2, 1, M1, Tax[1], tabk(1)))
+      return fpca_check_launch(ctx, "cov_vpass_s2");
     FPCA_LAUNCHED(ctx, "cov_vpass_s2");
     // pass along s1 (axis 0): rows L + a*M2
     VJobs j2{};
@@ -639,11 +1324,36 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     j2.j[3] = VJob{mids + 3 * PP, nullptr, 0, 2, {0, 1, 0}, {varr + 6 * PP, varr + 7 * PP, nullptr}};
     j2.j[4] = VJob{mids + 4 * PP, nullptr, 0, 1, {0, 0, 0}, {varr + 8 * PP, nullptr, nullptr}};
     j2.j[5] = VJob{mids + 5 * PP, nullptr, 0, 1, {3, 0, 0}, {varr + 9 * PP, nullptr, nullptr}};
-    k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, M2, 6), vblk,
-                       sizeof(T) * (TROWS * TW + (size_t)M1 * VCOLS), ctx->stream>>>(
-        j2, P, M1, M2, Tax[0], tabk(0));
+    if (!launch_vpass<T, COMP>(ctx, j2, 6, P, M1, M2, M2, Tax[0], tabk(0)))
+      return fpca_check_launch(ctx, "cov_vpass_s1");
     FPCA_LAUNCHED(ctx, "cov_vpass_s1");
     // t-side + solve
+    if constexpr (sizeof(T) == 4) {
+      if (M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) {
+        const Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
+        const size_t sm2 = hs2_smem(hg);
+        if (sm2 <= ctx->smem_optin) {
+          const dim3 grid((M1 + HT - 1) / HT, P);
+          const float* va = reinterpret_cast<const float*>(varr);
+          float* gm = reinterpret_cast<float*>(gamma);
+          const Epilogue<float>& ef = *reinterpret_cast<const Epilogue<float>*>(&ep);
+          if (ef.esc_count) cudaMemsetAsync(ef.esc_count, 0, sizeof(unsigned), ctx->stream);
+          switch (M2) {
+            case 8: launch_hsolve2<COMP, 8>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
+            case 16: launch_hsolve2<COMP, 16>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
+            case 32: launch_hsolve2<COMP, 32>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
+            default: launch_hsolve2<COMP, 64>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
+          }
+          FPCA_LAUNCHED(ctx, "cov_hpass_solve");
+          if (ef.esc_count) {
+            k_escalated_f64<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(
+                P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef);
+            FPCA_LAUNCHED(ctx, "cov_escalated_f64");
+          }
+          return FPCA_OK;
+        }
+      }
+    }
     constexpr int NT = 512, PPT = 2;
     const int R = M1, C = M2;
     const int TH = std::min(R, (NT * PPT) / C);
@@ -666,9 +1376,8 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
   j1.j[0] = VJob{w, sub_w, 0, 3, {0, 1, 2}, {varr + 0 * PP, varr + 1 * PP, varr + 2 * PP}};
   j1.j[1] = VJob{v, sub_v, 0, 2, {0, 1, 0}, {varr + 3 * PP, varr + 4 * PP, nullptr}};
   j1.j[2] = VJob{cnt, sub_cnt, 1, 1, {3, 0, 0}, {varr + 5 * PP, nullptr, nullptr}};
-  k_vpass<T, COMP><<<dim3((P + VCOLS - 1) / VCOLS, 1, 3), vblk,
-                     sizeof(T) * (TROWS * TW + (size_t)M1 * VCOLS), ctx->stream>>>(
-      j1, P, M1, 1, Tax[0], tabk(0));
+  if (!launch_vpass<T, COMP>(ctx, j1, 3, P, M1, 1, 1, Tax[0], tabk(0)))
+    return fpca_check_launch(ctx, "cov_vpass_s1");
   FPCA_LAUNCHED(ctx, "cov_vpass_s1");
   constexpr int NT = 128, PPT = 1;
   if (M1 > NT * PPT) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "d = 1 needs m <= 128");
@@ -690,10 +1399,14 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
   const long long PP = (long long)P * P;
   const int F = bins->nfold > 0 ? bins->nfold : 1;
   const int nmid = d == 2 ? 6 : 0;
+  // queue of escalated FP32 fits (d = 2 FP32 kernel): up to 2^21 points
+  const int esc_cap = (sizeof(T) == 4 && d == 2) ? (int)std::min<long long>(PP, 1ll << 21) : 0;
   const size_t need = WsCarve::round(sizeof(double) * 3 * TROWS * TW) +
                       WsCarve::round(sizeof(T) * PP * (size_t)(nmid + narr(d))) +
                       (F > 1 ? WsCarve::round(sizeof(T) * PP) * 2 + WsCarve::round(4 * PP) : 0) +
-                      WsCarve::round(sizeof(double) * 3 * (size_t)nh * F) + 4096;
+                      WsCarve::round(sizeof(double) * 3 * (size_t)nh * F) +
+                      WsCarve::round(sizeof(float) * 21 * (size_t)esc_cap) +
+                      WsCarve::round(sizeof(int2) * (size_t)esc_cap) + 8192;
   void* ws = fpca_workspace(ctx, need);
   if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
   WsCarve carve(ws);
@@ -701,6 +1414,17 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
   T* mids = carve.take<T>((size_t)PP * nmid);
   T* varr = carve.take<T>((size_t)PP * narr(d));
   double* cvacc = carve.take<double>((size_t)3 * nh * F);
+  float* esc_slots = carve.take<float>((size_t)21 * esc_cap);
+  int2* esc_idx = carve.take<int2>((size_t)esc_cap);
+  unsigned* esc_count = carve.take<unsigned>(1);
+  auto with_queue = [&](Epilogue<T>& ep) {
+    if (esc_cap > 0) {
+      ep.esc_slots = reinterpret_cast<float*>(esc_slots);
+      ep.esc_idx = esc_idx;
+      ep.esc_count = esc_count;
+      ep.esc_cap = esc_cap;
+    }
+  };
   const T* w = static_cast<const T*>(bins->w);
   const T* v = static_cast<const T*>(bins->v);
   const int32_t* cnt = bins->cnt;
@@ -734,6 +1458,7 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
     // the fit on all bins: Gamma_hat, status, projection
     if (gamma || status || y) {
       Epilogue<T> ep{};
+      with_queue(ep);
       if (y) {
         ep.omega = omega;
         ep.l = l;
@@ -752,6 +1477,7 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
       const T* fq = static_cast<const T*>(bins->q);
       for (int f = 0; f < F; ++f) {
         Epilogue<T> ep{};
+        with_queue(ep);
         ep.wf = fw + (size_t)f * PP;
         ep.vf = fv + (size_t)f * PP;
         ep.qf = fq + (size_t)f * PP;
@@ -792,7 +1518,7 @@ fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t*
   const int T0 = host_taps(tp.h[0], tp.m[0]);
   const int T1 = g->d > 1 ? host_taps(tp.h[1], tp.m[1]) : 0;
   const int T2 = g->d > 2 ? host_taps(tp.h[2], tp.m[2]) : 0;
-  const int nb = (P + 127) / 128;
+  const int nb = (P + 3) / 4;  // 4 warps per block, one warp per node
   if (g->d == 1)
     k_smooth_mean<1><<<nb, 128, 0, ctx->stream>>>(P, tp, tab, cnt, w, v, mu, status, T0, T1, T2);
   else if (g->d == 2)

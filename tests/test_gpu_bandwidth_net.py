@@ -1,0 +1,147 @@
+"""The bandwidth network and its input features on the GPU against the FP64 oracle.
+
+Tolerances: forward outputs rel <= 1e-4, gradient rel-L2 <= 1e-3 (FP32
+accumulation against FP64 at the same FP16-rounded weights), one AdamW step
+rel <= 1e-5 where the gradient is not negligible, features abs <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import fpca_synth as fs
+from oracle import features as ofeat
+from oracle import mlp as omlp
+from oracle import smoother as sm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1510_04439_gb300 import binding as B
+    return B.Context(0)
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def init_params(seed):
+    """He-style initial parameters drawn on the host (passed in as inputs)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in omlp.LAYERS:
+        parts.append(rng.standard_normal(fi * fo) * np.sqrt(2.0 / fi))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts)
+
+
+def test_param_count_matches_oracle(ctx):
+    assert ctx.bw_param_count() == omlp.param_count()
+
+
+def test_forward_and_gradient_vs_oracle(ctx):
+    rng = np.random.default_rng(5)
+    theta = init_params(1).astype(np.float32).astype(np.float64)
+    B = 37
+    X = rng.standard_normal((B, 32))
+    Y = rng.standard_normal((B, 6))
+    M = (rng.random((B, 6)) < 0.8).astype(np.uint8)
+    th = dev(theta, torch.float32)
+    out = torch.empty(B, 6, dtype=torch.float32, device=DEV)
+    ctx.bw_predict(th, dev(X, torch.float32), out)
+    ctx.sync()
+    t16 = omlp.fp16_weights(theta)
+    ref, _ = omlp.forward(t16, X.astype(np.float32).astype(np.float64))
+    assert np.allclose(host(out), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+    loss = torch.empty(1, dtype=torch.float32, device=DEV)
+    grad = torch.empty(omlp.param_count(), dtype=torch.float32, device=DEV)
+    ctx.bw_train_step(th, None, None, 0, dev(X, torch.float32), dev(Y, torch.float32), dev(M),
+                      loss=loss, grad=grad)
+    ctx.sync()
+    rl, rg = omlp.loss_and_grad(t16, X.astype(np.float32).astype(np.float64),
+                                Y.astype(np.float32).astype(np.float64), M)
+    assert abs(float(host(loss)[0]) - rl) <= 1e-4 * abs(rl)
+    g = host(grad).astype(np.float64)
+    assert np.linalg.norm(g - rg) <= 1e-3 * np.linalg.norm(rg)
+
+
+def test_adamw_step_vs_oracle(ctx):
+    rng = np.random.default_rng(6)
+    theta = init_params(2).astype(np.float32).astype(np.float64)
+    B = 64
+    X = rng.standard_normal((B, 32)).astype(np.float32)
+    Y = rng.standard_normal((B, 6)).astype(np.float32)
+    M = np.ones((B, 6), dtype=np.uint8)
+    th = dev(theta, torch.float32)
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    grad = torch.empty_like(th)
+    lr, wd = 1e-3, 1e-4
+    ctx.bw_train_step(th, m, v, 1, dev(X), dev(Y), dev(M), lr=lr, wd=wd, grad=grad)
+    ctx.sync()
+    g = host(grad).astype(np.float64)
+    ref, _, _ = omlp.adamw_step(theta, np.zeros_like(theta), np.zeros_like(theta), g, 1, lr, wd)
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert np.allclose(host(th)[big], ref[big], rtol=1e-5, atol=1e-7)
+
+
+def test_training_reduces_loss(ctx):
+    rng = np.random.default_rng(7)
+    B = 256
+    X = rng.standard_normal((B, 32)).astype(np.float32)
+    Wt = rng.standard_normal((32, 6)) * 0.3
+    Y = np.tanh(X @ Wt).astype(np.float32)
+    M = np.ones((B, 6), dtype=np.uint8)
+    th = dev(init_params(3), torch.float32)
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    loss = torch.empty(1, dtype=torch.float32, device=DEV)
+    Xd, Yd, Md = dev(X), dev(Y), dev(M)
+    first = None
+    for step in range(1, 301):
+        ctx.bw_train_step(th, m, v, step, Xd, Yd, Md, lr=1e-3, wd=1e-4, loss=loss)
+        if step == 1:
+            ctx.sync()
+            first = float(host(loss)[0])
+    ctx.sync()
+    last = float(host(loss)[0])
+    assert last < 0.05 * first
+
+
+@pytest.mark.parametrize("kind", ["dense", "sparse", "dense1d"])
+def test_features_vs_oracle(ctx, kind):
+    from paper_1510_04439_gb300 import binding as B
+    if kind == "dense":
+        D = fs.make_dense(2, (16, 16), 120, [2.0, 1.0], sigma=0.5, seed=3, domain="disk", dropout=0.2)
+    elif kind == "dense1d":
+        D = fs.make_dense(1, (48,), 90, [2.0, 1.0], sigma=0.3, mean="1d", seed=4, dropout=0.3)
+    else:
+        D = fs.make_sparse(2, (12, 12), 700, [2.0, 1.0], seed=8, nfold=0)
+    m, P = D.m, D.P
+    if kind == "sparse":
+        data = ctx.sparse(dev(D.offs), dev(D.t), dev(D.y))
+        cnt, Wm, Vm, V2m = sm.bin_mean_sparse(D.offs, D.t, D.y, m)
+        Ni = np.diff(D.offs)
+        r = sm.residuals_sparse(D.t, D.y, np.zeros(P), m)
+        C, W, V, _ = sm.bin_cov_sparse(D.offs, D.t, r, m)
+        C, W, V = C[0], W[0], V[0]
+    else:
+        data = ctx.dense(dev(D.y), dev(D.mask))
+        cnt, Wm, Vm, V2m = sm.bin_mean_dense(D.y, D.mask, m)
+        Ni = D.mask.sum(axis=1)
+        C, W, V = sm.bin_cov_dense(D.y, D.mask)
+    ref = ofeat.features(len(m), m, Ni, cnt, Wm, Vm, V2m, C, W, V)
+    feat = torch.empty(32, dtype=torch.float32, device=DEV)
+    ctx.bw_features(data, m, dev(cnt, torch.int32), dev(Wm), dev(Vm), dev(V2m), dev(C, torch.int32),
+                    dev(W), dev(V), feat)
+    ctx.sync()
+    assert np.allclose(host(feat), ref, rtol=1e-5, atol=1e-4), np.abs(host(feat) - ref).max()

@@ -233,8 +233,8 @@ def test_smooth_cov_d1(ctx, B, prec):
 
 def test_smooth_cov_affine_and_symmetry_through_abi(ctx, B):
     rng = np.random.default_rng(21)
-    m = (12, 10)
-    P = 120
+    m = (12, 16)
+    P = 192
     c = sm.centres(m)
     A = rng.random((P, P)) * (rng.random((P, P)) < 0.6)
     W = A + A.T
@@ -455,3 +455,64 @@ def test_fused_projection_matches_product(ctx, B):
     ctx.sync()
     ref = np.where(np.isnan(rG), 0.0, rG) @ om.astype(np.float32).astype(np.float64)
     assert rel_l2(host(y).astype(np.float64), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32c"])
+@pytest.mark.parametrize("m,h", [((13, 16), (0.2, 0.25)), ((20, 24), (0.3, 0.12)), ((9, 8), (0.6, 0.45))])
+def test_smooth_cov_f32_d2_ragged_tiles(ctx, B, prec, m, h):
+    """FP32 t-side kernel: t-plane rows not a multiple of the tile height, wide and narrow windows."""
+    D = fs.make_dense(2, m, 80, [2.0, 1.0, 0.5], sigma=0.3, seed=m[0] * 7 + m[1], dropout=0.2)
+    _, _, C, W, V = _oracle_cov_bins(D, (0.3, 0.3))
+    P = D.P
+    p = B.F32 if prec == "f32" else B.F32C
+    G = torch.empty(P, P, dtype=torch.float32, device=DEV)
+    st = torch.empty(P, P, dtype=torch.uint8, device=DEV)
+    ctx.smooth_cov_project(D.m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32),
+                           [h], p, gamma=G, status=st)
+    ctx.sync()
+    rG, rst = sm.smooth_cov_grid(D.m, h, C, W, V)
+    gst = host(st)
+    assert np.mean(gst == rst) > 0.999
+    ok = (rst == sm.STATUS_OK) & (gst == sm.STATUS_OK)
+    assert rel_l2(host(G).astype(np.float64)[ok], rG[ok]) <= 1e-5
+    fb = (rst == sm.STATUS_FALLBACK) & (gst == sm.STATUS_FALLBACK)
+    if fb.any():
+        assert rel_l2(host(G).astype(np.float64)[fb], rG[fb]) <= 1e-5
+
+
+@pytest.mark.slow
+def test_sparse_cv_pipeline_vs_oracle(ctx, B):
+    """Sparse workload shape (Uniform{5..20} points per subject, 5 folds) on a
+    16 x 16 bin grid: mean bins, mean fit, fold-split covariance bins and the CV
+    grid through the ABI, against the oracle end to end."""
+    from oracle import cv as ocv
+    D = fs.sparse_2d(n=2000, m=16)
+    m = D.m
+    P = D.P
+    hmu = (0.1, 0.1)
+    hs = [0.06, 0.12, 0.24]
+    offs, t, y = dev(D.offs), dev(D.t), dev(D.y)
+    data = ctx.sparse(offs, t, y)
+    cnt = torch.empty(P, dtype=torch.int32, device=DEV)
+    w, v = (torch.empty(P, dtype=torch.float64, device=DEV) for _ in range(2))
+    ctx.bin_mean(data, m, cnt, w, v)
+    mu = torch.empty(P, dtype=torch.float64, device=DEV)
+    ctx.smooth_mean(m, cnt, w, v, hmu, mu)
+    C = torch.empty(5, P, P, dtype=torch.int32, device=DEV)
+    W, V, Q = (torch.empty(5, P, P, dtype=torch.float32, device=DEV) for _ in range(3))
+    ctx.bin_cov(data, m, mu, B.F32, C, W, V, q=Q, fold=dev(D.fold), nfold=5)
+    cv = torch.empty(len(hs), dtype=torch.float64, device=DEV)
+    ctx.smooth_cov_project(m, C, W, V, [(h, h) for h in hs], B.F32, q=Q, nfold=5, cv=cv)
+    ctx.sync()
+    rc, rw, rv, _ = sm.bin_mean_sparse(D.offs, D.t, D.y, m)
+    rmu, _ = sm.smooth_mean(m, hmu, rc, rw, rv)
+    assert np.allclose(host(mu), rmu, rtol=1e-10, atol=1e-12)
+    r = sm.residuals_sparse(D.t, D.y, rmu, m)
+    rC, rW, rV, rQ = sm.bin_cov_sparse(D.offs, D.t, r, m, D.fold, 5)
+    assert np.array_equal(host(C), rC)
+    ref = np.array([ocv.cv_score(m, [h, h], rC, rW, rV, rQ) for h in hs])
+    got = host(cv)
+    assert np.array_equal(np.isfinite(got), np.isfinite(ref))
+    fin = np.isfinite(ref)
+    assert np.allclose(got[fin], ref[fin], rtol=1e-4)
+    assert np.argmin(np.where(fin, got, np.inf)) == np.argmin(np.where(fin, ref, np.inf))
