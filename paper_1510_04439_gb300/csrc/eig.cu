@@ -763,9 +763,9 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   cudaMemsetAsync(A, 0, sizeof(double) * l * l, ctx->stream);
   k_cross_gram<TS><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, Q, Z, A);
   FPCA_LAUNCHED(ctx, "ritz_gram");
-  if (l <= 32) {
-    k_jacobi_warp<<<1, 32, 0, ctx->stream>>>(l, A, V, 60);
-  } else {
+  {
+    // (the one-warp variant k_jacobi_warp measured slower on GB300: its
+    // serialised FP64 updates outweigh the saved block barriers)
     static bool jattr = false;
     if (!jattr) {
       cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
