@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU time budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the CV-grid measurement reported beside the headline")
     return ap.parse_args()
 
 
@@ -378,6 +380,38 @@ def main():
                                     "achieved": ach_u, "peak": peak, "unit": "TFLOP/s",
                                     "frac": ach_u / peak, "ms_per_launch": hu[0] / hu[1]}}
 
+    # ---- the CV bandwidth grid on the sparse workload (reported beside) ----
+    cvx = None
+    if not args.no_extras:
+        Ds = fs.sparse_2d()
+        hs = [float(h) for h in fs.cv_bandwidth_grid()]
+        Ps = Ds.P
+        sb = pipeline.alloc_sparse_cv(torch, dev, Ps, Ds.nfold, len(hs))
+        so, st_, sy, sf = (torch.from_numpy(a).to(dev) for a in (Ds.offs, Ds.t, Ds.y, Ds.fold))
+        pipeline.run_sparse_cv(ctx, Ds.m, so, st_, sy, sf, Ds.nfold, (0.1, 0.1), hs, sb)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        evs = []
+        for _ in range(3):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pipeline.run_sparse_cv(ctx, Ds.m, so, st_, sy, sf, Ds.nfold, (0.1, 0.1), hs, sb)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        prof_cv = ctx.profile_read()
+        ctx.profile(False)
+        ms_cv = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        scores = sb.scores.cpu().numpy()
+        fits = len(hs) * Ds.nfold
+        cvx = {"workload": f"sparse_2d_64x64_n{Ds.n}_5fold_16h", "ms_per_grid": ms_cv,
+               "fits": fits, "value": fits * float(Ps) * Ps / (ms_cv * 1e-3), "unit": UNIT,
+               "best_h": hs[int(np.argmin(scores))],
+               "kernels": {k: {"ms_total": v[0] / 3, "launches": v[1] // 3}
+                           for k, v in sorted(prof_cv.items(), key=lambda kv: -kv[1][0])[:6]}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npts, el = oracle_sample_rate(args.cpu_seconds)
@@ -406,6 +440,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "variant_uncompensated": variant,
+            "cv_grid": cvx,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernels": kernels,

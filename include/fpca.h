@@ -242,7 +242,7 @@ fpca_status fpca_bw_train_step(fpca_ctx* ctx, float* params, float* adam_m, floa
 /* The network's input: 32 summary numbers of one dataset (device float
  * feat[32]) from its observations (for the per-subject counts N_i), its mean
  * bins (cnt, w, v, v2 as produced by fpca_bin_mean; v2 may be NULL) and its
- * pooled covariance bins (nfold <= 1).  Features, in order: d; log n; log
+ * covariance bins (fold slices are pooled).  Features, in order: d; log n; log
  * mean N_i; std/mean N_i; log min N_i; log max N_i; log(1 + mean bin count);
  * var/mean^2 and skewness of bin counts; fraction of empty bins; log mean
  * within-bin variance v2/w - (v/w)^2; log variance of the binned mean v/w;

@@ -194,9 +194,9 @@ class Context:
     def bw_param_count(self):
         return int(self.lib.fpca_bw_param_count())
 
-    def bw_features(self, data, m, cnt, w, v, v2, ccnt, cw, cv, feat):
+    def bw_features(self, data, m, cnt, w, v, v2, ccnt, cw, cv, feat, nfold=0):
         bins = CovBins()
-        bins.nfold = 0
+        bins.nfold = int(nfold)
         bins.prec = F64 if cw.dtype.itemsize == 8 else F32
         bins.cnt, bins.w, bins.v = ccnt.data_ptr(), cw.data_ptr(), cv.data_ptr()
         bins.q = None

@@ -119,35 +119,49 @@ __global__ void k_feat_bins(int P, GridInfo gi, const int32_t* __restrict__ cnt,
   }
 }
 
+// Covariance-bin sums over the pooled fold slices (F slices of PP entries).
 template <typename T>
-__global__ void k_feat_cov(long long PP, int P, int s0, const int32_t* __restrict__ C,
+__global__ void k_feat_cov(long long PP, int P, int s0, int F, const int32_t* __restrict__ C,
                            const T* __restrict__ W, const T* __restrict__ V, double* acc) {
   __shared__ double red[9][8];
   double loc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  auto pooled = [&](long long e, double& w, double& v) {
+    w = 0.0;
+    v = 0.0;
+    for (int f = 0; f < F; ++f) {
+      w += (double)W[f * PP + e];
+      v += (double)V[f * PP + e];
+    }
+  };
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
        e += (long long)gridDim.x * blockDim.x) {
-    loc[7] += (double)C[e];
-    if (C[e] > 0) loc[8] += 1.0;
-    const double wv = (double)W[e];
+    int cc = 0;
+    for (int f = 0; f < F; ++f) cc += C[f * PP + e];
+    loc[7] += (double)cc;
+    if (cc > 0) loc[8] += 1.0;
+    double wv, vv;
+    pooled(e, wv, vv);
     if (!(wv > 0.0)) continue;
-    const double g = (double)V[e] / wv;
+    const double g = vv / wv;
     loc[0] += g;
     loc[1] += g * g;
     loc[2] += 1.0;
     const int p = (int)(e / P), q = (int)(e - (long long)p * P);
     if (p + s0 < P) {
       const long long e1 = e + (long long)s0 * P;
-      const double w1 = (double)W[e1];
+      double w1, v1;
+      pooled(e1, w1, v1);
       if (w1 > 0.0) {
-        const double dd = (double)V[e1] / w1 - g;
+        const double dd = v1 / w1 - g;
         loc[3] += dd * dd;
         loc[4] += 1.0;
       }
       if (q + s0 < P) {
         const long long e2 = e1 + s0;
-        const double w2 = (double)W[e2];
+        double w2, v2;
+        pooled(e2, w2, v2);
         if (w2 > 0.0) {
-          const double dd = (double)V[e2] / w2 - g;
+          const double dd = v2 / w2 - g;
           loc[5] += dd * dd;
           loc[6] += 1.0;
         }
@@ -263,21 +277,15 @@ extern "C" fpca_status fpca_bw_features(fpca_ctx* ctx, const fpca_data* data,
   k_feat_bins<<<(P + 255) / 256, 256, 0, ctx->stream>>>(P, gi, cnt, w, v, v2, acc);
   FPCA_LAUNCHED(ctx, "feat_bins");
   const int nb = (int)std::min<long long>((PP + 255) / 256, 4096);
-  for (int f = 0; f < F; ++f) {
-    // pooled covariance bins: the fold slices are summed by the reductions
-    // only when there is one slice; with folds, pool first
-    if (F > 1) break;
-    if (bins->prec == FPCA_F64)
-      k_feat_cov<double><<<nb, 256, 0, ctx->stream>>>(PP, P, gi.stride[0], bins->cnt,
-                                                      static_cast<const double*>(bins->w),
-                                                      static_cast<const double*>(bins->v), acc);
-    else
-      k_feat_cov<float><<<nb, 256, 0, ctx->stream>>>(PP, P, gi.stride[0], bins->cnt,
-                                                     static_cast<const float*>(bins->w),
-                                                     static_cast<const float*>(bins->v), acc);
-    FPCA_LAUNCHED(ctx, "feat_cov");
-  }
-  if (F > 1) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "features take pooled covariance bins (nfold <= 1)");
+  if (bins->prec == FPCA_F64)
+    k_feat_cov<double><<<nb, 256, 0, ctx->stream>>>(PP, P, gi.stride[0], F, bins->cnt,
+                                                    static_cast<const double*>(bins->w),
+                                                    static_cast<const double*>(bins->v), acc);
+  else
+    k_feat_cov<float><<<nb, 256, 0, ctx->stream>>>(PP, P, gi.stride[0], F, bins->cnt,
+                                                   static_cast<const float*>(bins->w),
+                                                   static_cast<const float*>(bins->v), acc);
+  FPCA_LAUNCHED(ctx, "feat_cov");
   k_feat_finish<<<1, 32, 0, ctx->stream>>>(gi, P, PP, acc, feat);
   FPCA_LAUNCHED(ctx, "feat_finish");
   return FPCA_OK;

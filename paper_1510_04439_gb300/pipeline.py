@@ -56,3 +56,39 @@ def run_dense(ctx, m, y, mask, h_mu, h_cov, k, bufs, bin_prec=B.BF16, smooth_pre
     ctx.rproj_eig(m, bufs.gamma, k, bufs.evals, bufs.evecs, bufs.fve, domain=bufs.cnt,
                   omega=omega, power_iters=power_iters, full=full)
     return bufs
+
+
+@dataclass
+class SparseCVBuffers:
+    cnt: object
+    w: object
+    v: object
+    mu: object
+    ccnt: object
+    cw: object
+    cv_: object
+    cq: object
+    scores: object
+
+
+def alloc_sparse_cv(torch, device, P, nfold, nh):
+    z = lambda *s, dt=torch.float64: torch.empty(*s, dtype=dt, device=device)  # noqa: E731
+    return SparseCVBuffers(
+        cnt=z(P, dt=torch.int32), w=z(P), v=z(P), mu=z(P),
+        ccnt=z(nfold, P, P, dt=torch.int32), cw=z(nfold, P, P, dt=torch.float32),
+        cv_=z(nfold, P, P, dt=torch.float32), cq=z(nfold, P, P, dt=torch.float32),
+        scores=z(nh))
+
+
+def run_sparse_cv(ctx, m, offs, t, y, fold, nfold, h_mu, hs, bufs, prec=B.F32C):
+    """Mean bins and fit, fold-split covariance bins, and the CV score of every
+    isotropic bandwidth in ``hs`` (one smoothing pass per bandwidth and fold)."""
+    data = ctx.sparse(offs, t, y)
+    ctx.bin_mean(data, m, bufs.cnt, bufs.w, bufs.v)
+    ctx.smooth_mean(m, bufs.cnt, bufs.w, bufs.v, h_mu, bufs.mu)
+    ctx.bin_cov(data, m, bufs.mu, B.F32, bufs.ccnt, bufs.cw, bufs.cv_, q=bufs.cq, fold=fold,
+                nfold=nfold)
+    d = len(m)
+    ctx.smooth_cov_project(m, bufs.ccnt, bufs.cw, bufs.cv_, [[h] * d for h in hs], prec,
+                           q=bufs.cq, nfold=nfold, cv=bufs.scores)
+    return bufs

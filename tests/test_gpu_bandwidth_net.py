@@ -117,7 +117,7 @@ def test_training_reduces_loss(ctx):
     assert last < 0.05 * first
 
 
-@pytest.mark.parametrize("kind", ["dense", "sparse", "dense1d"])
+@pytest.mark.parametrize("kind", ["dense", "sparse", "dense1d", "sparse_folds"])
 def test_features_vs_oracle(ctx, kind):
     from paper_1510_04439_gb300 import binding as B
     if kind == "dense":
@@ -127,6 +127,24 @@ def test_features_vs_oracle(ctx, kind):
     else:
         D = fs.make_sparse(2, (12, 12), 700, [2.0, 1.0], seed=8, nfold=0)
     m, P = D.m, D.P
+    nfold = 0
+    if kind == "sparse_folds":
+        # the fold slices are pooled by the kernel: the expected value uses their sums
+        nfold = 3
+        fold = (np.arange(D.n) % nfold).astype(np.int32)
+        data = ctx.sparse(dev(D.offs), dev(D.t), dev(D.y))
+        cnt, Wm, Vm, V2m = sm.bin_mean_sparse(D.offs, D.t, D.y, m)
+        Ni = np.diff(D.offs)
+        r = sm.residuals_sparse(D.t, D.y, np.zeros(P), m)
+        Cf, Wf, Vf, _ = sm.bin_cov_sparse(D.offs, D.t, r, m, fold=fold, nfold=nfold)
+        C, W, V = Cf.sum(0), Wf.sum(0), Vf.sum(0)
+        ref = ofeat.features(len(m), m, Ni, cnt, Wm, Vm, V2m, C, W, V)
+        feat = torch.empty(32, dtype=torch.float32, device=DEV)
+        ctx.bw_features(data, m, dev(cnt, torch.int32), dev(Wm), dev(Vm), dev(V2m),
+                        dev(Cf, torch.int32), dev(Wf), dev(Vf), feat, nfold=nfold)
+        ctx.sync()
+        assert np.allclose(host(feat), ref, rtol=1e-5, atol=1e-4), np.abs(host(feat) - ref).max()
+        return
     if kind == "sparse":
         data = ctx.sparse(dev(D.offs), dev(D.t), dev(D.y))
         cnt, Wm, Vm, V2m = sm.bin_mean_sparse(D.offs, D.t, D.y, m)
@@ -145,3 +163,36 @@ def test_features_vs_oracle(ctx, kind):
                     dev(W), dev(V), feat)
     ctx.sync()
     assert np.allclose(host(feat), ref, rtol=1e-5, atol=1e-4), np.abs(host(feat) - ref).max()
+
+
+def test_bandwidth_workflow_small(ctx):
+    """Labels, training and the proposal + check evaluation end to end on a few datasets:
+    the batched CV grid agrees with single-bandwidth CV calls, labels are the grid argmin,
+    and the evaluation rows are complete."""
+    from paper_1510_04439_gb300 import bandwidth as bw
+    lab = bw.Labeller(ctx, torch)
+    ds = bw.draw_dataset(11)
+    prep = lab.prepare(ds)
+    grid = host(lab.cv(prep, bw.HGRID))
+    for j in (0, 7, 15):
+        one = host(lab.cv(prep, [bw.HGRID[j]]))[0]
+        if np.isfinite(grid[j]):
+            assert abs(one - grid[j]) <= 1e-9 * abs(grid[j])
+        else:
+            assert not np.isfinite(one)
+    X, Y, M, best = bw.make_table(ctx, torch, [11, 12, 13, 14])
+    assert X.shape == (4, 32) and np.isfinite(X).all()
+    assert best[0] == int(np.argmin(np.where(np.isfinite(grid), grid, np.inf)))
+    for k in range(4):
+        d = int(round(X[k, 0]))
+        assert M[k, 3:3 + d].all() and not M[k, :3].any() and not M[k, 3 + d:].any()
+        assert np.allclose(Y[k, 3:3 + d], np.log(bw.HGRID[best[k]]))
+    Xs, mu, sd = bw.standardize(X)
+    th, hist = bw.train(ctx, torch, Xs, Y, M, epochs=20, batch=4)
+    assert hist[-1] < hist[0]
+    rows = bw.evaluate(ctx, torch, th, mu, sd, [21, 22])
+    assert len(rows) == 2
+    for r in rows:
+        assert bw.HGRID[0] <= r["prop_h"] <= bw.HGRID[-1]
+        if r["fallback"]:
+            assert r["final_score"] == r["grid_best"]
