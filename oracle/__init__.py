@@ -12,7 +12,9 @@ Modules
             per-point solve and status
   eigen     matrixisation and rescaling (Section 3.1, Eq. 3.1) and the random
             projection (Section 3.4)
+  block     the covariance smoother at chosen output pairs (rows, tiles) from
+            the data, for grids whose P x P bins are too large to hold
   cv        cross-validation of the covariance bandwidth (Section 3.3)
   mlp       the bandwidth-proposal network (forward, manual backward, AdamW)
 """
-from . import smoother, eigen, cv  # noqa: F401
+from . import smoother, eigen, cv, block  # noqa: F401
