@@ -71,19 +71,23 @@ def draw_dataset(seed):
 
 
 class Labeller:
-    """GPU bins, features and CV scores of datasets on one context."""
+    """GPU bins, features, CV scores and final FPCA fits of datasets on one context."""
 
     def __init__(self, ctx, torch):
         self.ctx = ctx
         self.torch = torch
         self.dev = ctx.device
 
-    def prepare(self, ds):
+    def upload(self, ds):
+        return {k: self.torch.from_numpy(ds[k]).to(self.dev) for k in ("offs", "t", "y", "fold")}
+
+    def prepare(self, ds, tensors=None, features=True):
+        """Mean bins and fit, fold-split covariance bins, and (optionally) the features."""
         torch = self.torch
         m = ds["m"]
         P = int(np.prod(m))
         bufs = pipeline.alloc_sparse_cv(torch, self.dev, P, NFOLD, len(HGRID))
-        t = {k: torch.from_numpy(ds[k]).to(self.dev) for k in ("offs", "t", "y", "fold")}
+        t = tensors if tensors is not None else self.upload(ds)
         data = self.ctx.sparse(t["offs"], t["t"], t["y"])
         v2 = torch.empty_like(bufs.w)
         self.ctx.bin_mean(data, m, bufs.cnt, bufs.w, bufs.v, v2)
@@ -91,10 +95,18 @@ class Labeller:
         self.ctx.smooth_mean(m, bufs.cnt, bufs.w, bufs.v, hmu, bufs.mu)
         self.ctx.bin_cov(data, m, bufs.mu, B.F32, bufs.ccnt, bufs.cw, bufs.cv_, q=bufs.cq,
                          fold=t["fold"], nfold=NFOLD)
-        feat = torch.empty(32, dtype=torch.float32, device=self.dev)
-        self.ctx.bw_features(data, m, bufs.cnt, bufs.w, bufs.v, v2, bufs.ccnt, bufs.cw, bufs.cv_,
-                             feat, nfold=NFOLD)
-        return dict(bufs=bufs, tensors=t, data=data, feat=feat, m=m, d=len(m))
+        prep = dict(bufs=bufs, tensors=t, data=data, m=m, d=len(m), v2=v2, feat=None)
+        if features:
+            self.features(prep)
+        return prep
+
+    def features(self, prep):
+        b = prep["bufs"]
+        feat = self.torch.empty(32, dtype=self.torch.float32, device=self.dev)
+        self.ctx.bw_features(prep["data"], prep["m"], b.cnt, b.w, b.v, prep["v2"], b.ccnt, b.cw,
+                             b.cv_, feat, nfold=NFOLD)
+        prep["feat"] = feat
+        return feat
 
     def cv(self, prep, hs):
         """CV score of each isotropic bandwidth in hs (one pass per bandwidth and fold)."""
@@ -105,6 +117,29 @@ class Labeller:
         self.ctx.smooth_cov_project(prep["m"], b.ccnt, b.cw, b.cv_, [[float(h)] * d for h in hs],
                                     B.F32C, q=b.cq, nfold=NFOLD, cv=out)
         return out
+
+    def fit(self, prep, h, k, omega):
+        """Final covariance surface at bandwidth h on the pooled bins and its top-k
+        eigenpairs by random projection (k + 10 columns, 2 power iterations)."""
+        torch = self.torch
+        b = prep["bufs"]
+        m = prep["m"]
+        P = int(np.prod(m))
+        gamma = torch.empty(P, P, dtype=torch.float32, device=self.dev)
+        self.ctx.smooth_cov_project(m, b.ccnt, b.cw, b.cv_, [[float(h)] * prep["d"]], B.F32C,
+                                    nfold=NFOLD, gamma=gamma)
+        evals = torch.empty(k, dtype=torch.float64, device=self.dev)
+        evecs = torch.empty(k, P, dtype=torch.float64, device=self.dev)   # vector j in row j
+        self.ctx.rproj_eig(m, gamma, k, evals, evecs, omega=omega, power_iters=2)
+        return evals, evecs
+
+
+def subspace_sine(a, b):
+    """Largest principal-angle sine between the column spaces of a and b."""
+    qa, _ = np.linalg.qr(a)
+    qb, _ = np.linalg.qr(b)
+    s = np.linalg.svd(qa.T @ qb, compute_uv=False)
+    return float(math.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2)))
 
 
 def make_table(ctx, torch, seeds, log_every=0):
@@ -182,52 +217,95 @@ def predict(ctx, torch, th, X):
 
 
 def evaluate(ctx, torch, th, mu, sd, seeds):
-    """Per held-out dataset: grid CV time and best score, proposal + check time
-    and score, fallback decision."""
+    """Per held-out dataset, the whole FPCA (bins, bandwidth choice, final surface and
+    top-k eigenfunctions, k = the true number of components) by both methods:
+
+      grid:    CV over the 16 bandwidths, fit at the best one;
+      learned: features -> network -> CV check at h x {0.8, 1, 1.25} -> fit at the
+               best checked bandwidth, or the grid when a neighbour beats the
+               proposal by more than 5% (fallback).
+
+    Records wall times of each stage (GPU work plus host overhead, synchronised),
+    CV scores, and the eigenfunction subspace error of both fits against the truth."""
+    import fpca_synth as fs
     lab = Labeller(ctx, torch)
     rows = []
+
+    def clock():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
     for s in seeds:
         ds = draw_dataset(int(s))
-        prep = lab.prepare(ds)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        m = ds["m"]
+        P = int(np.prod(m))
+        k = len(ds["lam"])
+        omega = torch.from_numpy(fs.gaussian_test_matrix(P, k + 10, int(s)).astype(np.float32)).to(ctx.device)
+        tens = lab.upload(ds)
+        t0 = clock()
+        prep = lab.prepare(ds, tens, features=False)
+        t1 = clock()
         grid = lab.cv(prep, HGRID).cpu().numpy()
-        t_grid = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        f = (prep["feat"].cpu().numpy()[None, :] - mu) / sd
+        t2 = clock()
+        fin = np.isfinite(grid)
+        jb = int(np.argmin(np.where(fin, grid, np.inf))) if fin.any() else len(HGRID) // 2
+        _, vec_g = lab.fit(prep, HGRID[jb], k, omega)
+        vec_g = vec_g.cpu().numpy().T
+        t3 = clock()
+        feat = lab.features(prep).cpu().numpy()
+        f = (feat[None, :] - mu) / sd
         out = predict(ctx, torch, th, f)[0]
         hp = float(np.exp(np.mean(out[3:3 + ds["d"]])))
         hp = float(np.clip(hp, HGRID[0], HGRID[-1]))
         cand = [hp * 0.8, hp, hp * 1.25]
         chk = lab.cv(prep, cand).cpu().numpy()
-        t_prop = time.perf_counter() - t0
-        fallback = bool(np.isfinite(chk[1]) and min(chk[0], chk[2]) < 0.95 * chk[1]) or \
-            not np.isfinite(chk[1])
-        fin = np.isfinite(grid)
+        t4 = clock()
+        fallback = (not np.isfinite(chk[1])) or bool(min(chk[0], chk[2]) < 0.95 * chk[1])
+        if fallback:
+            h_l = float(HGRID[jb])       # the grid scores computed above stand in for a rerun
+        else:
+            h_l = float(cand[int(np.nanargmin(np.where(np.isfinite(chk), chk, np.nan)))])
+        t5 = clock()
+        _, vec_l = lab.fit(prep, h_l, k, omega)
+        vec_l = vec_l.cpu().numpy().T
+        t6 = clock()
         best = float(np.min(grid[fin])) if fin.any() else math.inf
         prop = float(np.nanmin(np.where(np.isfinite(chk), chk, np.nan))) if np.isfinite(chk).any() \
             else math.inf
-        rows.append(dict(seed=int(s), d=ds["d"], grid_best=best,
-                         grid_h=float(HGRID[np.argmin(np.where(fin, grid, np.inf))]),
-                         prop_h=hp, prop_score=prop, t_grid=t_grid, t_prop=t_prop,
-                         fallback=fallback,
-                         # the workflow's result: the grid when the check falls back
-                         final_score=best if fallback else prop,
-                         t_final=t_prop + (t_grid if fallback else 0.0)))
+        c = fs.grid_centres(m)
+        phi = np.stack([fs.eval_fourier(sp, c) for sp in ds["specs"]], axis=1)
+        t_prep, t_cv, t_fit_g = t1 - t0, t2 - t1, t3 - t2
+        t_sel, t_fit_l = t4 - t3, t6 - t5
+        rows.append(dict(
+            seed=int(s), d=ds["d"], k=k, grid_best=best, grid_h=float(HGRID[jb]), prop_h=hp,
+            prop_score=prop, fallback=fallback, final_h=h_l,
+            final_score=best if fallback else prop,
+            t_grid=t_cv, t_prop=t_sel,
+            t_final=t_sel + (t_cv if fallback else 0.0),
+            fpca_grid=t_prep + t_cv + t_fit_g,
+            fpca_learned=t_prep + t_sel + (t_cv if fallback else 0.0) + t_fit_l,
+            sine_grid=subspace_sine(vec_g, phi), sine_learned=subspace_sine(vec_l, phi)))
     return rows
 
 
 def summarize(rows):
-    """Share of datasets whose final CV score is within 5% of the grid optimum, and
-    the mean wall time of both selections (GPU work plus host overhead)."""
+    """Share of datasets whose final CV score is within 5% of the grid optimum, mean
+    wall times of both selections and of both whole FPCA runs, and the eigenfunction
+    subspace errors of both fits."""
     ok = [r for r in rows if np.isfinite(r["grid_best"])]
     ratio = np.array([r["final_score"] / r["grid_best"] for r in ok])
     pratio = np.array([r["prop_score"] / r["grid_best"] for r in ok])
+    sg = np.array([r["sine_grid"] for r in rows])
+    sl = np.array([r["sine_learned"] for r in rows])
+    mean = lambda key: float(np.mean([r[key] for r in rows]))  # noqa: E731
     return dict(n=len(rows), within5=float(np.mean(ratio <= 1.05)),
                 median_ratio=float(np.median(ratio)), proposal_within5=float(np.mean(pratio <= 1.05)),
-                fallback_rate=float(np.mean([r["fallback"] for r in rows])),
-                t_grid=float(np.mean([r["t_grid"] for r in rows])),
-                t_final=float(np.mean([r["t_final"] for r in rows])))
+                fallback_rate=mean("fallback"), t_grid=mean("t_grid"), t_final=mean("t_final"),
+                fpca_grid_s=mean("fpca_grid"), fpca_learned_s=mean("fpca_learned"),
+                fpca_speedup=mean("fpca_grid") / mean("fpca_learned"),
+                sine_grid_median=float(np.median(sg)), sine_learned_median=float(np.median(sl)),
+                sine_grid_mean=float(np.mean(sg)), sine_learned_mean=float(np.mean(sl)),
+                sine_worse_by_0p01=float(np.mean(sl > sg + 0.01)))
 
 
 def main():
@@ -237,10 +315,17 @@ def main():
     ap.add_argument("--eval", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--out", default="bandwidth_run.npz")
+    ap.add_argument("--rows", default=None, help="write the per-dataset evaluation rows (JSON)")
+    ap.add_argument("--table", default=None,
+                    help="reuse the labelled table (X, Y, M, best) of an earlier run's output")
     a = ap.parse_args()
     ctx = B.Context(0)
     t0 = time.time()
-    X, Y, M, best = make_table(ctx, torch, np.arange(a.train), log_every=200)
+    if a.table:
+        z = np.load(a.table)
+        X, Y, M, best = z["X"], z["Y"], z["M"], z["best"]
+    else:
+        X, Y, M, best = make_table(ctx, torch, np.arange(a.train), log_every=200)
     t_label = time.time() - t0
     Xs, mu, sd = standardize(X)
     t0 = time.time()
@@ -249,9 +334,12 @@ def main():
     rows = evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(a.eval))
     summ = summarize(rows)
     summ.update(t_label=t_label, t_train=t_train, final_loss=hist[-1], first_loss=hist[0],
-                train=a.train, epochs=a.epochs)
+                train=int(X.shape[0]), epochs=a.epochs)
     np.savez(a.out, params=th.cpu().numpy(), mu=mu, sd=sd, X=X, Y=Y, M=M, best=best,
              loss=np.array(hist))
+    if a.rows:
+        with open(a.rows, "w") as fh:
+            json.dump(rows, fh)
     print(json.dumps(summ), flush=True)
 
 

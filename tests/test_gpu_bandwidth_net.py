@@ -196,3 +196,24 @@ def test_bandwidth_workflow_small(ctx):
         assert bw.HGRID[0] <= r["prop_h"] <= bw.HGRID[-1]
         if r["fallback"]:
             assert r["final_score"] == r["grid_best"]
+
+
+@pytest.mark.slow
+def test_learned_bandwidth_gain(ctx):
+    """What the trained network gains: on held-out datasets the whole FPCA with the
+    learned proposal (plus its 3-bandwidth CV check) is faster than the 16-bandwidth
+    CV grid, its CV score stays within 5% of the grid optimum, and its eigenfunctions
+    are as accurate as the grid method's (subspace sine against the truth)."""
+    from paper_1510_04439_gb300 import bandwidth as bw
+    X, Y, M, _ = bw.make_table(ctx, torch, np.arange(300))
+    Xs, mu, sd = bw.standardize(X)
+    th, hist = bw.train(ctx, torch, Xs, Y, M, epochs=150)
+    assert hist[-1] < 0.2 * hist[0]
+    rows = bw.evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(24))
+    s = bw.summarize(rows)
+    assert s["within5"] >= 0.9, s
+    assert s["fpca_learned_s"] < s["fpca_grid_s"], s
+    assert s["sine_learned_median"] <= s["sine_grid_median"] + 0.02, s
+    assert s["sine_grid_median"] < 0.5, s          # the fits do recover the eigenfunctions
+    for r in rows:
+        assert np.isfinite(r["sine_grid"]) and np.isfinite(r["sine_learned"])
