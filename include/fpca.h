@@ -285,6 +285,70 @@ fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, const void* y,
                                  const uint8_t* mask, int32_t* cnt, double* w, double* v,
                                  double* v2);
 
+/* ---- d = 3: covariance smoothing fused into its projection ----------------
+ *
+ * For a 32 x 32 x 32 grid the covariance grid has P^2 = 1.07e9 points; these
+ * entry points smooth it (Eq. 2.4 with the Section 3.2 binning) and apply it
+ * to a block of vectors without forming the P x P bins or the P x P surface,
+ * for the random projection of Section 3.4.
+ *
+ * Scope: d = 3, every subject observed at every grid node (dense layout,
+ * mask NULL), 2 <= M_k <= 64, residual mode, the same bandwidth vector h for
+ * s and t with 1..8 kernel taps per axis (taps = #{k >= 1 : k/(h_k M_k) < 1}).
+ * Other inputs return FPCA_E_UNSUPPORTED.
+ *
+ * Arithmetic: residuals R~ = (Y - mu_hat)/sqrt(n) in BF16 for the tensor-core
+ * products (FP32 accumulation), FP32 elsewhere; per-point local solves in
+ * FP32 (an ill-conditioned one makes fpca_sync() return FPCA_E_NUMERIC);
+ * Rayleigh-Ritz in FP64.  For fully observed data every local system is
+ * regular (status FPCA_PT_OK at every point), so no status array is produced.
+ */
+
+/* Bytes of the factored covariance bins of n subjects on `grid` (0 if the
+ * grid is not 3-dimensional).  Host function, no device work. */
+size_t fpca_cov_factor_bytes(const fpca_grid* grid, int n);
+
+/* Covariance bins of fully observed gridded data in factored form (Eq. 2.4,
+ * Section 3.2): the bins are W[p,q] = sum_i w_i (p != q) and
+ * V[p,q] = sum_i w_i R_ip R_iq with the diagonal p == q dropped, so the
+ * n x P residual matrix R = Y - mu_hat determines them; it is stored (with
+ * its node-wise sums of squares) instead of the P x P arrays.
+ *  data   dense layout, mask NULL, y n x P (F32 or F64), n >= 2.
+ *  mu     P doubles, the mean fit at the nodes (fpca_smooth_mean).
+ *  factor device buffer of at least fpca_cov_factor_bytes(grid, n) bytes,
+ *         overwritten; opaque, read by the calls below with the same grid
+ *         and n. */
+fpca_status fpca_bin_cov_factor(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                                const double* mu, void* factor, size_t factor_bytes);
+
+/* y = Gamma_hat x: the covariance surface of Eq. (2.4) at bandwidth h (host,
+ * 3 doubles), residual mode, matrixised as in Section 3.1 (row = s, column
+ * = t, nodes in C order), times the P x l block x.
+ *  x, y   P x l floats, row-major (row = node), 1 <= l <= 64. */
+fpca_status fpca_smooth_cov_apply(fpca_ctx* ctx, const fpca_grid* grid, const void* factor,
+                                  int n, const double* h, const float* x, int l, float* y);
+
+/* Gamma_hat at the output pairs of ntiles tile pairs (for checking): tiles
+ * (HOST, ntiles x 6 int32) holds per tile the s-box corner (multiples of
+ * 4, 4, 8) and the t-box corner (multiples of 4, 4, 4); out (device,
+ * ntiles x 128 x 64 floats) receives Gamma_hat(s, t) for the 4 x 4 x 8 s-box
+ * (C order) against the 4 x 4 x 4 t-box (C order), NaN where a node lies off
+ * the grid.  Synchronises the context's stream before returning. */
+fpca_status fpca_smooth_cov_tiles(fpca_ctx* ctx, const fpca_grid* grid, const void* factor,
+                                  int n, const double* h, int ntiles, const int32_t* tiles,
+                                  float* out);
+
+/* Random projection of Section 3.4 on the fused operator: Y = Gamma_hat Omega,
+ * power_iters re-orthonormalised power steps, Rayleigh-Ritz on l columns in
+ * FP64, rescaling lambda = theta dV, phi = psi / sqrt(dV) (dV = 1/P), sign and
+ * FVE (trace of Gamma_hat from its diagonal) as fpca_rproj_eig.
+ *  omega  P x l floats (device), k < l <= 64.
+ *  evals k, evecs P x k column-major (vector j at evecs + j*P), fve k (may
+ *  be NULL): device doubles. */
+fpca_status fpca_rproj_eig_factor(fpca_ctx* ctx, const fpca_grid* grid, const void* factor,
+                                  int n, const double* h, const float* omega, int l, int k,
+                                  int power_iters, double* evals, double* evecs, double* fve);
+
 #ifdef __cplusplus
 }
 #endif

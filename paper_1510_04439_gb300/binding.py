@@ -28,7 +28,8 @@ SYMBOLS = (
     "fpca_launch_count", "fpca_bin_mean", "fpca_smooth_mean", "fpca_bin_cov",
     "fpca_smooth_cov_project", "fpca_rproj_eig", "fpca_profile_enable", "fpca_profile_count",
     "fpca_profile_entry", "fpca_bin_mean_static", "fpca_bw_param_count", "fpca_bw_predict",
-    "fpca_bw_train_step", "fpca_bw_features",
+    "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
+    "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor",
 )
 
 
@@ -111,6 +112,15 @@ def load(path=LIB_PATH):
     lib.fpca_bw_train_step.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, ctypes.c_float,
                                        ctypes.c_float, vp, vp]
     lib.fpca_bin_mean_static.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp]
+    lib.fpca_cov_factor_bytes.argtypes = [ctypes.POINTER(Grid), i32]
+    lib.fpca_cov_factor_bytes.restype = ctypes.c_size_t
+    lib.fpca_bin_cov_factor.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp,
+                                        ctypes.c_size_t]
+    lib.fpca_smooth_cov_apply.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp, i32, vp]
+    lib.fpca_smooth_cov_tiles.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, i32,
+                                          ctypes.POINTER(ctypes.c_int32), vp]
+    lib.fpca_rproj_eig_factor.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp, i32, i32,
+                                          i32, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
     lib.fpca_profile_count.argtypes = [vp]
     lib.fpca_profile_entry.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
@@ -118,7 +128,7 @@ def load(path=LIB_PATH):
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count",
-                        "fpca_bw_param_count"):
+                        "fpca_bw_param_count", "fpca_cov_factor_bytes"):
             f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -203,6 +213,35 @@ class Context:
         self._check(self.lib.fpca_bw_features(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
                                               _ptr(cnt), _ptr(w), _ptr(v), _ptr(v2),
                                               ctypes.byref(bins), _ptr(feat)))
+
+    # ---- d = 3 fused smoother ------------------------------------------------
+    def cov_factor_bytes(self, m, n):
+        return int(self.lib.fpca_cov_factor_bytes(ctypes.byref(Grid.of(m)), int(n)))
+
+    def bin_cov_factor(self, data, m, mu, factor):
+        """factor: a uint8 device tensor of at least cov_factor_bytes(m, n) bytes."""
+        self._check(self.lib.fpca_bin_cov_factor(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                                 _ptr(mu), _ptr(factor), int(factor.numel())))
+
+    def smooth_cov_apply(self, m, factor, n, h, x, y):
+        self._check(self.lib.fpca_smooth_cov_apply(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),
+                                                   int(n), _doubles(h), _ptr(x), int(x.shape[1]),
+                                                   _ptr(y)))
+
+    def smooth_cov_tiles(self, m, factor, n, h, tiles, out):
+        """tiles: host int32 array (ntiles, 6) of s- and t-box corners."""
+        import numpy as np
+        tl = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1, 6))
+        arr = (ctypes.c_int32 * tl.size)(*tl.ravel().tolist())
+        self._check(self.lib.fpca_smooth_cov_tiles(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),
+                                                   int(n), _doubles(h), int(tl.shape[0]), arr,
+                                                   _ptr(out)))
+
+    def rproj_eig_factor(self, m, factor, n, h, omega, k, evals, evecs, fve=None, power_iters=0):
+        self._check(self.lib.fpca_rproj_eig_factor(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),
+                                                   int(n), _doubles(h), _ptr(omega),
+                                                   int(omega.shape[1]), int(k), int(power_iters),
+                                                   _ptr(evals), _ptr(evecs), _ptr(fve)))
 
     def bw_predict(self, params, feat, out):
         self._check(self.lib.fpca_bw_predict(self.h, _ptr(params), _ptr(feat), int(feat.shape[0]),

@@ -205,6 +205,7 @@ void fpca_destroy(fpca_ctx* ctx) {
   if (ctx->prof_last) cudaEventDestroy(ctx->prof_last);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->f3_lists) cudaFree(ctx->f3_lists);
   delete ctx;
 }
 
@@ -256,6 +257,8 @@ fpca_status fpca_sync(fpca_ctx* ctx) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     if (herr == DERR_TIMEOUT)
       return fpca_fail(ctx, FPCA_E_TIMEOUT, "a device-side bounded wait ran out");
+    if (herr == DERR_NUMERIC)
+      return fpca_fail(ctx, FPCA_E_NUMERIC, "an ill-conditioned local system in the fused d = 3 smoother");
     return fpca_fail(ctx, FPCA_E_CUDA, "device-side check failed (code %d)", herr);
   }
   return FPCA_OK;

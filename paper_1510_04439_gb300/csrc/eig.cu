@@ -802,3 +802,65 @@ fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, 
   return rproj_typed<float, float>(ctx, g, static_cast<const float*>(gamma), domain, omega, l, k,
                                    power_iters, 0, evals, evecs, fve);
 }
+
+// ---------------------------------------------------------------------------
+// Random projection of Section 3.4 on an operator: the covariance matrix is
+// never formed, only its products Y = Sigma X (P x l, FP32, row-major) through
+// op.apply.  The steps are those of the dense path above: range finder with
+// CholeskyQR2 and power iterations, Rayleigh-Ritz in FP64, rescaling and FVE
+// (trace of Sigma supplied by the caller in ws.trace[0], unscaled).
+// ---------------------------------------------------------------------------
+size_t rproj_ws_bytes(int P, int l) {
+  return 3 * WsCarve::round(sizeof(float) * (size_t)P * l) +
+         5 * WsCarve::round(sizeof(double) * (size_t)l * l) + WsCarve::round(sizeof(double) * 4) +
+         WsCarve::round(sizeof(int) * 3 * (size_t)l) + 2048;
+}
+
+void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w) {
+  w.Y = c.take<float>((size_t)P * l);
+  w.Q = c.take<float>((size_t)P * l);
+  w.Z = c.take<float>((size_t)P * l);
+  w.G = c.take<double>((size_t)l * l);
+  w.Rinv = c.take<double>((size_t)l * l);
+  w.work = c.take<double>((size_t)l * l);
+  w.A = c.take<double>((size_t)l * l);
+  w.V = c.take<double>((size_t)l * l);
+  w.trace = c.take<double>(4);
+  w.order = c.take<int>(3 * (size_t)l);
+}
+
+fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, double dv,
+                           const float* omega, RprojOp op, const RprojWs& w, double* evals,
+                           double* evecs, double* fve) {
+  fpca_status s = op.apply(op.self, omega, w.Y);
+  if (s != FPCA_OK) return s;
+  for (int it = 0; it < power_iters; ++it) {
+    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work);
+    if (s != FPCA_OK) return s;
+    s = op.apply(op.self, w.Q, w.Y);
+    if (s != FPCA_OK) return s;
+  }
+  s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work);
+  if (s != FPCA_OK) return s;
+  s = op.apply(op.self, w.Q, w.Z);
+  if (s != FPCA_OK) return s;
+  cudaMemsetAsync(w.A, 0, sizeof(double) * l * l, ctx->stream);
+  k_cross_gram<float><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, w.Q, w.Z, w.A);
+  FPCA_LAUNCHED(ctx, "ritz_gram");
+  static bool jattr = false;
+  if (!jattr) {
+    cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * 64 * 64 * sizeof(double)));
+    jattr = true;
+  }
+  k_jacobi_small<<<1, 256, 2 * (size_t)l * l * sizeof(double), ctx->stream>>>(l, w.A, w.V, 60);
+  FPCA_LAUNCHED(ctx, "jacobi");
+  k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, w.A, w.order);
+  FPCA_LAUNCHED(ctx, "eig_order");
+  k_ritz_vectors<float><<<(P + 127) / 128, 128, 0, ctx->stream>>>(P, l, k, w.Q, w.V, w.order,
+                                                                   evecs);
+  FPCA_LAUNCHED(ctx, "ritz_vectors");
+  k_finish<<<k, 1024, 0, ctx->stream>>>(P, l, k, dv, w.A, w.order, w.trace, evals, evecs, fve);
+  FPCA_LAUNCHED(ctx, "eig_finish");
+  return FPCA_OK;
+}

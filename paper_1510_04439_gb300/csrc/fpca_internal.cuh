@@ -35,10 +35,15 @@ struct fpca_ctx {
   std::vector<cudaEvent_t> prof_pool;
   std::map<std::string, std::pair<double, uint64_t>> prof_totals;
   std::vector<std::string> prof_names;  // stable storage for fpca_profile_entry
+  // d = 3 fused smoother: tile-pair work lists for the last grid / taps seen
+  void* f3_lists = nullptr;
+  size_t f3_lists_bytes = 0;
+  int f3_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int f3_ncta = 0, f3_nitems = 0, f3_npairs = 0;
 };
 
 // Device error codes written by kernels into ctx->d_err.
-enum { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BOUNDS = 2 };
+enum { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BOUNDS = 2, DERR_NUMERIC = 3 };
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 #define FPCA_WAIT_LIMIT_NS 2000000000ull
@@ -118,6 +123,20 @@ fpca_status smooth_cov_run(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins
                            const float* omega, int l, void* gamma, uint8_t* status, float* y,
                            double* cv);
 // eig.cu
+struct RprojOp {
+  fpca_status (*apply)(void* self, const float* X, float* Y);  // Y = Sigma X, P x l
+  void* self;
+};
+struct RprojWs {
+  float *Y, *Q, *Z;
+  double *G, *Rinv, *work, *A, *V, *trace;
+  int* order;
+};
+size_t rproj_ws_bytes(int P, int l);
+void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w);
+fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, double dv,
+                           const float* omega, RprojOp op, const RprojWs& w, double* evals,
+                           double* evecs, double* fve);
 fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, int gamma_prec,
                           const int32_t* domain, const float* omega, int l, int k,
                           int power_iters, int full, double* evals, double* evecs,
