@@ -36,6 +36,117 @@ H = (0.15, 0.15)
 K_EIG, L_RP, Q_POWER = 8, 18, 2
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
+BW_TRAIN, BW_EVAL = 400, 40
+F3_K, F3_L = 10, 64
+
+
+def near_pairs(m, T):
+    """Tile pairs (128-node s-boxes 4x4x8 by 64-node t-boxes 4x4x4) holding output
+    pairs whose kernel windows share nodes, and the output pairs they hold."""
+    nb = [(m[0] + 3) // 4, (m[1] + 3) // 4, (m[2] + 7) // 8]
+    sx = [4, 4, 8]
+    cnt = 1
+    for k in range(3):
+        ns, nt = nb[k], (nb[k] if k < 2 else 2 * nb[k])
+        tx = 4
+        c = 0
+        for a in range(ns):
+            slo, shi = sx[k] * a, min(sx[k] * a + sx[k] - 1, m[k] - 1)
+            for b in range(nt):
+                tlo = tx * b
+                if tlo > m[k] - 1:
+                    continue
+                thi = min(tlo + tx - 1, m[k] - 1)
+                if max(0, tlo - shi, slo - thi) <= 2 * T[k]:
+                    c += 1
+        cnt *= c
+    return cnt
+
+
+def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush):
+    """n = 2000 volumes on 32^3: mean bins, mean fit, factored covariance bins and the
+    fused smoother -> random projection (k = 10, l = 64, no power step), timed on the
+    device with the L2 flushed between steps."""
+    D = fs.dense_3d()
+    m, n, h = D.m, D.n, [0.15, 0.15, 0.15]
+    P = D.P
+    y = torch.from_numpy(D.y.astype(np.float32)).to(dev)
+    data = ctx.dense(y)
+    cnt = torch.empty(P, dtype=torch.int32, device=dev)
+    w = torch.empty(P, dtype=torch.float64, device=dev)
+    v = torch.empty_like(w)
+    mu = torch.empty_like(w)
+    fac = torch.empty(ctx.cov_factor_bytes(m, n), dtype=torch.uint8, device=dev)
+    om = torch.from_numpy(fs.gaussian_test_matrix(P, F3_L, fs.SEED_BASE + 3).astype(np.float32)).to(dev)
+    ev = torch.empty(F3_K, dtype=torch.float64, device=dev)
+    evec = torch.empty(F3_K, P, dtype=torch.float64, device=dev)
+    fve = torch.empty_like(ev)
+    Yb = torch.empty(P, F3_L, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.bin_mean(data, m, cnt, w, v)
+        ctx.smooth_mean(m, cnt, w, v, h, mu)
+        ctx.bin_cov_factor(data, m, mu, fac)
+        ctx.rproj_eig_factor(m, fac, n, h, om, F3_K, ev, evec, fve, power_iters=0)
+
+    step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    evs = []
+    for _ in range(3):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    # one Gamma_hat X pass on its own (B planes included)
+    ctx.smooth_cov_apply(m, fac, n, h, om, Yb)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        ctx.smooth_cov_apply(m, fac, n, h, om, Yb)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_apply = a.elapsed_time(b) / 3
+    npairs = near_pairs(m, [taps(hk, mk) for hk, mk in zip(h, m)])
+    near = prof.get("f3_near")
+    roof = None
+    if near:
+        n_pad = (n + 127) // 128 * 128
+        per_launch = near[0] / near[1]
+        flops = npairs * (7 * 128 * 64 * n_pad * 2 + 128 * 64 * 64 * 2)
+        achieved = flops / (per_launch * 1e-3) / 1e12
+        peak = measured_peak("bf16_tflops_sustained")
+        roof = {"kernel": "f3_near", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "tile_pairs": npairs, "ms_per_launch": per_launch,
+                "flops_basis": "7 BF16 products 128x64xK(n_pad) + the 128x64x64 correction product per tile pair"}
+    passes = 2.0
+    pts = float(P) * P
+    return {"workload": "dense_3d_32x32x32_n2000_h0.15", "ms_per_step": ms,
+            "value": passes * pts / (ms * 1e-3), "unit": UNIT,
+            "cov_points_per_pass": pts, "passes": passes, "ms_per_apply": ms_apply,
+            "evals": [float(x) for x in ev.cpu().numpy()],
+            "roofline_near": roof,
+            "kernels": {k: {"ms_total": v[0] / 3, "launches": v[1] // 3}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+
+
+def measured_peak(key):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d[key]) if key in d else None
+    except Exception:
+        return None
 
 
 def parse():
@@ -412,6 +523,24 @@ def main():
                "kernels": {k: {"ms_total": v[0] / 3, "launches": v[1] // 3}
                            for k, v in sorted(prof_cv.items(), key=lambda kv: -kv[1][0])[:6]}}
 
+    # ---- d = 3 volumes: smoothing fused into the projection (reported beside) ----
+    f3x = None
+    if not args.no_extras:
+        f3x = bench_fused3(torch, np, fs, B, ctx, dev, stream, flush)
+
+    # ---- learned bandwidths against the CV grid (reported beside) ----
+    bwx = None
+    if not args.no_extras and rank == 0:
+        from paper_1510_04439_gb300 import bandwidth as bw
+        t0 = time.time()
+        X, Y, M, _ = bw.make_table(ctx, torch, np.arange(BW_TRAIN))
+        t_lab = time.time() - t0
+        Xs, mu_x, sd_x = bw.standardize(X)
+        th, hist = bw.train(ctx, torch, Xs, Y, M, epochs=150)
+        rows = bw.evaluate(ctx, torch, th, mu_x, sd_x, 10 ** 6 + np.arange(BW_EVAL))
+        bwx = dict(bw.summarize(rows), train=BW_TRAIN, label_s=t_lab, final_loss=hist[-1],
+                   note="short in-bench training; the full 5000/200 run is the module CLI")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npts, el = oracle_sample_rate(args.cpu_seconds)
@@ -441,6 +570,8 @@ def main():
             "roofline": roof,
             "variant_uncompensated": variant,
             "cv_grid": cvx,
+            "fused_3d": f3x,
+            "learned_bandwidth": bwx,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernels": kernels,

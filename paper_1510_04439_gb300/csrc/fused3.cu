@@ -245,17 +245,19 @@ __global__ void __launch_bounds__(256) k_f3_conv(ConvArgs a) {
 // point geometry: k0, mu1, var of the product kernel at node (c0, c1, c2)
 // ---------------------------------------------------------------------------
 struct PtGeo {
-  float k0, mu1[3], var[3];
+  float k0, ik0, mu1[3], var[3], ivar[3];
 };
 
 __device__ __forceinline__ PtGeo f3_geo(const Tab3* __restrict__ tab, int c0, int c1, int c2) {
   PtGeo p;
   const int c[3] = {c0, c1, c2};
   p.k0 = tab->k0[0][c0] * tab->k0[1][c1] * tab->k0[2][c2];
+  p.ik0 = 1.f / p.k0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     p.mu1[j] = tab->mu1[j][c[j]];
     p.var[j] = tab->var[j][c[j]];
+    p.ivar[j] = 1.f / p.var[j];
   }
   return p;
 }
@@ -356,13 +358,13 @@ __global__ void k_f3_ycombine(Geo3 g, const Tab3* __restrict__ tab, int l, int l
 // P01, P02, P03); returns the normalisation 1/(k0(s) k0(t)).
 __device__ __forceinline__ float f3_beta(const PtGeo& s, const PtGeo& t, const float Pv[7],
                                          float beta[7]) {
-  const float inv = 1.f / (s.k0 * t.k0);
+  const float inv = s.ik0 * t.ik0;
   const float z0 = Pv[0] * inv;
   float b0 = z0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    beta[1 + j] = (Pv[1 + j] * inv - s.mu1[j] * z0) / s.var[j];
-    beta[4 + j] = (Pv[4 + j] * inv - t.mu1[j] * z0) / t.var[j];
+    beta[1 + j] = (Pv[1 + j] * inv - s.mu1[j] * z0) * s.ivar[j];
+    beta[4 + j] = (Pv[4 + j] * inv - t.mu1[j] * z0) * t.ivar[j];
     b0 -= s.mu1[j] * beta[1 + j] + t.mu1[j] * beta[4 + j];
   }
   beta[0] = b0;
@@ -423,7 +425,8 @@ __device__ __forceinline__ float f3_corr(const PtGeo& s, const PtGeo& t, const f
       A[i][j] = ap - Ad[i][j];
     }
   }
-  // Cholesky A = L L' (lower, in place); pivots checked against the diagonal
+  // Cholesky A = L L' (lower, in place; il = 1/L_jj); pivots checked against the diagonal
+  float il[7];
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     float dj = A[j][j];
@@ -433,14 +436,13 @@ __device__ __forceinline__ float f3_corr(const PtGeo& s, const PtGeo& t, const f
       bad = 1;
       return 0.f;
     }
-    const float ljj = sqrtf(dj), il = 1.f / ljj;
-    A[j][j] = ljj;
+    il[j] = rsqrtf(dj);
 #pragma unroll
     for (int i = j + 1; i < 7; ++i) {
       float v = A[i][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) v = fmaf(-A[i][k], A[j][k], v);
-      A[i][j] = v * il;
+      A[i][j] = v * il[j];
     }
   }
   float yv[7];
@@ -449,14 +451,14 @@ __device__ __forceinline__ float f3_corr(const PtGeo& s, const PtGeo& t, const f
     float v = rhs[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) v = fmaf(-A[i][k], yv[k], v);
-    yv[i] = v / A[i][i];
+    yv[i] = v * il[i];
   }
 #pragma unroll
   for (int i = 6; i >= 0; --i) {
     float v = yv[i];
 #pragma unroll
     for (int k = i + 1; k < 7; ++k) v = fmaf(-A[k][i], yv[k], v);
-    yv[i] = v / A[i][i];
+    yv[i] = v * il[i];
   }
   return yv[0];
 }
@@ -538,7 +540,9 @@ constexpr int NNSTAGE = 3;
 constexpr int WMAX = 12;                   // window-union extent per axis (taps <= 4)
 constexpr int F3_TSTAGE = 4;               // largest taps the staged kernel takes
 constexpr int G0_FLOATS = WMAX * WMAX * 16 * 2;
-constexpr int G1_FLOATS = WMAX * 16 * 16 * 3;
+constexpr int G1_S0 = 16 * 3 + 1;           // padded strides of G1 (bank spread)
+constexpr int G1_P2 = 16 * G1_S0 + 5;
+constexpr int G1_FLOATS = WMAX * G1_P2;
 constexpr int PT_FLOATS = 576;             // pair tables: rho slices, t geometry, taps
 constexpr int OFF_CORR = NNSTAGE * NSTAGE_BYTES;
 constexpr int OFF_XT = OFF_CORR + CORR_BYTES;
@@ -547,6 +551,7 @@ constexpr int OFF_G1 = OFF_G0 + G0_FLOATS * 4;
 constexpr int OFF_PT = OFF_G1 + G1_FLOATS * 4;
 constexpr int OFF_BAR = OFF_PT + PT_FLOATS * 4;
 constexpr size_t NEAR_SMEM2 = OFF_BAR + 256 + 1024;
+static_assert(NEAR_SMEM2 <= 232448, "near kernel exceeds the 227 KB opt-in shared memory");
 
 struct NearArgs {
   Geo3 g;
@@ -580,7 +585,7 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
   float* rho0 = PT;              // [16][6]  (s0, t0)
   float* rho1 = PT + 96;         // [16][6]  (s1, t1)
   float* rho2 = PT + 192;        // [32][6]  (s2, t2)
-  float* tgeo = PT + 384;        // [3][4][3] k0, mu1, var of the T-box nodes per axis
+  float* tgeo = PT + 384;        // [3][4][3] 1/k0, mu1, var of the T-box nodes per axis
   float* tk = PT + 432;          // [3][17]  K(r/hM)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
   uint64_t* full = bars;
@@ -786,9 +791,10 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
         } else {
           const int e = i - 64 * 6, ax = e / 12, tl = (e % 12) / 3, qk = e % 3;
           const int tv = to[ax] + tl;
-          float v = qk == 0 ? 1.f : 0.f;
+          float v = qk == 1 ? 0.f : 1.f;
           if (tv < g.m[ax])
-            v = qk == 0 ? a.tab->k0[ax][tv] : qk == 1 ? a.tab->mu1[ax][tv] : a.tab->var[ax][tv];
+            v = qk == 0 ? 1.f / a.tab->k0[ax][tv]
+                        : qk == 1 ? a.tab->mu1[ax][tv] : a.tab->var[ax][tv];
           tgeo[e] = v;
         }
       }
@@ -832,7 +838,7 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
               c2 = fmaf(w * (p1 - s1) * ihM[1], src[0], c2);
             }
           }
-          float* o = G1 + ((p2i * 16 + st0) * 16 + st1) * 3;
+          float* o = G1 + p2i * G1_P2 + st0 * G1_S0 + st1 * 3;
           o[0] = c0;
           o[1] = c1;
           o[2] = c2;
@@ -879,11 +885,13 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
               Pv[p] = __uint_as_float(x);
             }
             PtGeo tg;
-            tg.k0 = tgeo[0 * 12 + tl[0] * 3] * tgeo[1 * 12 + tl[1] * 3] * tgeo[2 * 12 + tl[2] * 3];
+            tg.ik0 = tgeo[0 * 12 + tl[0] * 3] * tgeo[1 * 12 + tl[1] * 3] * tgeo[2 * 12 + tl[2] * 3];
+            tg.k0 = 1.f / tg.ik0;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
               tg.mu1[k] = tgeo[k * 12 + tl[k] * 3 + 1];
               tg.var[k] = tgeo[k * 12 + tl[k] * 3 + 2];
+              tg.ivar[k] = 1.f / tg.var[k];
             }
             float beta[7];
             const float inv = f3_beta(sg, tg, Pv, beta);
@@ -910,7 +918,7 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
               float Q0 = 0.f, Qs[3] = {0.f, 0.f, 0.f};
               for (int p2 = lo; p2 <= hi; ++p2) {
                 const float w = tk[34 + p2 - sc[2] + F3_TMAX] * tk[34 + p2 - tc[2] + F3_TMAX];
-                const float* src = G1 + (((p2 - wlo[2]) * 16 + st0) * 16 + st1) * 3;
+                const float* src = G1 + (p2 - wlo[2]) * G1_P2 + st0 * G1_S0 + st1 * 3;
                 Q0 = fmaf(w, src[0], Q0);
                 Qs[0] = fmaf(w, src[1], Qs[0]);
                 Qs[1] = fmaf(w, src[2], Qs[1]);
