@@ -63,11 +63,11 @@ def near_pairs(m, T):
     return cnt
 
 
-def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush):
+def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush, shape=(32, 2000)):
     """n = 2000 volumes on 32^3: mean bins, mean fit, factored covariance bins and the
     fused smoother -> random projection (k = 10, l = 64, no power step), timed on the
     device with the L2 flushed between steps."""
-    D = fs.dense_3d()
+    D = fs.dense_3d(n=shape[1], m=shape[0])
     m, n, h = D.m, D.n, [0.15, 0.15, 0.15]
     P = D.P
     y = torch.from_numpy(D.y.astype(np.float32)).to(dev)
@@ -131,7 +131,7 @@ def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush):
                 "flops_basis": "7 BF16 products 128x64xK(n_pad) + the 128x64x64 correction product per tile pair"}
     passes = 2.0
     pts = float(P) * P
-    return {"workload": "dense_3d_32x32x32_n2000_h0.15", "ms_per_step": ms,
+    return {"workload": f"dense_3d_{m[0]}x{m[1]}x{m[2]}_n{n}_h0.15", "ms_per_step": ms,
             "value": passes * pts / (ms * 1e-3), "unit": UNIT,
             "cov_points_per_pass": pts, "passes": passes, "ms_per_apply": ms_apply,
             "evals": [float(x) for x in ev.cpu().numpy()],
@@ -158,6 +158,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU time budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused3-only", action="store_true",
+                    help="run only the d = 3 fused smoother extra (profiling)")
+    ap.add_argument("--fused3-shape", default="32,2000",
+                    help="grid extent per axis and subjects of the d = 3 extra (default 32,2000)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CV-grid measurement reported beside the headline")
     return ap.parse_args()
@@ -347,6 +351,14 @@ def main():
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.fused3_only:
+        M3, N3 = (int(x) for x in args.fused3_shape.split(","))
+        ctx = B.Context(local_rank, torch.cuda.current_stream(dev))
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        out = bench_fused3(torch, np, fs, B, ctx, dev, torch.cuda.current_stream(dev), flush,
+                           (M3, N3))
+        print(json.dumps({"fused_3d": out}), flush=True)
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -526,7 +538,8 @@ def main():
     # ---- d = 3 volumes: smoothing fused into the projection (reported beside) ----
     f3x = None
     if not args.no_extras:
-        f3x = bench_fused3(torch, np, fs, B, ctx, dev, stream, flush)
+        f3x = bench_fused3(torch, np, fs, B, ctx, dev, stream, flush,
+                           tuple(int(x) for x in args.fused3_shape.split(",")))
 
     # ---- learned bandwidths against the CV grid (reported beside) ----
     bwx = None

@@ -117,19 +117,102 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// G (l x l, FP64) += A' B over a chunk of rows (A, B: P x l).
+// Partial Gram products A'B (l x l) over blocks of GR_ROWS rows (A, B: P x l),
+// written per block and summed in block order by k_gram_sum (no atomics, so the
+// result does not depend on scheduling).
+//
+// FP32 inputs use error-free transformations so that the sums keep about FP64
+// accuracy at FP32 speed (GB300 runs FP64 at 1/64 of the FP32 rate): each
+// product a*b is split exactly as p + e with e = fma(a, b, -p) (Dekker's
+// two-product through an FMA), p is accumulated by Knuth's two-sum and the
+// rounding errors are summed separately (the compensated dot product of Ogita,
+// Rump and Oishi, "Accurate sum and dot product", 2005).  FP64 inputs use
+// plain FP64 sums.
+constexpr int GR_ROWS = 256;
+constexpr int GR_SUB = 32;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
 template <typename TX>
-__global__ void k_cross_gram(int P, int l, const TX* __restrict__ A, const TX* __restrict__ B,
-                             double* __restrict__ G) {
-  const int rows_per_block = 64;
-  const int r0 = blockIdx.x * rows_per_block;
-  const int r1 = min(P, r0 + rows_per_block);
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e - (e / l) * l;
-    double s = 0.0;
-    for (int r = r0; r < r1; ++r) s += (double)A[(long long)r * l + i] * (double)B[(long long)r * l + j];
-    atomicAdd(G + e, s);
+__global__ void __launch_bounds__(256)
+    k_cross_gram(int P, int l, const TX* __restrict__ A, const TX* __restrict__ B,
+                 double* __restrict__ part) {
+  __shared__ TX As[GR_SUB * 64], Bs[GR_SUB * 64];
+  const int r0 = blockIdx.x * GR_ROWS, r1 = min(P, r0 + GR_ROWS);
+  const int ne = l * l;
+  // up to 16 entries per thread (l <= 64, 256 threads)
+  float hs[16], hc[16];
+  double dsum[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    hs[k] = 0.f;
+    hc[k] = 0.f;
+    dsum[k] = 0.0;
   }
+  for (int rb = r0; rb < r1; rb += GR_SUB) {
+    const int nr = min(GR_SUB, r1 - rb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
+      As[e] = A[(long long)rb * l + e];
+      Bs[e] = B[(long long)rb * l + e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = threadIdx.x + k * 256;
+      if (e >= ne) break;
+      const int i = e / l, j = e - (e / l) * l;
+      if constexpr (sizeof(TX) == 4) {
+        float s = hs[k], c = hc[k];
+        for (int r = 0; r < nr; ++r) {
+          const float a = As[r * l + i], b = Bs[r * l + j];
+          const float pp = a * b;
+          const float pe = fmaf(a, b, -pp);
+          float t, te;
+          two_sum(s, pp, t, te);
+          s = t;
+          c += te + pe;
+        }
+        hs[k] = s;
+        hc[k] = c;
+      } else {
+        double d = dsum[k];
+        for (int r = 0; r < nr; ++r) d += (double)As[r * l + i] * (double)Bs[r * l + j];
+        dsum[k] = d;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int e = threadIdx.x + k * 256;
+    if (e >= ne) break;
+    part[(long long)blockIdx.x * ne + e] =
+        sizeof(TX) == 4 ? (double)hs[k] + (double)hc[k] : dsum[k];
+  }
+}
+
+// G = sum over blocks of the partial products, in block order (FP64).
+__global__ void k_gram_sum(int nb, int ne, const double* __restrict__ part, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(long long)b * ne + e];
+  G[e] = s;
+}
+
+template <typename TX>
+fpca_status launch_cross_gram(fpca_ctx* ctx, int P, int l, const TX* A, const TX* B, double* part,
+                              double* G, const char* name) {
+  const int nb = (P + GR_ROWS - 1) / GR_ROWS;
+  k_cross_gram<TX><<<nb, 256, 0, ctx->stream>>>(P, l, A, B, part);
+  FPCA_LAUNCHED(ctx, name);
+  k_gram_sum<<<(l * l + 255) / 256, 256, 0, ctx->stream>>>(nb, l * l, part, G);
+  FPCA_LAUNCHED(ctx, "gram_sum");
+  return FPCA_OK;
 }
 
 // Upper Cholesky G = R'R and Rinv (one block, l <= 64, shared memory).
@@ -363,53 +446,42 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// The same cyclic parallel Jacobi for n <= 64 with A and V in shared memory;
-// results are copied back to A and V in global memory.
-__global__ void __launch_bounds__(256)
-    k_jacobi_small(int n, double* __restrict__ Ag, double* __restrict__ Vg, int max_sweeps) {
-  extern __shared__ double jsm[];
-  double* A = jsm;          // n x n
-  double* V = jsm + n * n;  // n x n
-  __shared__ double cs[64];
-  __shared__ int pr[64];
-  __shared__ double red[8];
-  __shared__ int done;
+// Cyclic parallel Jacobi sweeps (the pair schedule of k_jacobi) on A and V
+// in shared memory, in the arithmetic of T, until off(A)^2 <= tol * diag(A)^2
+// or max_sweeps; every thread of the block takes part.
+template <typename T>
+__device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double tol, T* cs,
+                              int* pr, double* red, int* done) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = (n + 1) & ~1;
   const int np = ne / 2;
-  // (A + A')/2: a Rayleigh-Ritz matrix formed as Q'(Sigma Q) is symmetric
-  // only to rounding, and the rotations zero one triangle
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e - (e / n) * n;
-    A[e] = 0.5 * (Ag[e] + Ag[j * n + i]);
-    V[e] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int e = tid; e < n * n; e += nt) {
-      const double a = A[e];
-      if (e / n == e % n) dia += a * a;
+      const int r = e / n, c = e - r * n;
+      const double a = (double)A[r * ld + c];
+      if (r == c) dia += a * a;
       else off += a * a;
     }
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
       dia += __shfl_xor_sync(0xffffffffu, dia, o);
     }
-    if ((tid & 31) == 0) red[tid >> 5] = off;
-    __syncthreads();
-    double offt = 0.0;
-    for (int w = 0; w < nt / 32; ++w) offt += red[w];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = dia;
-    __syncthreads();
-    if (tid == 0) {
-      double diat = 0.0;
-      for (int w = 0; w < nt / 32; ++w) diat += red[w];
-      done = (offt <= 1e-26 * diat) || offt == 0.0;
+    if ((tid & 31) == 0) {
+      red[2 * (tid >> 5)] = off;
+      red[2 * (tid >> 5) + 1] = dia;
     }
     __syncthreads();
-    if (done) break;
+    if (tid == 0) {
+      double ot = 0.0, dt = 0.0;
+      for (int w = 0; w < nt / 32; ++w) {
+        ot += red[2 * w];
+        dt += red[2 * w + 1];
+      }
+      *done = (ot <= tol * dt) || ot == 0.0;
+    }
+    __syncthreads();
+    if (*done) break;
     for (int step = 0; step < ne - 1; ++step) {
       if (tid < np) {
         const int i = tid;
@@ -426,13 +498,13 @@ __global__ void __launch_bounds__(256)
           p = q;
           q = tt;
         }
-        double c = 1.0, sn = 0.0;
+        T c = T(1), sn = T(0);
         if (q < n) {
-          const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+          const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+          if (fabs(apq) > T(1e-30) && fabs(apq) > T(1e-18) * sqrt(fabs(app) * fabs(aqq))) {
+            const T tau = (aqq - app) / (T(2) * apq);
+            const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + tt * tt);
             sn = tt * c;
           }
         }
@@ -446,123 +518,135 @@ __global__ void __launch_bounds__(256)
         const int i = e / n, k = e - (e / n) * n;
         const int p = pr[2 * i], q = pr[2 * i + 1];
         if (q >= n) continue;
-        const double c = cs[2 * i], sn = cs[2 * i + 1];
-        const double akp = A[k * n + p], akq = A[k * n + q];
-        A[k * n + p] = c * akp - sn * akq;
-        A[k * n + q] = sn * akp + c * akq;
-        const double vkp = V[k * n + p], vkq = V[k * n + q];
-        V[k * n + p] = c * vkp - sn * vkq;
-        V[k * n + q] = sn * vkp + c * vkq;
+        const T c = cs[2 * i], sn = cs[2 * i + 1];
+        const T akp = A[k * ld + p], akq = A[k * ld + q];
+        A[k * ld + p] = c * akp - sn * akq;
+        A[k * ld + q] = sn * akp + c * akq;
+        const T vkp = V[k * ld + p], vkq = V[k * ld + q];
+        V[k * ld + p] = c * vkp - sn * vkq;
+        V[k * ld + q] = sn * vkp + c * vkq;
       }
       __syncthreads();
       for (int e = tid; e < np * n; e += nt) {
         const int i = e / n, k = e - (e / n) * n;
         const int p = pr[2 * i], q = pr[2 * i + 1];
         if (q >= n) continue;
-        const double c = cs[2 * i], sn = cs[2 * i + 1];
-        const double apk = A[p * n + k], aqk = A[q * n + k];
-        A[p * n + k] = c * apk - sn * aqk;
-        A[q * n + k] = sn * apk + c * aqk;
+        const T c = cs[2 * i], sn = cs[2 * i + 1];
+        const T apk = A[p * ld + k], aqk = A[q * ld + k];
+        A[p * ld + k] = c * apk - sn * aqk;
+        A[q * ld + k] = sn * apk + c * aqk;
       }
       __syncthreads();
     }
-  }
-  for (int e = tid; e < n * n; e += nt) {
-    Ag[e] = A[e];
-    Vg[e] = V[e];
   }
 }
 
-// Cyclic parallel Jacobi by one warp for n <= 32 (A, V in shared memory,
-// warp-synchronous: no block barriers).  Same rotations and pair schedule as
-// the block version.
-__global__ void __launch_bounds__(32)
-    k_jacobi_warp(int n, double* __restrict__ Ag, double* __restrict__ Vg, int max_sweeps) {
-  __shared__ double A[32 * 32];
-  __shared__ double V[32 * 32];
-  __shared__ double cs[32];
-  __shared__ int pr[32];
-  const int lane = threadIdx.x;
-  const int ne = (n + 1) & ~1;
-  const int np = ne / 2;
-  for (int e = lane; e < n * n; e += 32) {
+// Symmetric eigendecomposition of the n x n (n <= 64) Rayleigh-Ritz matrix with an
+// FP64 result at a fraction of the FP64 work (GB300 runs FP64 at 1/64 of FP32):
+//  1. cyclic Jacobi in FP32 on (A + A')/2 (off-diagonal to 3e-5 of the diagonal, at
+//     most 10 sweeps: FP32 rounding stalls it near 1e-7), one block;
+//  2. two steps of the iterative refinement of Ogita and Aishima ("Iterative
+//     refinement for symmetric eigenvalue decomposition", 2018) in FP64 on the FP32
+//     eigenvectors X:  R = I - X'X,  S = X'AX,  lambda_i = s_ii / (1 - r_ii),
+//     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs and
+//     r_ij / 2 inside clusters (gap <= delta = 2(|S - diag S| + |A| |R|), Frobenius
+//     norms), X <- X + X E.  Each step squares the error, so two steps reach FP64.
+//     The n x n x n FP64 products run one output row per block.
+// Outputs: A <- diag(lambda), V <- eigenvectors (columns, FP64).
+__global__ void __launch_bounds__(1024)
+    k_rr_jacobi32(int n, double* __restrict__ Ag, double* __restrict__ Asym,
+                  double* __restrict__ X) {
+  __shared__ float A32[64 * 65], V32[64 * 65];
+  __shared__ float cs32[64];
+  __shared__ int pr[64];
+  __shared__ double red[64];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e - (e / n) * n;
-    A[e] = 0.5 * (Ag[e] + Ag[j * n + i]);
-    V[e] = (i == j) ? 1.0 : 0.0;
+    const double a = 0.5 * (Ag[e] + Ag[j * n + i]);
+    Asym[e] = a;
+    A32[i * (n + 1) + j] = (float)a;
+    V32[i * (n + 1) + j] = (i == j) ? 1.f : 0.f;
   }
-  __syncwarp();
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int e = lane; e < n * n; e += 32) {
-      const double a = A[e];
-      if (e / n == e % n) dia += a * a;
-      else off += a * a;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dia += __shfl_xor_sync(0xffffffffu, dia, o);
-    }
-    if (off <= 1e-26 * dia || off == 0.0) break;
-    for (int step = 0; step < ne - 1; ++step) {
-      if (lane < np) {
-        const int i = lane;
-        int p, q;
-        if (i == 0) {
-          p = ne - 1;
-          q = step;
-        } else {
-          p = (step + i) % (ne - 1);
-          q = (step - i + (ne - 1)) % (ne - 1);
-        }
-        if (p > q) {
-          const int tt = p;
-          p = q;
-          q = tt;
-        }
-        double c = 1.0, sn = 0.0;
-        if (q < n) {
-          const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            sn = tt * c;
-          }
-        }
-        pr[2 * i] = p;
-        pr[2 * i + 1] = q;
-        cs[2 * i] = c;
-        cs[2 * i + 1] = sn;
-      }
-      __syncwarp();
-      for (int e = lane; e < np * n; e += 32) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pr[2 * i], q = pr[2 * i + 1];
-        if (q >= n) continue;
-        const double c = cs[2 * i], sn = cs[2 * i + 1];
-        const double akp = A[k * n + p], akq = A[k * n + q];
-        A[k * n + p] = c * akp - sn * akq;
-        A[k * n + q] = sn * akp + c * akq;
-        const double vkp = V[k * n + p], vkq = V[k * n + q];
-        V[k * n + p] = c * vkp - sn * vkq;
-        V[k * n + q] = sn * vkp + c * vkq;
-      }
-      __syncwarp();
-      for (int e = lane; e < np * n; e += 32) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pr[2 * i], q = pr[2 * i + 1];
-        if (q >= n) continue;
-        const double c = cs[2 * i], sn = cs[2 * i + 1];
-        const double apk = A[p * n + k], aqk = A[q * n + k];
-        A[p * n + k] = c * apk - sn * aqk;
-        A[q * n + k] = sn * apk + c * aqk;
-      }
-      __syncwarp();
-    }
+  __syncthreads();
+  jacobi_sweeps<float>(n, n + 1, A32, V32, 10, 1e-9, cs32, pr, red, &done);
+  for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * (n + 1) + e % n];
+}
+
+// Row i (block) of C = op(L) M (+ D): op(L) = L' when tl, else L; one thread per column.
+__global__ void k_rr_rowmm(int n, const double* __restrict__ L, int tl, const double* __restrict__ M,
+                           double* __restrict__ C, double diag, double sign) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += (tl ? L[k * n + i] : L[i * n + k]) * M[k * n + j];
+  C[i * n + j] = ((i == j) ? diag : 0.0) + sign * s;
+}
+
+// lambda, the cluster threshold and E (one block).
+__global__ void __launch_bounds__(1024)
+    k_rr_correction(int n, const double* __restrict__ A, const double* __restrict__ R,
+                    const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam) {
+  __shared__ double red[32][3];
+  __shared__ double lm[64];
+  __shared__ double delta;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lm[i] = S[i * n + i] / (1.0 - R[i * n + i]);
+  double so = 0.0, an = 0.0, rn = 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (i != j) so += S[e] * S[e];
+    an += A[e] * A[e];
+    rn += R[e] * R[e];
   }
-  for (int e = lane; e < n * n; e += 32) {
-    Ag[e] = A[e];
-    Vg[e] = V[e];
+  for (int o = 16; o > 0; o >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    an += __shfl_xor_sync(0xffffffffu, an, o);
+    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+  }
+  if ((tid & 31) == 0) {
+    red[tid >> 5][0] = so;
+    red[tid >> 5][1] = an;
+    red[tid >> 5][2] = rn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < nt / 32; ++w) {
+      a += red[w][0];
+      b += red[w][1];
+      c += red[w][2];
+    }
+    delta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    const double gap = lm[j] - lm[i];
+    E[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lm[j] * R[e]) / gap;
+  }
+  for (int i = tid; i < n; i += nt) lam[i] = lm[i];
+}
+
+// X <- X + X E (row i per block; the row is read before it is written).
+__global__ void k_rr_update(int n, double* __restrict__ X, const double* __restrict__ E) {
+  __shared__ double row[64];
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j < n) row[j] = X[i * n + j];
+  __syncthreads();
+  if (j >= n) return;
+  double s = row[j];
+  for (int k = 0; k < n; ++k) s += row[k] * E[k * n + j];
+  X[i * n + j] = s;
+}
+
+__global__ void k_rr_out(int n, const double* __restrict__ lam, const double* __restrict__ X,
+                         double* __restrict__ Ag, double* __restrict__ Vg) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    Ag[e] = (i == j) ? lam[i] : 0.0;
+    Vg[e] = X[e];
   }
 }
 
@@ -651,6 +735,36 @@ __global__ void k_finish(int P, int n, int k, double dv, const double* __restric
   }
 }
 
+// Rayleigh-Ritz eigensolver (FP32 Jacobi + two FP64 refinement steps); scratch
+// holds 5 l^2 + l doubles.
+fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double* scratch) {
+  const size_t nn = (size_t)l * l;
+  double* As = scratch;
+  double* X = As + nn;
+  double* R = X + nn;
+  double* U = R + nn;
+  double* S = U + nn;
+  double* lam = S + nn;
+  double* E = U;  // U is dead once S is formed
+  k_rr_jacobi32<<<1, 1024, 0, ctx->stream>>>(l, A, As, X);
+  FPCA_LAUNCHED(ctx, "jacobi");
+  for (int step = 0; step < 2; ++step) {
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, As, 0, X, U, 0.0, 1.0);   // U = A X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, U, S, 0.0, 1.0);    // S = X' A X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_correction<<<1, 1024, 0, ctx->stream>>>(l, As, R, S, E, lam);
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_update<<<l, 64, 0, ctx->stream>>>(l, X, E);
+    FPCA_LAUNCHED(ctx, "jacobi");
+  }
+  k_rr_out<<<(int)((nn + 255) / 256), 256, 0, ctx->stream>>>(l, lam, X, A, V);
+  FPCA_LAUNCHED(ctx, "jacobi");
+  return FPCA_OK;
+}
+
 template <typename TS>
 fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, TS* Y) {
   const int nb8 = (P + 7) / 8;
@@ -671,12 +785,11 @@ fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, T
 
 template <typename TS>
 fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, double* Rinv,
-                      double* work) {
+                      double* work, double* part) {
   for (int pass = 0; pass < 2; ++pass) {
     TS* src = pass == 0 ? Y : Q;
-    cudaMemsetAsync(G, 0, sizeof(double) * l * l, ctx->stream);
-    k_cross_gram<TS><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, src, src, G);
-    FPCA_LAUNCHED(ctx, "gram");
+    fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
+    if (gs != FPCA_OK) return gs;
     if (l <= 32)
       k_chol_inv_warp<<<1, 32, 0, ctx->stream>>>(l, G, Rinv);
     else
@@ -701,7 +814,8 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
                       3 * WsCarve::round(sizeof(double) * (size_t)l * l) +
                       2 * WsCarve::round(sizeof(double) * (size_t)n * n) +
                       WsCarve::round(sizeof(double) * 2 * n) + WsCarve::round(sizeof(int) * 3 * n) +
-                      4096;
+                      WsCarve::round(sizeof(double) * (size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l) +
+                      WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) + 4096;
   void* ws = fpca_workspace(ctx, need);
   if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
   WsCarve carve(ws);
@@ -719,6 +833,8 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   double* cs = carve.take<double>(2 * n);
   int* pairs = carve.take<int>(2 * n);
   int* order = carve.take<int>(n);
+  double* part = carve.take<double>((size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l);
+  double* rrs = carve.take<double>(5 * (size_t)l * l + l);
 
   cudaMemsetAsync(trace, 0, sizeof(double), ctx->stream);
   k_matrixize<TG, TS><<<dim3((P + 31) / 32, (P + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(
@@ -751,30 +867,21 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   fpca_status s = launch_proj<TS>(ctx, P, l, S, Om, Y);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work);
+    s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part);
     if (s != FPCA_OK) return s;
     s = launch_proj<TS>(ctx, P, l, S, Q, Y);
     if (s != FPCA_OK) return s;
   }
-  s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work);
+  s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part);
   if (s != FPCA_OK) return s;
   s = launch_proj<TS>(ctx, P, l, S, Q, Z);
   if (s != FPCA_OK) return s;
-  cudaMemsetAsync(A, 0, sizeof(double) * l * l, ctx->stream);
-  k_cross_gram<TS><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, Q, Z, A);
-  FPCA_LAUNCHED(ctx, "ritz_gram");
+  s = launch_cross_gram<TS>(ctx, P, l, Q, Z, part, A, "ritz_gram");
+  if (s != FPCA_OK) return s;
   {
-    // (the one-warp variant k_jacobi_warp measured slower on GB300: its
-    // serialised FP64 updates outweigh the saved block barriers)
-    static bool jattr = false;
-    if (!jattr) {
-      cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(2 * 64 * 64 * sizeof(double)));
-      jattr = true;
-    }
-    k_jacobi_small<<<1, 256, 2 * (size_t)l * l * sizeof(double), ctx->stream>>>(l, A, V, 60);
+    fpca_status js = launch_jacobi_rr(ctx, l, A, V, rrs);
+    if (js != FPCA_OK) return js;
   }
-  FPCA_LAUNCHED(ctx, "jacobi");
   k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, A, order);
   FPCA_LAUNCHED(ctx, "eig_order");
   k_ritz_vectors<TS><<<(P + 127) / 128, 128, 0, ctx->stream>>>(P, l, k, Q, V, order, evecs);
@@ -813,7 +920,9 @@ fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, 
 size_t rproj_ws_bytes(int P, int l) {
   return 3 * WsCarve::round(sizeof(float) * (size_t)P * l) +
          5 * WsCarve::round(sizeof(double) * (size_t)l * l) + WsCarve::round(sizeof(double) * 4) +
-         WsCarve::round(sizeof(int) * 3 * (size_t)l) + 2048;
+         WsCarve::round(sizeof(int) * 3 * (size_t)l) +
+         WsCarve::round(sizeof(double) * (size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l) +
+         WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) + 2048;
 }
 
 void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w) {
@@ -827,6 +936,8 @@ void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w) {
   w.V = c.take<double>((size_t)l * l);
   w.trace = c.take<double>(4);
   w.order = c.take<int>(3 * (size_t)l);
+  w.part = c.take<double>((size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l);
+  w.rr = c.take<double>(5 * (size_t)l * l + l);
 }
 
 fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, double dv,
@@ -835,26 +946,19 @@ fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, 
   fpca_status s = op.apply(op.self, omega, w.Y);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work);
+    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part);
     if (s != FPCA_OK) return s;
     s = op.apply(op.self, w.Q, w.Y);
     if (s != FPCA_OK) return s;
   }
-  s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work);
+  s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part);
   if (s != FPCA_OK) return s;
   s = op.apply(op.self, w.Q, w.Z);
   if (s != FPCA_OK) return s;
-  cudaMemsetAsync(w.A, 0, sizeof(double) * l * l, ctx->stream);
-  k_cross_gram<float><<<(P + 63) / 64, 256, 0, ctx->stream>>>(P, l, w.Q, w.Z, w.A);
-  FPCA_LAUNCHED(ctx, "ritz_gram");
-  static bool jattr = false;
-  if (!jattr) {
-    cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * 64 * 64 * sizeof(double)));
-    jattr = true;
-  }
-  k_jacobi_small<<<1, 256, 2 * (size_t)l * l * sizeof(double), ctx->stream>>>(l, w.A, w.V, 60);
-  FPCA_LAUNCHED(ctx, "jacobi");
+  s = launch_cross_gram<float>(ctx, P, l, w.Q, w.Z, w.part, w.A, "ritz_gram");
+  if (s != FPCA_OK) return s;
+  s = launch_jacobi_rr(ctx, l, w.A, w.V, w.rr);
+  if (s != FPCA_OK) return s;
   k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, w.A, w.order);
   FPCA_LAUNCHED(ctx, "eig_order");
   k_ritz_vectors<float><<<(P + 127) / 128, 128, 0, ctx->stream>>>(P, l, k, w.Q, w.V, w.order,

@@ -131,6 +131,8 @@ struct RprojWs {
   float *Y, *Q, *Z;
   double *G, *Rinv, *work, *A, *V, *trace;
   int* order;
+  double* part;  // per-block partial Gram products
+  double* rr;    // Rayleigh-Ritz eigensolver scratch (5 l^2 + l)
 };
 size_t rproj_ws_bytes(int P, int l);
 void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w);

@@ -43,6 +43,7 @@ constexpr int SB = 128, TB = 64, BK = 64;  // S-tile rows, T-tile columns, K chu
 constexpr int CORR_BYTES = SB * TB * 2;    // BF16 corrections of one tile pair
 constexpr int XT_BYTES = 64 * 128;         // up to 64 vectors x 64 nodes, BF16
 constexpr int NEAR_THREADS = 320;          // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int F3_CHUNKS = 8;               // CTAs sharing one S-tile's T-list
 
 struct Geo3 {
   int m[3];
@@ -371,96 +372,108 @@ __device__ __forceinline__ float f3_beta(const PtGeo& s, const PtGeo& t, const f
   return inv;
 }
 
-// corr = e0' (A_p - A_d)^{-1} (A_d beta - z_d) for a near pair, all normalised by
-// k0(s) k0(t): r[j][.] the per-axis diagonal-pair ratios (00,10,01,20,11,02),
-// Q0 / Qs the diagonal moments sum_p K_s K_t [1, u_s] D'_p, dx = t - s.
-__device__ __forceinline__ float f3_corr(const PtGeo& s, const PtGeo& t, const float r[3][6],
-                                         float Q0, const float Qs[3], const int dx[3],
-                                         const float ihM[3], const float beta[7], float inv,
-                                         int& bad) {
-  const float qj[3] = {r[1][0] * r[2][0], r[0][0] * r[2][0], r[0][0] * r[1][0]};
-  float Ad[7][7];
-  Ad[0][0] = r[0][0] * qj[0];
+// corr = e0' (A_p - A_d)^{-1} (A_d beta - z_d) for a near pair (all moments
+// normalised by k0(s) k0(t)).
+//
+// On the diagonal pairs p = q the design row is x = [1, u, u - delta] with
+// u = u_s(p) and delta = (t - s)/hM, i.e. x = T [1, u] for a fixed 7 x 4 matrix T,
+// so A_d = T Md T' and z_d = T qd with the 4 x 4 moment matrix Md of the
+// diagonal pairs (a product measure over the axes: per-axis ratios r00, r10,
+// r20 of sum_p K_s K_t u^a) and qd = sum_p K_s K_t [1, u] D'_p.  With A_p's
+// closed-form inverse (the product-form fit) the Woodbury identity gives
+//     corr = g' (I - Md H)^{-1} c,   g = T' A_p^{-1} e0,   H = T' A_p^{-1} T,
+//     c = Md T' beta - qd,
+// a 4 x 4 solve; g and H have closed forms in the per-axis moments.
+__device__ __forceinline__ float f3_corr(const PtGeo& s, const PtGeo& t, const float r00[3],
+                                         const float r10[3], const float r20[3], float Q0,
+                                         const float Qs[3], const int dx[3], const float ihM[3],
+                                         const float beta[7], float inv, int& bad) {
+  float dl[3], as[3], et[3], ft[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    Ad[0][1 + j] = r[j][1] * qj[j];
-    Ad[0][4 + j] = r[j][2] * qj[j];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (j == k) {
-        Ad[1 + j][1 + k] = r[j][3] * qj[j];
-        Ad[1 + j][4 + k] = r[j][4] * qj[j];
-        Ad[4 + j][4 + k] = r[j][5] * qj[j];
-      } else {
-        const int o = 3 - j - k;
-        Ad[1 + j][1 + k] = r[j][1] * r[k][1] * r[o][0];
-        Ad[1 + j][4 + k] = r[j][1] * r[k][2] * r[o][0];
-        Ad[4 + j][4 + k] = r[j][2] * r[k][2] * r[o][0];
-      }
-    }
+    dl[j] = dx[j] * ihM[j];
+    as[j] = s.mu1[j] * s.ivar[j];
+    et[j] = (t.mu1[j] + dl[j]) * t.ivar[j];
+    ft[j] = t.mu1[j] * t.ivar[j];
   }
-#pragma unroll
-  for (int i = 0; i < 7; ++i)
-#pragma unroll
-    for (int j = 0; j < i; ++j) Ad[i][j] = Ad[j][i];
-  float zd[7];
-  zd[0] = Q0 * inv;
+  // H (arrow-shaped: H00, H0k = Hk0, diagonal Hkk) and g
+  float H00 = 1.f, g0 = 1.f, H0[3], Hd[3], gk[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    zd[1 + j] = Qs[j] * inv;
-    zd[4 + j] = (Qs[j] - dx[j] * ihM[j] * Q0) * inv;   // u_t = u_s + (s - t)/hM
+    H00 = fmaf(s.mu1[j], as[j], fmaf(t.mu1[j] + dl[j], et[j], H00));
+    g0 = fmaf(s.mu1[j], as[j], fmaf(t.mu1[j], et[j], g0));
+    H0[j] = -(as[j] + et[j]);
+    Hd[j] = s.ivar[j] + t.ivar[j];
+    gk[j] = -(as[j] + ft[j]);
   }
-  const float m1[7] = {1.f, s.mu1[0], s.mu1[1], s.mu1[2], t.mu1[0], t.mu1[1], t.mu1[2]};
-  float A[7][7], rhs[7];
+  // Md: w0 = prod r00; Md0j = r10_j prod_{k!=j} r00; Mdjj = r20_j prod_{k!=j} r00;
+  // Mdjk = r10_j r10_k r00_o
+  const float q[3] = {r00[1] * r00[2], r00[0] * r00[2], r00[0] * r00[1]};
+  float Md[4][4];
+  Md[0][0] = r00[0] * q[0];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    float acc = -zd[i];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) acc = fmaf(Ad[i][j], beta[j], acc);
-    rhs[i] = acc;
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      float ap = m1[i] * m1[j];
-      if (i == j && i >= 1) ap += (i <= 3 ? s.var[i - 1] : t.var[i - 4]);
-      A[i][j] = ap - Ad[i][j];
-    }
+  for (int j = 0; j < 3; ++j) {
+    Md[0][1 + j] = Md[1 + j][0] = r10[j] * q[j];
+    Md[1 + j][1 + j] = r20[j] * q[j];
   }
-  // Cholesky A = L L' (lower, in place; il = 1/L_jj); pivots checked against the diagonal
-  float il[7];
+  Md[1][2] = Md[2][1] = r10[0] * r10[1] * r00[2];
+  Md[1][3] = Md[3][1] = r10[0] * r10[2] * r00[1];
+  Md[2][3] = Md[3][2] = r10[1] * r10[2] * r00[0];
+  // c = Md T' beta - qd, T' beta = [b0 - sum delta_j bt_j, bs_j + bt_j]
+  float tb[4];
+  tb[0] = beta[0];
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    float dj = A[j][j];
+  for (int j = 0; j < 3; ++j) {
+    tb[0] = fmaf(-dl[j], beta[4 + j], tb[0]);
+    tb[1 + j] = beta[1 + j] + beta[4 + j];
+  }
+  const float qd[4] = {Q0 * inv, Qs[0] * inv, Qs[1] * inv, Qs[2] * inv};
+  float c[4];
 #pragma unroll
-    for (int k = 0; k < j; ++k) dj = fmaf(-A[j][k], A[j][k], dj);
-    if (!(dj > 1e-4f * A[j][j])) {
+  for (int a = 0; a < 4; ++a) {
+    float v = -qd[a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) v = fmaf(Md[a][b], tb[b], v);
+    c[a] = v;
+  }
+  // M4 = I - Md H
+  float M4[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float v = Md[a][0] * H00;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v = fmaf(Md[a][1 + k], H0[k], v);
+    M4[a][0] = (a == 0 ? 1.f : 0.f) - v;
+#pragma unroll
+    for (int b = 1; b < 4; ++b)
+      M4[a][b] = (a == b ? 1.f : 0.f) - fmaf(Md[a][0], H0[b - 1], Md[a][b] * Hd[b - 1]);
+  }
+  // Gaussian elimination (M4 is the identity minus a small term: no pivoting)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!(fabsf(M4[k][k]) > 1e-4f)) {
       bad = 1;
       return 0.f;
     }
-    il[j] = rsqrtf(dj);
+    const float ip = 1.f / M4[k][k];
 #pragma unroll
-    for (int i = j + 1; i < 7; ++i) {
-      float v = A[i][j];
+    for (int i = k + 1; i < 4; ++i) {
+      const float f = M4[i][k] * ip;
 #pragma unroll
-      for (int k = 0; k < j; ++k) v = fmaf(-A[i][k], A[j][k], v);
-      A[i][j] = v * il[j];
+      for (int j = k + 1; j < 4; ++j) M4[i][j] = fmaf(-f, M4[k][j], M4[i][j]);
+      c[i] = fmaf(-f, c[k], c[i]);
     }
+    M4[k][k] = ip;
   }
-  float yv[7];
+  float y[4];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    float v = rhs[i];
+  for (int i = 3; i >= 0; --i) {
+    float v = c[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) v = fmaf(-A[i][k], yv[k], v);
-    yv[i] = v * il[i];
+    for (int j = i + 1; j < 4; ++j) v = fmaf(-M4[i][j], y[j], v);
+    y[i] = v * M4[i][i];
   }
-#pragma unroll
-  for (int i = 6; i >= 0; --i) {
-    float v = yv[i];
-#pragma unroll
-    for (int k = i + 1; k < 7; ++k) v = fmaf(-A[k][i], yv[k], v);
-    yv[i] = v * il[i];
-  }
-  return yv[0];
+  return fmaf(g0, y[0], fmaf(gk[0], y[1], fmaf(gk[1], y[2], gk[2] * y[3])));
 }
 
 // Diagonal moments by direct sums over the shared window (used for the trace).
@@ -562,9 +575,9 @@ struct NearArgs {
   int l;
   float* Y;                 // P x l (mode 0)
   const int* cta_off;       // mode 0: per-CTA ranges of items
-  const int* items;         // S-tile indices
-  const int* t_off;         // per S-tile ranges of tlist
-  const int* tlist;         // T-tile indices
+  const int* items;         // items x 4: S-tile, first and end index into tlist, output slot
+  const int* tlist;         // T-tile indices, grouped per S-tile
+  float* Ypart;             // mode 0: per-slot partial sums of corr X (128 x lp each)
   const int* pairs;         // mode 1: npairs x 2 (S, T)
   int npairs;
   float* tiles_out;         // mode 1: npairs x 128 x 64
@@ -582,11 +595,11 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
   float* G0 = reinterpret_cast<float*>(smem + OFF_G0);
   float* G1 = reinterpret_cast<float*>(smem + OFF_G1);
   float* PT = reinterpret_cast<float*>(smem + OFF_PT);
-  float* rho0 = PT;              // [16][6]  (s0, t0)
-  float* rho1 = PT + 96;         // [16][6]  (s1, t1)
-  float* rho2 = PT + 192;        // [32][6]  (s2, t2)
-  float* tgeo = PT + 384;        // [3][4][3] 1/k0, mu1, var of the T-box nodes per axis
-  float* tk = PT + 432;          // [3][17]  K(r/hM)
+  float* rho0 = PT;              // [16][3]  (s0, t0): r00, r10, r20
+  float* rho1 = PT + 48;         // [16][3]  (s1, t1)
+  float* rho2 = PT + 96;         // [32][3]  (s2, t2)
+  float* tgeo = PT + 192;        // [3][4][3] 1/k0, mu1, var of the T-box nodes per axis
+  float* tk = PT + 240;          // [3][17]  K(r/hM)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
   uint64_t* full = bars;
   uint64_t* empty = bars + NNSTAGE;
@@ -634,10 +647,10 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
   auto for_pairs = [&](auto&& f) {
     if (apply) {
       for (int it = it_lo; it < it_hi; ++it) {
-        const int S = a.items[it];
-        const int t0 = a.t_off[S], t1 = a.t_off[S + 1];
+        const int S = a.items[4 * it], t0 = a.items[4 * it + 1], t1 = a.items[4 * it + 2];
+        const int slot = a.items[4 * it + 3];
         for (int j = t0; j < t1; ++j)
-          if (!f(S, a.tlist[j], j == t0, j == t1 - 1, 0)) return;
+          if (!f(S, a.tlist[j], j == t0, j == t1 - 1, slot)) return;
       }
     } else {
       for (int pi = blockIdx.x; pi < a.npairs; pi += gridDim.x)
@@ -776,9 +789,9 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
         staged = staged && wlen[k] > 0;
       }
       // pair tables
-      for (int i = et; i < 64 * 6 + 36; i += 256) {
-        if (i < 64 * 6) {
-          const int e = i / 6, qk = i % 6;
+      for (int i = et; i < 64 * 3 + 36; i += 256) {
+        if (i < 64 * 3) {
+          const int e = i / 3, qk = i % 3;
           int ax, sl, tl;
           if (e < 16) { ax = 0; sl = e >> 2; tl = e & 3; }
           else if (e < 32) { ax = 1; sl = (e - 16) >> 2; tl = (e - 16) & 3; }
@@ -786,10 +799,10 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
           const int sv = so[ax] + sl, tv = to[ax] + tl, dd = tv - sv;
           float v = 0.f;
           if (sv < g.m[ax] && tv < g.m[ax] && dd <= 2 * g.T[ax] && -dd <= 2 * g.T[ax])
-            v = a.tab->rho[ax][sv][dd + 2 * F3_TMAX][qk];
+            v = a.tab->rho[ax][sv][dd + 2 * F3_TMAX][qk == 2 ? 3 : qk];
           PT[i] = v;
         } else {
-          const int e = i - 64 * 6, ax = e / 12, tl = (e % 12) / 3, qk = e % 3;
+          const int e = i - 64 * 3, ax = e / 12, tl = (e % 12) / 3, qk = e % 3;
           const int tv = to[ax] + tl;
           float v = qk == 1 ? 0.f : 1.f;
           if (tv < g.m[ax])
@@ -901,16 +914,12 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 3; ++k) near = near && dx[k] <= 2 * g.T[k] && -dx[k] <= 2 * g.T[k];
             if (near) {
-              float rr[3][6];
-              const float* r0 = rho0 + (dr[0] * 4 + tl[0]) * 6;
-              const float* r1 = rho1 + (dr[1] * 4 + tl[1]) * 6;
-              const float* r2 = rho2 + (dr[2] * 4 + tl[2]) * 6;
-#pragma unroll
-              for (int qk = 0; qk < 6; ++qk) {
-                rr[0][qk] = r0[qk];
-                rr[1][qk] = r1[qk];
-                rr[2][qk] = r2[qk];
-              }
+              const float* r0 = rho0 + (dr[0] * 4 + tl[0]) * 3;
+              const float* r1 = rho1 + (dr[1] * 4 + tl[1]) * 3;
+              const float* r2 = rho2 + (dr[2] * 4 + tl[2]) * 3;
+              const float r00[3] = {r0[0], r1[0], r2[0]};
+              const float r10[3] = {r0[1], r1[1], r2[1]};
+              const float r20[3] = {r0[2], r1[2], r2[2]};
               // stage 3, axis 2, from G1
               const int st0 = dr[0] * 4 + tl[0], st1 = dr[1] * 4 + tl[1];
               const int lo = max(max(sc[2], tc[2]) - g.T[2], 0);
@@ -924,7 +933,7 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
                 Qs[1] = fmaf(w, src[2], Qs[1]);
                 Qs[2] = fmaf(w * (p2 - sc[2]) * ihM[2], src[0], Qs[2]);
               }
-              corr = f3_corr(sg, tg, rr, Q0, Qs, dx, ihM, beta, inv, bad);
+              corr = f3_corr(sg, tg, r00, r10, r20, Q0, Qs, dx, ihM, beta, inv, bad);
             }
           }
           const int cj = (ch & 1) * 4 + j;
@@ -968,6 +977,7 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
           }
           ptx::tc_fence_after();
           const int cpw = a.lp / 2;
+          float* yp = a.Ypart + ((long long)slot * SB + r) * a.lp;
           for (int c0 = half * cpw; c0 < (half + 1) * cpw; c0 += 8) {
             uint32_t y[8];
             asm volatile(
@@ -976,12 +986,11 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
                   "=r"(y[6]), "=r"(y[7])
                 : "r"(tmem + lane_base + 448 + c0));
             ptx::tmem_ld_wait();
-            if (s_ok) {
-              float* yr = a.Y + (((long long)sc[0] * g.m[1] + sc[1]) * g.m[2] + sc[2]) * a.l;
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (c0 + j < a.l) yr[c0 + j] += __uint_as_float(y[j]);
-            }
+            float4* d4 = reinterpret_cast<float4*>(yp + c0);
+            d4[0] = make_float4(__uint_as_float(y[0]), __uint_as_float(y[1]), __uint_as_float(y[2]),
+                                __uint_as_float(y[3]));
+            d4[1] = make_float4(__uint_as_float(y[4]), __uint_as_float(y[5]), __uint_as_float(y[6]),
+                                __uint_as_float(y[7]));
           }
           ptx::tc_fence_before();
         }
@@ -994,6 +1003,25 @@ __global__ void __launch_bounds__(NEAR_THREADS, 1)
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 2) ptx::tmem_dealloc(tmem, 512);
+}
+
+// Y += the partial correction sums of the NCHUNK slots of each S-tile, in slot order.
+__global__ void k_f3_yreduce(Geo3 g, int nchunk, int l, int lp, const float* __restrict__ Ypart,
+                             float* __restrict__ Y) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nS = g.nb[0] * g.nb[1] * g.nb[2];
+  if (e >= (long long)nS * SB * l) return;
+  const int c = (int)(e % l);
+  const int r = (int)((e / l) % SB);
+  const int S = (int)(e / ((long long)l * SB));
+  int o[3], d[3];
+  f3_tile_origin_S(g, S, o);
+  f3_srow(r, d);
+  const int c0 = o[0] + d[0], c1 = o[1] + d[1], c2 = o[2] + d[2];
+  if (c0 >= g.m[0] || c1 >= g.m[1] || c2 >= g.m[2]) return;
+  float acc = 0.f;
+  for (int k = 0; k < nchunk; ++k) acc += Ypart[(((long long)S * nchunk + k) * SB + r) * lp + c];
+  Y[(((long long)c0 * g.m[1] + c1) * g.m[2] + c2) * l + c] += acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1119,14 +1147,17 @@ __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __
       const PtGeo sg = f3_geo(tab, c0, c1, c2);
       float beta[7];
       const float inv = f3_beta(sg, sg, Pv, beta);
-      float r[3][6];
-      for (int j = 0; j < 3; ++j)
-        for (int q = 0; q < 6; ++q) r[j][q] = tab->rho[j][sc[j]][2 * F3_TMAX][q];
+      float r00[3], r10[3], r20[3];
+      for (int j = 0; j < 3; ++j) {
+        r00[j] = tab->rho[j][sc[j]][2 * F3_TMAX][0];
+        r10[j] = tab->rho[j][sc[j]][2 * F3_TMAX][1];
+        r20[j] = tab->rho[j][sc[j]][2 * F3_TMAX][3];
+      }
       float Q0, Qs[3];
       f3_tdiag_direct(g, tab, Dp, sc, sc, Q0, Qs);
       const int dx[3] = {0, 0, 0};
       int bad = 0;
-      const float corr = f3_corr(sg, sg, r, Q0, Qs, dx, tab->inv_hM, beta, inv, bad);
+      const float corr = f3_corr(sg, sg, r00, r10, r20, Q0, Qs, dx, tab->inv_hM, beta, inv, bad);
       if (bad) atomicExch(err, DERR_NUMERIC);
       contrib = (double)(beta[0] + corr);
     }
@@ -1243,7 +1274,6 @@ fpca_status ensure_lists(fpca_ctx* ctx, const Geo3& g) {
   if (ctx->f3_lists && std::memcmp(key, ctx->f3_key, sizeof(key)) == 0) return FPCA_OK;
   const int nS = g.nb[0] * g.nb[1] * g.nb[2];
   std::vector<int> t_off(nS + 1, 0), tlist;
-  std::vector<std::pair<int, int>> load;  // (pairs, S)
   for (int S = 0; S < nS; ++S) {
     const int b2 = S % g.nb[2], b1 = (S / g.nb[2]) % g.nb[1], b0 = S / (g.nb[2] * g.nb[1]);
     const int slo[3] = {4 * b0, 4 * b1, 8 * b2};
@@ -1266,31 +1296,37 @@ fpca_status ensure_lists(fpca_ctx* ctx, const Geo3& g) {
       }
       if (ok) tlist.push_back(T);
     }
-    load.push_back({(int)tlist.size() - t_off[S], S});
   }
   t_off[nS] = (int)tlist.size();
-  // longest-first greedy assignment of S-tiles to at most one CTA per SM
-  const int ncta = std::max(1, std::min(nS, ctx->num_sms > 0 ? ctx->num_sms : 148));
-  std::sort(load.begin(), load.end(), [](auto& x, auto& y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
-  std::vector<std::vector<int>> per(ncta);
-  std::vector<long long> acc(ncta, 0);
-  for (auto& it : load) {
-    int best = 0;
-    for (int c = 1; c < ncta; ++c)
-      if (acc[c] < acc[best]) best = c;
-    per[best].push_back(it.second);
-    acc[best] += it.first;
+  // Each S-tile's T-list is cut into F3_CHUNKS nearly equal items; items are dealt
+  // round-robin to the CTAs in S-tile order, so that the chunks of one S-tile run
+  // on different SMs at about the same time and share its operands through L2.
+  std::vector<int> items;
+  for (int S = 0; S < nS; ++S) {
+    const int len = t_off[S + 1] - t_off[S];
+    for (int k = 0; k < F3_CHUNKS; ++k) {
+      const int tb = t_off[S] + (int)((long long)len * k / F3_CHUNKS);
+      const int te = t_off[S] + (int)((long long)len * (k + 1) / F3_CHUNKS);
+      if (te > tb) {
+        items.push_back(S);
+        items.push_back(tb);
+        items.push_back(te);
+        items.push_back(S * F3_CHUNKS + k);
+      }
+    }
   }
-  std::vector<int> cta_off(ncta + 1, 0), items;
+  const int nitems = (int)items.size() / 4;
+  const int ncta = std::max(1, std::min(nitems, ctx->num_sms > 0 ? ctx->num_sms : 148));
+  std::vector<int> cta_off(ncta + 1, 0), order;
   for (int c = 0; c < ncta; ++c) {
-    cta_off[c] = (int)items.size();
-    items.insert(items.end(), per[c].begin(), per[c].end());
+    cta_off[c] = (int)order.size() / 4;
+    for (int it = c; it < nitems; it += ncta)
+      order.insert(order.end(), items.begin() + 4 * it, items.begin() + 4 * it + 4);
   }
-  cta_off[ncta] = (int)items.size();
+  cta_off[ncta] = (int)order.size() / 4;
   std::vector<int> all;
   all.insert(all.end(), cta_off.begin(), cta_off.end());
-  all.insert(all.end(), items.begin(), items.end());
-  all.insert(all.end(), t_off.begin(), t_off.end());
+  all.insert(all.end(), order.begin(), order.end());
   all.insert(all.end(), tlist.begin(), tlist.end());
   const size_t bytes = all.size() * sizeof(int);
   if (bytes > ctx->f3_lists_bytes) {
@@ -1309,7 +1345,7 @@ fpca_status ensure_lists(fpca_ctx* ctx, const Geo3& g) {
     return fpca_fail(ctx, FPCA_E_CUDA, "work list upload");
   std::memcpy(ctx->f3_key, key, sizeof(key));
   ctx->f3_ncta = ncta;
-  ctx->f3_nitems = (int)items.size();
+  ctx->f3_nitems = nitems;
   ctx->f3_npairs = (int)tlist.size();
   return FPCA_OK;
 }
@@ -1331,6 +1367,7 @@ struct F3Work {
   float* Zp;            // nsplit x 128 x n_pad
   __nv_bfloat16* Zb;    // 128 x n_pad
   float* Wf;            // p_pad x 128
+  float* Ypart;         // S-tiles x F3_CHUNKS x 128 x lp
   CUtensorMap mapB, mapX, mapUt, mapRb, mapRbt, mapZb;
   fpca_ctx* ctx;
 };
@@ -1343,6 +1380,7 @@ size_t f3_work_bytes(const Geo3& g, int l, int lp, int nsplit) {
   b += WsCarve::round(2 * 128 * (size_t)g.p_pad) + WsCarve::round(2 * (size_t)lp * g.p_pad);
   b += WsCarve::round(sizeof(float) * (size_t)nsplit * 128 * g.n_pad);
   b += WsCarve::round(2 * 128 * (size_t)g.n_pad) + WsCarve::round(sizeof(float) * (size_t)g.p_pad * 128);
+  b += WsCarve::round(sizeof(float) * (size_t)(g.p_pad / SB) * F3_CHUNKS * SB * lp);
   return b + 4096;
 }
 
@@ -1359,6 +1397,7 @@ void f3_work_carve(WsCarve& c, F3Work& w) {
   w.Zp = c.take<float>((size_t)w.nsplit * 128 * g.n_pad);
   w.Zb = c.take<__nv_bfloat16>(128 * (size_t)g.n_pad);
   w.Wf = c.take<float>((size_t)g.p_pad * 128);
+  w.Ypart = c.take<float>((size_t)(g.p_pad / SB) * F3_CHUNKS * SB * w.lp);
 }
 
 fpca_status conv_launch(fpca_ctx* ctx, const F3Work& w, int axis, int ncols, const float* in,
@@ -1470,12 +1509,14 @@ fpca_status f3_near_launch(fpca_ctx* ctx, const F3Work& w, int mode, float* Y, c
   int grid;
   if (mode == 0) {
     const int* L = static_cast<const int*>(ctx->f3_lists);
-    const int ncta = ctx->f3_ncta, nS = w.g.nb[0] * w.g.nb[1] * w.g.nb[2];
+    const int ncta = ctx->f3_ncta;
     a.cta_off = L;
     a.items = L + ncta + 1;
-    a.t_off = a.items + ctx->f3_nitems;
-    a.tlist = a.t_off + nS + 1;
+    a.tlist = a.items + 4 * ctx->f3_nitems;
+    a.Ypart = w.Ypart;
     grid = ncta;
+    const size_t nS = (size_t)w.g.nb[0] * w.g.nb[1] * w.g.nb[2];
+    cudaMemsetAsync(w.Ypart, 0, sizeof(float) * nS * F3_CHUNKS * SB * w.lp, ctx->stream);
   } else {
     a.pairs = pairs;
     a.npairs = npairs;
@@ -1484,6 +1525,13 @@ fpca_status f3_near_launch(fpca_ctx* ctx, const F3Work& w, int mode, float* Y, c
   }
   k_f3_near<<<grid, NEAR_THREADS, NEAR_SMEM2, ctx->stream>>>(w.mapB, w.mapX, a);
   FPCA_LAUNCHED(ctx, "f3_near");
+  if (mode == 0) {
+    const long long nS = (long long)w.g.nb[0] * w.g.nb[1] * w.g.nb[2];
+    const long long tot = nS * SB * w.l;
+    k_f3_yreduce<<<(int)((tot + 255) / 256), 256, 0, ctx->stream>>>(w.g, F3_CHUNKS, w.l, w.lp,
+                                                                   w.Ypart, Y);
+    FPCA_LAUNCHED(ctx, "f3_yreduce");
+  }
   return FPCA_OK;
 }
 
