@@ -233,87 +233,64 @@ __device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], 
 }
 
 // ---------------------------------------------------------------------------
-// mean smoother, Eq. (2.3): one warp per output node, FP64 window sums
+// mean smoother by separable sums (Eq. 2.3, FP64): the moments
+//   S_e = sum_b K(c_b - x) u^e W_b (|e| <= 2),  T_e = sum_b K u^e V_b (|e| <= 1)
+// and the window count of non-empty bins are products of 1-D kernels, so they
+// are built one axis at a time (the last axis first), each pass applying
+// K u^power (or the box of the window, for the count) along one axis to the
+// arrays of the previous pass; then one (d+1)-dimensional solve per node.
 // ---------------------------------------------------------------------------
-// Lanes stride over the window's bins; the (d+1)(d+2)/2 entries of A, the
-// d+1 entries of r and the non-empty count are reduced across the warp and
-// lane 0 solves.
-template <int DIM>
-__global__ void __launch_bounds__(128)
-    k_smooth_mean(int P, TapParams tp, const double* __restrict__ tab,
-                  const int32_t* __restrict__ cnt, const double* __restrict__ w,
-                  const double* __restrict__ v, double* __restrict__ mu,
-                  uint8_t* __restrict__ status, int T0, int T1, int T2) {
-  constexpr int D = DIM + 1;
-  constexpr int NA = D * (D + 1) / 2;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int p = warp;
+constexpr int MJ_MAX = 16;  // jobs per pass (d = 3: 6, 10, 15)
+
+struct MeanPass {
+  int axis, stride, T, njobs;
+  int src[MJ_MAX], row[MJ_MAX];  // row: 0 K, 1 K u, 2 K u^2, 3 box
+};
+
+__global__ void k_mean_prep(int P, const int32_t* __restrict__ cnt, const double* __restrict__ w,
+                            const double* __restrict__ v, double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  int j[3] = {0, 0, 0};
-  {
-    int rem = p;
-    for (int k = DIM - 1; k >= 0; --k) {
-      j[k] = rem % tp.m[k];
-      rem /= tp.m[k];
-    }
+  out[p] = w[p];
+  out[P + p] = v[p];
+  out[2 * P + p] = cnt[p] > 0 ? 1.0 : 0.0;
+}
+
+__global__ void k_mean_pass(int P, int M, MeanPass mp, const double* __restrict__ tab,
+                            const double* __restrict__ in, double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int c = (p / mp.stride) % M;
+  const int lo = max(-mp.T, -c), hi = min(mp.T, M - 1 - c);
+  const double* wt = tab + (size_t)mp.axis * TROWS * TW + TMAX;
+  for (int j = 0; j < mp.njobs; ++j) {
+    const double* src = in + (size_t)mp.src[j] * P;
+    const double* w = wt + mp.row[j] * TW;
+    double s = 0.0;
+    for (int r = lo; r <= hi; ++r) s = fma(w[r], src[p + r * mp.stride], s);
+    out[(size_t)j * P + p] = s;
   }
-  const int taps[3] = {T0, T1, T2};
-  int lo[3] = {0, 0, 0}, len[3] = {1, 1, 1};
-  for (int k = 0; k < DIM; ++k) {
-    lo[k] = max(-taps[k], -j[k]);
-    len[k] = min(taps[k], tp.m[k] - 1 - j[k]) - lo[k] + 1;
-  }
-  const int nwin = len[0] * len[1] * len[2];
-  double acc[NA + D + 1];
-#pragma unroll
-  for (int a = 0; a < NA + D + 1; ++a) acc[a] = 0.0;
-  for (int e = lane; e < nwin; e += 32) {
-    int off[3];
-    off[2] = lo[2] + e % len[2];
-    off[1] = lo[1] + (e / len[2]) % len[1];
-    off[0] = lo[0] + e / (len[2] * len[1]);
-    int b = 0;
-    double K = 1.0;
-    double z[D];
-    z[0] = 1.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      b = b * tp.m[k] + (j[k] + off[k]);
-      K *= tab[(size_t)k * TROWS * TW + off[k] + TMAX];
-      z[k + 1] = __ddiv_rn((double)off[k], __dmul_rn(tp.h[k], (double)tp.m[k]));
-    }
-    if (K == 0.0) continue;
-    const double kw = K * w[b], kv = K * v[b];
-    int a = 0;
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = r; c < D; ++c) acc[a++] += kw * z[r] * z[c];
-#pragma unroll
-    for (int r = 0; r < D; ++r) acc[NA + r] += kv * z[r];
-    acc[NA + D] += cnt[b] > 0 ? 1.0 : 0.0;
-  }
-#pragma unroll
-  for (int a = 0; a < NA + D + 1; ++a)
-    for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
-  if (lane != 0) return;
+}
+
+struct MeanIdx {
+  int a[16], r[4], n;  // array of each normal-matrix entry, right-hand side entry, count
+};
+
+template <int DIM>
+__global__ void k_mean_solve(int P, const double* __restrict__ mom, MeanIdx ix,
+                             double* __restrict__ mu, uint8_t* __restrict__ status) {
+  constexpr int D = DIM + 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
   double A[D][D], r[D];
-  {
-    int a = 0;
 #pragma unroll
-    for (int rr = 0; rr < D; ++rr)
+  for (int i = 0; i < D; ++i) {
+    r[i] = mom[(size_t)ix.r[i] * P + p];
 #pragma unroll
-      for (int c = rr; c < D; ++c) {
-        A[rr][c] = acc[a];
-        A[c][rr] = acc[a];
-        ++a;
-      }
-#pragma unroll
-    for (int rr = 0; rr < D; ++rr) r[rr] = acc[NA + rr];
+    for (int j = 0; j < D; ++j) A[i][j] = mom[(size_t)ix.a[i * D + j] * P + p];
   }
   uint8_t st;
-  mu[p] = fit_point<D, double>(A, r, acc[NA + D], st);
+  mu[p] = fit_point<D, double>(A, r, mom[(size_t)ix.n * P + p], st);
   if (status) status[p] = st;
 }
 
@@ -1511,20 +1488,96 @@ fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t*
     tp.m[k] = k < g->d ? g->m[k] : 1;
     tp.h[k] = k < g->d ? h[k] : 1.0;
   }
-  double* tab = static_cast<double*>(fpca_workspace(ctx, sizeof(double) * 3 * TROWS * TW));
-  if (!tab) return fpca_fail(ctx, FPCA_E_OOM, "workspace");
-  k_taps<<<g->d, 128, 0, ctx->stream>>>(tp, tab);
-  FPCA_LAUNCHED(ctx, "taps");
   const int T0 = host_taps(tp.h[0], tp.m[0]);
   const int T1 = g->d > 1 ? host_taps(tp.h[1], tp.m[1]) : 0;
   const int T2 = g->d > 2 ? host_taps(tp.h[2], tp.m[2]) : 0;
-  const int nb = (P + 3) / 4;  // 4 warps per block, one warp per node
+  const int taps[3] = {T0, T1, T2};
+  // pass plan: arrays carry (kind, exponents of the processed axes); kind 0 = W
+  // (total degree <= 2), 1 = V (<= 1), 2 = the non-empty indicator (box sums)
+  struct Arr {
+    int kind, deg, e[3];
+  };
+  std::vector<Arr> cur = {{0, 0, {0, 0, 0}}, {1, 0, {0, 0, 0}}, {2, 0, {0, 0, 0}}};
+  std::vector<MeanPass> passes;
+  for (int ax = g->d - 1; ax >= 0; --ax) {
+    MeanPass mp{};
+    mp.axis = ax;
+    int st = 1;
+    for (int k = ax + 1; k < g->d; ++k) st *= g->m[k];
+    mp.stride = st;
+    mp.T = taps[ax];
+    std::vector<Arr> next;
+    for (int i = 0; i < (int)cur.size(); ++i) {
+      const Arr& a = cur[i];
+      if (a.kind == 2) {
+        mp.src[mp.njobs] = i;
+        mp.row[mp.njobs++] = 3;
+        next.push_back(a);
+        continue;
+      }
+      const int maxd = (a.kind == 0 ? 2 : 1) - a.deg;
+      for (int e = 0; e <= maxd; ++e) {
+        mp.src[mp.njobs] = i;
+        mp.row[mp.njobs++] = e;
+        Arr b = a;
+        b.deg += e;
+        b.e[ax] = e;
+        next.push_back(b);
+      }
+    }
+    passes.push_back(mp);
+    cur = next;
+  }
+  // final array index of each normal-matrix entry
+  const int D = g->d + 1;
+  auto find = [&](int kind, const int e[3]) {
+    for (int i = 0; i < (int)cur.size(); ++i)
+      if (cur[i].kind == kind && cur[i].e[0] == e[0] && cur[i].e[1] == e[1] && cur[i].e[2] == e[2])
+        return i;
+    return -1;
+  };
+  MeanIdx ix{};
+  for (int i = 0; i < D; ++i) {
+    for (int j = 0; j < D; ++j) {
+      int e[3] = {0, 0, 0};
+      if (i > 0) e[i - 1] += 1;
+      if (j > 0) e[j - 1] += 1;
+      ix.a[i * D + j] = find(0, e);
+    }
+    int e[3] = {0, 0, 0};
+    if (i > 0) e[i - 1] = 1;
+    ix.r[i] = find(1, e);
+  }
+  {
+    const int e[3] = {0, 0, 0};
+    ix.n = find(2, e);
+  }
+  // workspace: taps table and two ping-pong stacks of MJ_MAX arrays
+  const size_t tb = (sizeof(double) * 3 * TROWS * TW + 255) & ~size_t(255);
+  const size_t stack = (sizeof(double) * (size_t)MJ_MAX * P + 255) & ~size_t(255);
+  char* base = static_cast<char*>(fpca_workspace(ctx, tb + 2 * stack));
+  if (!base) return fpca_fail(ctx, FPCA_E_OOM, "workspace");
+  double* tabw = reinterpret_cast<double*>(base);
+  double* bufA = reinterpret_cast<double*>(base + tb);
+  double* bufB = reinterpret_cast<double*>(base + tb + stack);
+  k_taps<<<g->d, 128, 0, ctx->stream>>>(tp, tabw);
+  FPCA_LAUNCHED(ctx, "taps");
+  const int nb = (P + 255) / 256;
+  k_mean_prep<<<nb, 256, 0, ctx->stream>>>(P, cnt, w, v, bufA);
+  FPCA_LAUNCHED(ctx, "mean_prep");
+  double* in = bufA;
+  double* out = bufB;
+  for (const MeanPass& mp : passes) {
+    k_mean_pass<<<nb, 256, 0, ctx->stream>>>(P, g->m[mp.axis], mp, tabw, in, out);
+    FPCA_LAUNCHED(ctx, "mean_pass");
+    std::swap(in, out);
+  }
   if (g->d == 1)
-    k_smooth_mean<1><<<nb, 128, 0, ctx->stream>>>(P, tp, tab, cnt, w, v, mu, status, T0, T1, T2);
+    k_mean_solve<1><<<nb, 256, 0, ctx->stream>>>(P, in, ix, mu, status);
   else if (g->d == 2)
-    k_smooth_mean<2><<<nb, 128, 0, ctx->stream>>>(P, tp, tab, cnt, w, v, mu, status, T0, T1, T2);
+    k_mean_solve<2><<<nb, 256, 0, ctx->stream>>>(P, in, ix, mu, status);
   else
-    k_smooth_mean<3><<<nb, 128, 0, ctx->stream>>>(P, tp, tab, cnt, w, v, mu, status, T0, T1, T2);
+    k_mean_solve<3><<<nb, 256, 0, ctx->stream>>>(P, in, ix, mu, status);
   FPCA_LAUNCHED(ctx, "smooth_mean");
   return FPCA_OK;
 }
