@@ -769,11 +769,14 @@ template <typename TS>
 fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, TS* Y) {
   const int nb8 = (P + 7) / 8;
   const int ksplit = P >= 2048 ? 8 : 1;
+  const int ksplit2 = P >= 2048 ? 2 : 1;   // (measured best for 4 rows per warp)
   cudaMemsetAsync(Y, 0, sizeof(TS) * (size_t)P * l, ctx->stream);
   if (l <= 8) {
     k_proj<TS, TS, 8, 4><<<dim3((nb8 + 3) / 4, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
+  } else if (l <= 20) {
+    k_proj<TS, TS, 20, 4><<<dim3((nb8 + 3) / 4, ksplit2), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else if (l <= 24) {
-    k_proj<TS, TS, 24, 2><<<dim3((nb8 + 1) / 2, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
+    k_proj<TS, TS, 24, 4><<<dim3((nb8 + 3) / 4, ksplit2), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else if (l <= 64) {
     k_proj<TS, TS, 64, 1><<<dim3(nb8, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
   } else {
@@ -783,10 +786,13 @@ fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, T
   return FPCA_OK;
 }
 
+// Orthonormal basis Q of range(Y) by Cholesky QR: passes = 2 (CholeskyQR2) for the
+// basis of the Rayleigh-Ritz step; one pass between power iterations, where only
+// a well-conditioned basis of the range is needed.
 template <typename TS>
 fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, double* Rinv,
-                      double* work, double* part) {
-  for (int pass = 0; pass < 2; ++pass) {
+                      double* work, double* part, int passes = 2) {
+  for (int pass = 0; pass < passes; ++pass) {
     TS* src = pass == 0 ? Y : Q;
     fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
     if (gs != FPCA_OK) return gs;
@@ -867,7 +873,7 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   fpca_status s = launch_proj<TS>(ctx, P, l, S, Om, Y);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part);
+    s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part, 1);
     if (s != FPCA_OK) return s;
     s = launch_proj<TS>(ctx, P, l, S, Q, Y);
     if (s != FPCA_OK) return s;
@@ -946,7 +952,7 @@ fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, 
   fpca_status s = op.apply(op.self, omega, w.Y);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part);
+    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part, 1);
     if (s != FPCA_OK) return s;
     s = op.apply(op.self, w.Q, w.Y);
     if (s != FPCA_OK) return s;

@@ -173,6 +173,8 @@ __global__ void k_f3_diag(Geo3 g, const float* __restrict__ Rt32, float* __restr
 // order unless IN_PERM (input rows in tile order) / OUT_BF16 (output rows in
 // tile order, BF16).
 // ---------------------------------------------------------------------------
+constexpr int CONV_NB = 8;  // output nodes per thread along the convolution axis
+
 struct ConvArgs {
   Geo3 g;
   const Tab3* tab;
@@ -188,57 +190,84 @@ struct ConvArgs {
 
 template <bool DUAL, bool OUT_BF16>
 __global__ void __launch_bounds__(256) k_f3_conv(ConvArgs a) {
+  // one thread: CONV_NB consecutive nodes of one line along the axis, 4 columns;
+  // every input row of the line segment (plus halo) is loaded once
+  constexpr int NB = CONV_NB;
   const int nc4 = a.ncols >> 2;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)a.g.P * nc4) return;
-  const int x = (int)(idx / nc4), c = (int)(idx - (long long)x * nc4) * 4;
-  const int c2 = x % a.g.m[2], c1 = (x / a.g.m[2]) % a.g.m[1], c0 = x / (a.g.m[2] * a.g.m[1]);
   const int ax = a.axis;
   const int M = ax == 0 ? a.g.m[0] : ax == 1 ? a.g.m[1] : a.g.m[2];
   const int T = ax == 0 ? a.g.T[0] : ax == 1 ? a.g.T[1] : a.g.T[2];
-  const int ca = ax == 0 ? c0 : ax == 1 ? c1 : c2;
   const long long stride = ax == 0 ? (long long)a.g.m[1] * a.g.m[2] : ax == 1 ? a.g.m[2] : 1;
+  const int nseg = (M + NB - 1) / NB;
+  const long long lines = (long long)a.g.P / M;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= lines * nseg * nc4) return;
+  const int c = (int)(idx % nc4) * 4;
+  const long long rest = idx / nc4;
+  const int seg = (int)(rest % nseg);
+  const long long line = rest / nseg;
+  // node of the line at axis coordinate 0
+  const long long base = (line / stride) * stride * M + (line % stride);
+  const int x0 = seg * NB;
   const bool ku = c >= a.ku_lo && c < a.ku_hi;
   const float* tk = ku ? a.tab->tapKu[ax] : a.tab->tapK[ax];
   const float* tu = a.tab->tapKu[ax];
-  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
-  const int lo = max(-T, -ca), hi = min(T, M - 1 - ca);
-  for (int r = lo; r <= hi; ++r) {
-    long long row;
-    if (a.in_perm)
-      row = f3_perm(a.g, c0 + (ax == 0 ? r : 0), c1 + (ax == 1 ? r : 0), c2 + (ax == 2 ? r : 0));
-    else
-      row = x + r * stride;
+  float4 s0[NB], s1[NB];
+#pragma unroll
+  for (int o = 0; o < NB; ++o) {
+    s0[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s1[o] = s0[o];
+  }
+  const int jlo = max(0, x0 - T), jhi = min(M - 1, x0 + NB - 1 + T);
+  for (int jn = jlo; jn <= jhi; ++jn) {
+    const long long node = base + jn * stride;
+    long long row = node;
+    if (a.in_perm) {
+      const int c2 = (int)(node % a.g.m[2]), c1 = (int)((node / a.g.m[2]) % a.g.m[1]);
+      const int c0 = (int)(node / ((long long)a.g.m[2] * a.g.m[1]));
+      row = f3_perm(a.g, c0, c1, c2);
+    }
     const float4 v = *reinterpret_cast<const float4*>(a.in + row * a.ld_in + c);
-    const float w = tk[r + F3_TMAX];
-    s0.x = fmaf(w, v.x, s0.x);
-    s0.y = fmaf(w, v.y, s0.y);
-    s0.z = fmaf(w, v.z, s0.z);
-    s0.w = fmaf(w, v.w, s0.w);
-    if (DUAL) {
-      const float u = tu[r + F3_TMAX];
-      s1.x = fmaf(u, v.x, s1.x);
-      s1.y = fmaf(u, v.y, s1.y);
-      s1.z = fmaf(u, v.z, s1.z);
-      s1.w = fmaf(u, v.w, s1.w);
+#pragma unroll
+    for (int o = 0; o < NB; ++o) {
+      const int r = jn - (x0 + o);   // input minus output offset
+      if (r < -T || r > T) continue;
+      const float w = tk[r + F3_TMAX];
+      s0[o].x = fmaf(w, v.x, s0[o].x);
+      s0[o].y = fmaf(w, v.y, s0[o].y);
+      s0[o].z = fmaf(w, v.z, s0[o].z);
+      s0[o].w = fmaf(w, v.w, s0[o].w);
+      if (DUAL) {
+        const float u = tu[r + F3_TMAX];
+        s1[o].x = fmaf(u, v.x, s1[o].x);
+        s1[o].y = fmaf(u, v.y, s1[o].y);
+        s1[o].z = fmaf(u, v.z, s1[o].z);
+        s1[o].w = fmaf(u, v.w, s1[o].w);
+      }
     }
   }
-  if (OUT_BF16) {
-    const long long row = f3_perm(a.g, c0, c1, c2);
-    __nv_bfloat162* o0 = reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(a.out0) +
-                                                           row * a.ld_out + c);
-    o0[0] = __floats2bfloat162_rn(s0.x, s0.y);
-    o0[1] = __floats2bfloat162_rn(s0.z, s0.w);
-    if (DUAL) {
-      __nv_bfloat162* o1 = reinterpret_cast<__nv_bfloat162*>(
-          static_cast<__nv_bfloat16*>(a.out1) + row * a.ld_out + c);
-      o1[0] = __floats2bfloat162_rn(s1.x, s1.y);
-      o1[1] = __floats2bfloat162_rn(s1.z, s1.w);
+#pragma unroll
+  for (int o = 0; o < NB; ++o) {
+    if (x0 + o >= M) break;
+    const long long x = base + (long long)(x0 + o) * stride;
+    if (OUT_BF16) {
+      const int c2 = (int)(x % a.g.m[2]), c1 = (int)((x / a.g.m[2]) % a.g.m[1]);
+      const int c0 = (int)(x / ((long long)a.g.m[2] * a.g.m[1]));
+      const long long row = f3_perm(a.g, c0, c1, c2);
+      __nv_bfloat162* o0 = reinterpret_cast<__nv_bfloat162*>(
+          static_cast<__nv_bfloat16*>(a.out0) + row * a.ld_out + c);
+      o0[0] = __floats2bfloat162_rn(s0[o].x, s0[o].y);
+      o0[1] = __floats2bfloat162_rn(s0[o].z, s0[o].w);
+      if (DUAL) {
+        __nv_bfloat162* o1 = reinterpret_cast<__nv_bfloat162*>(
+            static_cast<__nv_bfloat16*>(a.out1) + row * a.ld_out + c);
+        o1[0] = __floats2bfloat162_rn(s1[o].x, s1[o].y);
+        o1[1] = __floats2bfloat162_rn(s1[o].z, s1[o].w);
+      }
+    } else {
+      *reinterpret_cast<float4*>(static_cast<float*>(a.out0) + x * a.ld_out + c) = s0[o];
+      if (DUAL) *reinterpret_cast<float4*>(static_cast<float*>(a.out1) + x * a.ld_out + c) = s1[o];
     }
-  } else {
-    *reinterpret_cast<float4*>(static_cast<float*>(a.out0) + (long long)x * a.ld_out + c) = s0;
-    if (DUAL)
-      *reinterpret_cast<float4*>(static_cast<float*>(a.out1) + (long long)x * a.ld_out + c) = s1;
   }
 }
 
@@ -1416,7 +1445,8 @@ fpca_status conv_launch(fpca_ctx* ctx, const F3Work& w, int axis, int ncols, con
   a.ld_out = ld_out;
   a.ku_lo = ku_lo;
   a.ku_hi = ku_hi;
-  const long long total = (long long)w.g.P * (ncols / 4);
+  const int M = w.g.m[axis];
+  const long long total = (long long)(w.g.P / M) * ((M + CONV_NB - 1) / CONV_NB) * (ncols / 4);
   const int nb = (int)((total + 255) / 256);
   if (dual && bf16)
     k_f3_conv<true, true><<<nb, 256, 0, ctx->stream>>>(a);
