@@ -934,13 +934,26 @@ __global__ void __launch_bounds__(NT2, 2)
     }
   }
   if (ep.y) {
+    // y[s, :] += sum over this block's t of Gamma_hat(s, t) Omega[t, :]: warp sums by
+    // shuffles, then one pass over the warps' partials in shared memory
+    // (the warp partials reuse the mid rows: phase 3 reads only the slots)
+    float* yred = mid;  // [NT2 / 32][l]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c = 0; c < ep.l; ++c) {
       float sacc = 0.f;
 #pragma unroll
       for (int j = 0; j < PPT3; ++j)
         if (xts[j] >= 0) sacc = fmaf(gval[j], ep.omega[(long long)xts[j] * ep.l + c], sacc);
-      const double tot = block_sum<NT2>((double)sacc, red);
-      if (threadIdx.x == 0) atomicAdd(ep.y + (long long)xs * ep.l + c, (float)tot);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) yred[warp * ep.l + c] = sacc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ep.l; c += NT2) {
+      float tot = 0.f;
+#pragma unroll
+      for (int w = 0; w < NT2 / 32; ++w) tot += yred[w * ep.l + c];
+      atomicAdd(ep.y + (long long)xs * ep.l + c, tot);
     }
   }
 }

@@ -77,3 +77,26 @@ def test_null_context_is_rejected(libpath):
     lib = binding.load(libpath)
     assert lib.fpca_sync(None) == binding.E_INVALID_ARG
     assert lib.fpca_bin_mean(None, None, None, None, None, None, None) == binding.E_INVALID_ARG
+
+
+def test_cov_factor_bytes_is_a_host_function(libpath):
+    """The factor size needs no device: R/sqrt(n) in FP32 (P x n_pad) and in BF16 twice
+    (n_pad x p_pad, p_pad x n_pad), plus the P node sums, each 256-byte aligned."""
+    from paper_1510_04439_gb300 import binding
+    lib = binding.load(libpath)
+
+    def size(m, n):
+        return int(lib.fpca_cov_factor_bytes(binding.Grid.of(m), n))
+
+    def expect(m, n):
+        P = m[0] * m[1] * m[2]
+        n_pad = (n + 127) // 128 * 128
+        p_pad = 128 * ((m[0] + 3) // 4) * ((m[1] + 3) // 4) * ((m[2] + 7) // 8)
+        total = 0
+        for b in (4 * P * n_pad, 2 * n_pad * p_pad, 2 * p_pad * n_pad, 4 * P):
+            total += (b + 255) // 256 * 256
+        return total
+
+    for m, n in [((32, 32, 32), 2000), ((6, 5, 12), 45), ((8, 8, 8), 1)]:
+        assert size(m, n) == expect(m, n)
+    assert size((16, 16), 10) == 0          # not a 3-D grid

@@ -164,3 +164,45 @@ def test_full_size_rows_and_tiles(ctx):
         assert np.all(st == sm.STATUS_OK)
         errs.append(rel(got[i], ref))
     assert max(errs) < TOL, max(errs)
+
+
+def test_fused_rejects_what_it_does_not_cover(ctx):
+    """Masked data, other dimensions, too many taps, bad tile corners and bad l are
+    refused synchronously with a status, nothing launched."""
+    from paper_1510_04439_gb300 import binding as B
+    D = fs.make_dense(3, (8, 8, 8), 20, [2.0, 1.0], sigma=0.3, mean="exp", seed=3)
+    mu = np.zeros(D.P)
+    nbytes = ctx.cov_factor_bytes(D.m, D.n)
+    fac = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    masked = ctx.dense(dev(D.y.astype(np.float32)), dev(np.ones_like(D.mask, dtype=np.uint8)))
+    with pytest.raises(B.FpcaError) as e:
+        ctx.bin_cov_factor(masked, D.m, dev(mu), fac)
+    assert e.value.status == B.E_UNSUPPORTED
+    full = ctx.dense(dev(D.y.astype(np.float32)))
+    with pytest.raises(B.FpcaError) as e:
+        ctx.bin_cov_factor(full, D.m, dev(mu), fac[: nbytes // 2])
+    assert e.value.status == B.E_INVALID_ARG
+    ctx.bin_cov_factor(full, D.m, dev(mu), fac)
+    X = torch.zeros(D.P, 4, dtype=torch.float32, device=DEV)
+    Y = torch.empty_like(X)
+    with pytest.raises(B.FpcaError) as e:          # 0.9 * 8 = 7.2 -> 7 taps
+        ctx.smooth_cov_apply(D.m, fac, D.n, [0.9, 0.3, 0.3], X, Y)
+    assert e.value.status == B.E_UNSUPPORTED
+    with pytest.raises(B.FpcaError) as e:          # 0.1 * 8 < 1 -> no taps
+        ctx.smooth_cov_apply(D.m, fac, D.n, [0.1, 0.3, 0.3], X, Y)
+    assert e.value.status == B.E_UNSUPPORTED
+    with pytest.raises(B.FpcaError) as e:
+        ctx.smooth_cov_apply((16, 32), fac, D.n, [0.3, 0.3], X, Y)
+    assert e.value.status == B.E_UNSUPPORTED
+    wide = torch.zeros(D.P, 65, dtype=torch.float32, device=DEV)
+    with pytest.raises(B.FpcaError) as e:
+        ctx.smooth_cov_apply(D.m, fac, D.n, [0.3] * 3, wide, torch.empty_like(wide))
+    assert e.value.status == B.E_INVALID_ARG
+    out = torch.empty(1, 128, 64, dtype=torch.float32, device=DEV)
+    with pytest.raises(B.FpcaError) as e:
+        ctx.smooth_cov_tiles(D.m, fac, D.n, [0.3] * 3, [(0, 0, 4, 0, 0, 0)], out)
+    assert e.value.status == B.E_INVALID_ARG
+    # the context stays usable
+    ctx.smooth_cov_apply(D.m, fac, D.n, [0.3] * 3, X, Y)
+    ctx.sync()
+    assert float(host(Y).std()) == 0.0
