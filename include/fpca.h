@@ -285,6 +285,29 @@ fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, const void* y,
                                  const uint8_t* mask, int32_t* cnt, double* w, double* v,
                                  double* v2);
 
+/* ---- noise variance (Eq. 2.5-2.6) ------------------------------------------
+ *
+ * sigma2_hat(t) = b0(t) - Gamma_hat(t, t) - mu_hat(t)^2 at every grid node, where
+ * b0 is the local linear fit of Eq. (2.5) to the squared observations (the mean
+ * smoother of Eq. 2.3 applied to the bins cnt, w, v2 of fpca_bin_mean, bandwidth h,
+ * FP64).  The paper prints "+ mu_hat mu_hat"; since E[Y^2] = Gamma + sigma^2 + mu^2
+ * the mean term is subtracted.  Eq. (2.6) integrates over Omega; the integral is
+ * divided by |Omega| (the mean over the domain nodes) so that a constant sigma^2
+ * is recovered on any domain.
+ *  cnt, w, v2   P mean bins (fpca_bin_mean; v2 = sum Y^2 / N_i).
+ *  h            host, d doubles (h_sigma).
+ *  mu           P doubles, the mean fit.
+ *  gdiag        Gamma_hat(t, t): element p at gdiag + p * gdiag_stride (FP64 or FP32
+ *               per gdiag_prec) -- the diagonal of a P x P surface (stride P + 1) or
+ *               a length-P vector (stride 1).
+ *  domain       P int32 (e.g. the mean-bin counts; > 0 = inside Omega) or NULL (all).
+ *  sigma2_t     P doubles out (NaN where the b0 fit is EMPTY); status P uint8 out
+ *               (FPCA_PT_*) or NULL; sigma2 one double out (the average) or NULL. */
+fpca_status fpca_sigma2(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt, const double* w,
+                        const double* v2, const double* h, const double* mu, const void* gdiag,
+                        int gdiag_prec, long long gdiag_stride, const int32_t* domain,
+                        double* sigma2_t, uint8_t* status, double* sigma2);
+
 /* ---- d = 3: covariance smoothing fused into its projection ----------------
  *
  * For a 32 x 32 x 32 grid the covariance grid has P^2 = 1.07e9 points; these
@@ -337,6 +360,12 @@ fpca_status fpca_smooth_cov_apply(fpca_ctx* ctx, const fpca_grid* grid, const vo
 fpca_status fpca_smooth_cov_tiles(fpca_ctx* ctx, const fpca_grid* grid, const void* factor,
                                   int n, const double* h, int ntiles, const int32_t* tiles,
                                   float* out);
+
+/* Gamma_hat(t, t) at every node (P doubles, device) from the factored bins at
+ * bandwidth h: the diagonal of the surface that fpca_smooth_cov_apply applies,
+ * e.g. for fpca_sigma2 (stride 1). */
+fpca_status fpca_smooth_cov_diag(fpca_ctx* ctx, const fpca_grid* grid, const void* factor, int n,
+                                 const double* h, double* diag);
 
 /* Random projection of Section 3.4 on the fused operator: Y = Gamma_hat Omega,
  * power_iters re-orthonormalised power steps, Rayleigh-Ritz on l columns in

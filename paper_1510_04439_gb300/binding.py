@@ -29,7 +29,8 @@ SYMBOLS = (
     "fpca_smooth_cov_project", "fpca_rproj_eig", "fpca_profile_enable", "fpca_profile_count",
     "fpca_profile_entry", "fpca_bin_mean_static", "fpca_bw_param_count", "fpca_bw_predict",
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
-    "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor",
+    "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
+    "fpca_smooth_cov_diag",
 )
 
 
@@ -121,6 +122,9 @@ def load(path=LIB_PATH):
                                           ctypes.POINTER(ctypes.c_int32), vp]
     lib.fpca_rproj_eig_factor.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp, i32, i32,
                                           i32, vp, vp, vp]
+    lib.fpca_smooth_cov_diag.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp]
+    lib.fpca_sigma2.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp, i32,
+                                ctypes.c_longlong, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
     lib.fpca_profile_count.argtypes = [vp]
     lib.fpca_profile_entry.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p),
@@ -214,6 +218,17 @@ class Context:
                                               _ptr(cnt), _ptr(w), _ptr(v), _ptr(v2),
                                               ctypes.byref(bins), _ptr(feat)))
 
+    # ---- noise variance ------------------------------------------------------
+    def sigma2(self, m, cnt, w, v2, h, mu, gdiag, gdiag_stride, sigma2_t, status=None,
+               sigma2=None, domain=None):
+        """Eq. (2.5)-(2.6); gdiag a device tensor whose element p * gdiag_stride is
+        Gamma_hat(t_p, t_p) (e.g. a P x P surface with stride P + 1)."""
+        gp = F64 if gdiag.dtype.itemsize == 8 else F32
+        self._check(self.lib.fpca_sigma2(self.h, ctypes.byref(Grid.of(m)), _ptr(cnt), _ptr(w),
+                                         _ptr(v2), _doubles(h), _ptr(mu), _ptr(gdiag), gp,
+                                         int(gdiag_stride), _ptr(domain), _ptr(sigma2_t),
+                                         _ptr(status), _ptr(sigma2)))
+
     # ---- d = 3 fused smoother ------------------------------------------------
     def cov_factor_bytes(self, m, n):
         return int(self.lib.fpca_cov_factor_bytes(ctypes.byref(Grid.of(m)), int(n)))
@@ -236,6 +251,10 @@ class Context:
         self._check(self.lib.fpca_smooth_cov_tiles(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),
                                                    int(n), _doubles(h), int(tl.shape[0]), arr,
                                                    _ptr(out)))
+
+    def smooth_cov_diag(self, m, factor, n, h, diag):
+        self._check(self.lib.fpca_smooth_cov_diag(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),
+                                                  int(n), _doubles(h), _ptr(diag)))
 
     def rproj_eig_factor(self, m, factor, n, h, omega, k, evals, evecs, fve=None, power_iters=0):
         self._check(self.lib.fpca_rproj_eig_factor(self.h, ctypes.byref(Grid.of(m)), _ptr(factor),

@@ -418,4 +418,22 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
                        evals, evecs, fve);
 }
 
+fpca_status fpca_sigma2(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt, const double* w,
+                        const double* v2, const double* h, const double* mu, const void* gdiag,
+                        int gdiag_prec, long long gdiag_stride, const int32_t* domain,
+                        double* sigma2_t, uint8_t* status, double* sigma2) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
+  if (!valid_grid(ctx, grid, 1 << 20)) return FPCA_E_INVALID_ARG;
+  if (!cnt || !w || !v2 || !h || !mu || !gdiag || !sigma2_t)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "cnt, w, v2, h, mu, gdiag and sigma2_t are required");
+  if (gdiag_prec != FPCA_F64 && gdiag_prec != FPCA_F32)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "gdiag_prec must be FPCA_F64 or FPCA_F32");
+  if (gdiag_stride < 1) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "gdiag_stride must be >= 1");
+  for (int k = 0; k < grid->d; ++k)
+    if (!(h[k] > 0.0)) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "h[%d] must be positive", k);
+  return launch_sigma2(ctx, grid, cnt, w, v2, h, mu, gdiag, gdiag_prec, gdiag_stride, domain,
+                       sigma2_t, status, sigma2);
+}
+
 }  // extern "C"

@@ -118,6 +118,10 @@ fpca_status launch_gram_tc(fpca_ctx* ctx, int P, int Kpad, const uint16_t* ops, 
 fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt,
                                const double* w, const double* v, const double* h, double* mu,
                                uint8_t* status);
+fpca_status launch_sigma2(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const double* w,
+                          const double* v2, const double* h, const double* mu, const void* gdiag,
+                          int gprec, long long gstride, const int32_t* domain, double* sig_t,
+                          uint8_t* status, double* sigma2);
 fpca_status smooth_cov_run(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins* bins,
                            const double* h, int nh, int prec, const double* mu_raw,
                            const float* omega, int l, void* gamma, uint8_t* status, float* y,

@@ -1149,7 +1149,8 @@ __global__ void __launch_bounds__(128, 1)
 
 // trace of Gamma_hat: sum_s Gamma_hat(s, s) from the seven products at (s, s)
 __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __restrict__ Dp,
-                           const __nv_bfloat16* __restrict__ Bpl, double* trace, int* err) {
+                           const __nv_bfloat16* __restrict__ Bpl, double* trace, double* diag,
+                           int* err) {
   const int x = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   double contrib = 0.0;
@@ -1189,9 +1190,10 @@ __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __
       const float corr = f3_corr(sg, sg, r00, r10, r20, Q0, Qs, dx, tab->inv_hM, beta, inv, bad);
       if (bad) atomicExch(err, DERR_NUMERIC);
       contrib = (double)(beta[0] + corr);
+      if (diag) diag[x] = contrib;
     }
   }
-  if (lane == 0 && x < g.P) atomicAdd(trace, contrib);
+  if (trace && lane == 0 && x < g.P) atomicAdd(trace, contrib);
 }
 
 // ---------------------------------------------------------------------------
@@ -1767,11 +1769,32 @@ fpca_status fpca_rproj_eig_factor(fpca_ctx* ctx, const fpca_grid* grid, const vo
   s = f3_prepare(ctx, w, factor, h);
   if (s != FPCA_OK) return s;
   cudaMemsetAsync(rw.trace, 0, sizeof(double), ctx->stream);
-  k_f3_trace<<<(P + 7) / 8, 256, 0, ctx->stream>>>(w.g, w.tab, w.Dp, w.Bpl, rw.trace, ctx->d_err);
+  k_f3_trace<<<(P + 7) / 8, 256, 0, ctx->stream>>>(w.g, w.tab, w.Dp, w.Bpl, rw.trace, nullptr,
+                                                    ctx->d_err);
   FPCA_LAUNCHED(ctx, "f3_trace");
   RprojOp op{f3_apply_cb, &w};
   return rproj_operator(ctx, P, l, k, power_iters, 1.0 / (double)P, omega, op, rw, evals, evecs,
                         fve);
+}
+
+fpca_status fpca_smooth_cov_diag(fpca_ctx* ctx, const fpca_grid* grid, const void* factor, int n,
+                                 const double* h, double* diag) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
+  if (!diag) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "diag is required");
+  F3Work w{};
+  void* ws = nullptr;
+  fpca_status s = f3_setup(ctx, grid, factor, n, h, 16, 0, w, &ws);
+  if (s != FPCA_OK) return s;
+  WsCarve c(ws);
+  f3_work_carve(c, w);
+  s = f3_prepare(ctx, w, factor, h);
+  if (s != FPCA_OK) return s;
+  const int P = w.g.P;
+  k_f3_trace<<<(P + 7) / 8, 256, 0, ctx->stream>>>(w.g, w.tab, w.Dp, w.Bpl, nullptr, diag,
+                                                    ctx->d_err);
+  FPCA_LAUNCHED(ctx, "f3_diag_values");
+  return FPCA_OK;
 }
 
 }  // extern "C"

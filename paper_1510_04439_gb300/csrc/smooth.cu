@@ -294,6 +294,51 @@ __global__ void k_mean_solve(int P, const double* __restrict__ mom, MeanIdx ix,
   if (status) status[p] = st;
 }
 
+// sigma2(t) = b0(t) - Gamma_hat(t, t) - mu_hat(t)^2 in place of b0 (Eq. 2.5 with the
+// sign reading of the mean term); EMPTY fits give NaN.
+template <typename TG>
+__global__ void k_sigma2_curve(int P, const double* __restrict__ mu, const TG* __restrict__ gd,
+                               long long gstride, const uint8_t* __restrict__ st,
+                               double* __restrict__ sig) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double b0 = sig[p];
+  const bool empty = st ? st[p] == FPCA_PT_EMPTY : isnan(b0);
+  sig[p] = empty ? __longlong_as_double(0x7ff8000000000000ll)
+                 : b0 - (double)gd[(long long)p * gstride] - mu[p] * mu[p];
+}
+
+// Eq. (2.6): the mean of sigma2(t) over the domain nodes with a value (one block).
+__global__ void k_sigma2_mean(int P, const double* __restrict__ sig, const int32_t* __restrict__ dom,
+                              double* __restrict__ out) {
+  __shared__ double rs[32], rc[32];
+  double s = 0.0, c = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const double v = sig[p];
+    if ((!dom || dom[p] > 0) && !isnan(v)) {
+      s += v;
+      c += 1.0;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rs[threadIdx.x >> 5] = s;
+    rc[threadIdx.x >> 5] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ts += rs[w];
+      tc += rc[w];
+    }
+    out[0] = tc > 0.0 ? ts / tc : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // covariance: moment bookkeeping
 // ---------------------------------------------------------------------------
@@ -1592,6 +1637,29 @@ fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t*
   else
     k_mean_solve<3><<<nb, 256, 0, ctx->stream>>>(P, in, ix, mu, status);
   FPCA_LAUNCHED(ctx, "smooth_mean");
+  return FPCA_OK;
+}
+
+fpca_status launch_sigma2(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const double* w,
+                          const double* v2, const double* h, const double* mu, const void* gdiag,
+                          int gprec, long long gstride, const int32_t* domain, double* sig_t,
+                          uint8_t* status, double* sigma2) {
+  // b0 of Eq. (2.5): the mean smoother on the bins of Y^2, written into sig_t
+  fpca_status s = launch_smooth_mean(ctx, g, cnt, w, v2, h, sig_t, status);
+  if (s != FPCA_OK) return s;
+  const int P = grid_P(g);
+  const int nb = (P + 255) / 256;
+  if (gprec == FPCA_F64)
+    k_sigma2_curve<double><<<nb, 256, 0, ctx->stream>>>(P, mu, static_cast<const double*>(gdiag),
+                                                       gstride, status, sig_t);
+  else
+    k_sigma2_curve<float><<<nb, 256, 0, ctx->stream>>>(P, mu, static_cast<const float*>(gdiag),
+                                                      gstride, status, sig_t);
+  FPCA_LAUNCHED(ctx, "sigma2_curve");
+  if (sigma2) {
+    k_sigma2_mean<<<1, 1024, 0, ctx->stream>>>(P, sig_t, domain, sigma2);
+    FPCA_LAUNCHED(ctx, "sigma2_mean");
+  }
   return FPCA_OK;
 }
 
