@@ -15,7 +15,8 @@ Modules
   block     the covariance smoother at chosen output pairs (rows, tiles) from
             the data, for grids whose P x P bins are too large to hold
   variance  the noise variance of Eq. (2.5)-(2.6)
+  scores    PACE scores (Eq. 2.7), scores by integration, reconstruction
   cv        cross-validation of the covariance bandwidth (Section 3.3)
   mlp       the bandwidth-proposal network (forward, manual backward, AdamW)
 """
-from . import smoother, eigen, cv, block, variance  # noqa: F401
+from . import smoother, eigen, cv, block, variance, scores  # noqa: F401
