@@ -140,6 +140,50 @@ def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush, shape=(32, 2000)):
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
 
 
+def bench_scores(torch, np, B, ctx, D, bufs, y, mask, stream, flush, reps=5):
+    """Noise variance (Eq. 2.5-2.6), PACE scores (Eq. 2.7), scores by integration
+    and reconstruction on the dense workload's own fit (mu, Gamma_hat diagonal,
+    the k eigenpairs), each timed per launch with the profiler."""
+    P, n = D.P, D.n
+    dev = y.device
+    sig_t = torch.empty(P, dtype=torch.float64, device=dev)
+    s2 = torch.empty(1, dtype=torch.float64, device=dev)
+    pace = torch.empty((n, K_EIG), dtype=torch.float64, device=dev)
+    integ = torch.empty((n, K_EIG), dtype=torch.float64, device=dev)
+    xhat = torch.empty((n, P), dtype=torch.float32, device=dev)
+    data = ctx.dense(y, mask)
+
+    def run():
+        ctx.sigma2(D.m, bufs.cnt, bufs.w, bufs.v2, H, bufs.mu, bufs.gamma.reshape(-1), P + 1,
+                   sig_t, None, s2, domain=bufs.cnt)
+        ctx.scores_pace(data, D.m, bufs.mu, bufs.evals, bufs.evecs, K_EIG, s2, pace)
+        ctx.scores_integral(data, D.m, bufs.mu, bufs.evecs, K_EIG, integ)
+        ctx.reconstruct(D.m, bufs.mu, bufs.evecs, K_EIG, pace, n, xhat)
+
+    run()
+    ctx.sync()
+    ctx.profile(True)
+    for _ in range(reps):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.sync()
+    per = {k: v[0] / v[1] for k, v in prof.items()}
+    # algorithmic bytes: y (FP32) and mask read once; xhat written once (FP32)
+    yb = n * P * (y.element_size() + mask.element_size())
+    out = {"workload": f"dense_2d_disk_64x64_n{n}_L{K_EIG}", "sigma2": float(s2.item()),
+           "sigma2_true": D.sigma ** 2, "ms_per_launch": per}
+    if "scores_integral" in per:
+        out["scores_integral_gbs"] = yb / (per["scores_integral"] * 1e-3) / 1e9
+    if "scores_pace" in per:
+        out["scores_pace_gbs"] = yb / (per["scores_pace"] * 1e-3) / 1e9
+    if "reconstruct" in per:
+        out["reconstruct_gbs"] = n * P * 4 / (per["reconstruct"] * 1e-3) / 1e9
+    return out
+
+
 def measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -541,6 +585,11 @@ def main():
         f3x = bench_fused3(torch, np, fs, B, ctx, dev, stream, flush,
                            tuple(int(x) for x in args.fused3_shape.split(",")))
 
+    # ---- noise variance, scores and reconstruction (reported beside) ----
+    scx = None
+    if not args.no_extras:
+        scx = bench_scores(torch, np, B, ctx, D, bufs, y, mask, stream, flush)
+
     # ---- learned bandwidths against the CV grid (reported beside) ----
     bwx = None
     if not args.no_extras and rank == 0:
@@ -584,6 +633,7 @@ def main():
             "variant_uncompensated": variant,
             "cv_grid": cvx,
             "fused_3d": f3x,
+            "scores": scx,
             "learned_bandwidth": bwx,
             "cpu_baseline": cpu,
             "clocks": clk,

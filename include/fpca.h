@@ -308,6 +308,42 @@ fpca_status fpca_sigma2(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt
                         int gdiag_prec, long long gdiag_stride, const int32_t* domain,
                         double* sigma2_t, uint8_t* status, double* sigma2);
 
+/* ---- principal component scores (Section 2.1, Eq. 2.7) ----------------------
+ *
+ * Functions known on the grid (mu, phi_l) are read at an observation through the
+ * bin that holds it (the binning of Section 3.2).  evals (L doubles) and evecs
+ * (P x L column-major, phi_l at evecs + l * P, the normalisation of
+ * fpca_rproj_eig: sum_p phi_l(p)^2 / P = 1) are device arrays; 1 <= L <= 16.
+ * scores is n x L row-major device doubles, overwritten.
+ *
+ * fpca_scores_pace: the conditional expectation of Eq. (2.7),
+ *   A_i = Lambda Phi_i' (Phi_i Lambda Phi_i' + sigma^2 I)^{-1} (Y_i - mu(t_i)),
+ * evaluated through the push-through identity as the L x L system
+ *   (sigma^2 Lambda^{-1} + Phi_i' Phi_i) A_i = Phi_i' (Y_i - mu(t_i))
+ * (FP64 accumulation, FP64 Cholesky).  Gridded data (mask or all nodes) and
+ * scattered data (offs, t) are both accepted.  A subject without observations
+ * gets A_i = 0 (the prior mean).  sigma2 is ONE device double (e.g. the output
+ * of fpca_sigma2, so no host round trip separates the two calls); it must be
+ * >= 0 and every evals[l] > 0 (with sigma2 == 0 the system is singular for a
+ * subject with fewer than L observations).  A negative or NaN sigma2, a
+ * non-positive evals[l] or a non-positive pivot writes NaN scores for the
+ * subject and makes fpca_sync() return FPCA_E_NUMERIC.
+ *
+ * fpca_scores_integral: the integral of (Y_i - mu) phi_l over Omega as the
+ * Riemann sum over the subject's observed nodes, cell volume dV = 1/P (gridded
+ * data only; FP64).
+ *
+ * fpca_reconstruct: X_i(t_p) = mu(t_p) + sum_l A_il phi_l(t_p) at every node,
+ * n x P row-major FP32 out (FP64 arithmetic). */
+fpca_status fpca_scores_pace(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                             const double* mu, const double* evals, const double* evecs, int L,
+                             const double* sigma2, double* scores);
+fpca_status fpca_scores_integral(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                                 const double* mu, const double* evecs, int L, double* scores);
+fpca_status fpca_reconstruct(fpca_ctx* ctx, const fpca_grid* grid, const double* mu,
+                             const double* evecs, int L, const double* scores, int n,
+                             float* xhat);
+
 /* ---- d = 3: covariance smoothing fused into its projection ----------------
  *
  * For a 32 x 32 x 32 grid the covariance grid has P^2 = 1.07e9 points; these

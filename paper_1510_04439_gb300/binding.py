@@ -30,7 +30,7 @@ SYMBOLS = (
     "fpca_profile_entry", "fpca_bin_mean_static", "fpca_bw_param_count", "fpca_bw_predict",
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
-    "fpca_smooth_cov_diag",
+    "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
 )
 
 
@@ -123,6 +123,11 @@ def load(path=LIB_PATH):
     lib.fpca_rproj_eig_factor.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp, i32, i32,
                                           i32, vp, vp, vp]
     lib.fpca_smooth_cov_diag.argtypes = [vp, ctypes.POINTER(Grid), vp, i32, dbl_p, vp]
+    lib.fpca_scores_pace.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp,
+                                     i32, vp, vp]
+    lib.fpca_scores_integral.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp,
+                                         i32, vp]
+    lib.fpca_reconstruct.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i32, vp, i32, vp]
     lib.fpca_sigma2.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp, i32,
                                 ctypes.c_longlong, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
@@ -228,6 +233,24 @@ class Context:
                                          _ptr(v2), _doubles(h), _ptr(mu), _ptr(gdiag), gp,
                                          int(gdiag_stride), _ptr(domain), _ptr(sigma2_t),
                                          _ptr(status), _ptr(sigma2)))
+
+    # ---- scores and reconstruction -------------------------------------------
+    def scores_pace(self, data, m, mu, evals, evecs, L, sigma2, scores):
+        """Eq. (2.7); evecs P x k column-major (its first L columns are used);
+        sigma2 a one-element device tensor of float64."""
+        self._check(self.lib.fpca_scores_pace(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                              _ptr(mu), _ptr(evals), _ptr(evecs), int(L),
+                                              _ptr(sigma2), _ptr(scores)))
+
+    def scores_integral(self, data, m, mu, evecs, L, scores):
+        self._check(self.lib.fpca_scores_integral(self.h, ctypes.byref(data),
+                                                  ctypes.byref(Grid.of(m)), _ptr(mu), _ptr(evecs),
+                                                  int(L), _ptr(scores)))
+
+    def reconstruct(self, m, mu, evecs, L, scores, n, xhat):
+        self._check(self.lib.fpca_reconstruct(self.h, ctypes.byref(Grid.of(m)), _ptr(mu),
+                                              _ptr(evecs), int(L), _ptr(scores), int(n),
+                                              _ptr(xhat)))
 
     # ---- d = 3 fused smoother ------------------------------------------------
     def cov_factor_bytes(self, m, n):

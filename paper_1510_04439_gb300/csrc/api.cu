@@ -258,7 +258,7 @@ fpca_status fpca_sync(fpca_ctx* ctx) {
     if (herr == DERR_TIMEOUT)
       return fpca_fail(ctx, FPCA_E_TIMEOUT, "a device-side bounded wait ran out");
     if (herr == DERR_NUMERIC)
-      return fpca_fail(ctx, FPCA_E_NUMERIC, "an ill-conditioned local system in the fused d = 3 smoother");
+      return fpca_fail(ctx, FPCA_E_NUMERIC, "an ill-conditioned local system (fused d = 3 smoother) or a non-positive pivot (PACE scores)");
     return fpca_fail(ctx, FPCA_E_CUDA, "device-side check failed (code %d)", herr);
   }
   return FPCA_OK;
