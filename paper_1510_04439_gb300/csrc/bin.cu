@@ -47,10 +47,10 @@ __global__ void k_subject_counts(int n, int P, const uint8_t* __restrict__ mask,
   }
 }
 
-// Dense mean bins: a block covers 32 nodes; its 8 thread rows take every
-// 8th subject, and the 8 partial sums are added in a fixed order
-// (deterministic).  Weights 1/N_i.
-constexpr int MB_SLICES = 8;
+// Dense mean bins: a block covers 32 nodes; its MB_SLICES thread rows take
+// every MB_SLICES-th subject, and the partial sums are added by a fixed
+// pairwise tree (deterministic).  Weights 1/N_i.
+constexpr int MB_SLICES = 32;  // subject slices per block: short FP64 add chains
 __global__ void __launch_bounds__(32 * MB_SLICES)
     k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y_prec,
                      const uint8_t* __restrict__ mask, const int32_t* __restrict__ Ni,
@@ -58,13 +58,13 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
                      double* __restrict__ v2) {
   __shared__ double ps[3][MB_SLICES][32];
   __shared__ int pc[MB_SLICES][32];
-  __shared__ double winv[256];
+  __shared__ double winv[32 * MB_SLICES];
   const int p = blockIdx.x * 32 + threadIdx.x;
   int c = 0;
   double sw = 0.0, sv = 0.0, sv2 = 0.0;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int i0 = 0; i0 < n; i0 += 256) {
-    // 1/N_i for the next 256 subjects, one division per subject
+  for (int i0 = 0; i0 < n; i0 += 32 * MB_SLICES) {
+    // 1/N_i for the next 32 * MB_SLICES subjects, one division per subject
     __syncthreads();
     {
       const int i = i0 + tid;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
     }
     __syncthreads();
     if (p < P) {
-      const int iend = min(n, i0 + 256);
+      const int iend = min(n, i0 + 32 * MB_SLICES);
       for (int i = i0 + threadIdx.y; i < iend; i += MB_SLICES) {
         const size_t idx = (size_t)i * P + p;
         if (mask && !mask[idx]) continue;
@@ -92,19 +92,20 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
   ps[2][threadIdx.y][threadIdx.x] = sv2;
   pc[threadIdx.y][threadIdx.x] = c;
   __syncthreads();
-  if (threadIdx.y == 0 && p < P) {
-    int ct = 0;
-    double tw = 0.0, tv = 0.0, tv2 = 0.0;
-    for (int k = 0; k < MB_SLICES; ++k) {
-      ct += pc[k][threadIdx.x];
-      tw += ps[0][k][threadIdx.x];
-      tv += ps[1][k][threadIdx.x];
-      tv2 += ps[2][k][threadIdx.x];
+  // pairwise tree over the slices (fixed order; FP64 adds have a long latency)
+  for (int h = MB_SLICES / 2; h >= 1; h >>= 1) {
+    if (threadIdx.y < h) {
+      pc[threadIdx.y][threadIdx.x] += pc[threadIdx.y + h][threadIdx.x];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ps[a][threadIdx.y][threadIdx.x] += ps[a][threadIdx.y + h][threadIdx.x];
     }
-    cnt[p] = ct;
-    w[p] = tw;
-    v[p] = tv;
-    if (v2) v2[p] = tv2;
+    __syncthreads();
+  }
+  if (threadIdx.y == 0 && p < P) {
+    cnt[p] = pc[0][threadIdx.x];
+    w[p] = ps[0][0][threadIdx.x];
+    v[p] = ps[1][0][threadIdx.x];
+    if (v2) v2[p] = ps[2][0][threadIdx.x];
   }
 }
 

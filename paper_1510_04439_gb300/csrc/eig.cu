@@ -25,7 +25,9 @@ template <typename TG, typename TS>
 __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __restrict__ dom,
                             TS* __restrict__ S, double* __restrict__ trace) {
   __shared__ TS tile[32][33];
+  __shared__ double dsum;  // this block's part of the trace (diagonal blocks only)
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  if (threadIdx.x == 0 && threadIdx.y == 0) dsum = 0.0;
   // transposed tile: rows q in [bx, bx+32), columns p in [by, by+32)
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int q = bx + r, p = by + threadIdx.x;
@@ -45,9 +47,12 @@ __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __re
       TS sv = TS(0.5) * (g + tile[threadIdx.x][r]);
       if (dom && (dom[p] <= 0 || dom[q] <= 0)) sv = TS(0);
       S[(long long)p * P + q] = sv;
-      if (p == q) atomicAdd(trace, (double)sv);
+      if (p == q) atomicAdd(&dsum, (double)sv);
     }
   }
+  // one global atomic per diagonal block instead of one per diagonal entry
+  __syncthreads();
+  if (bx == by && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(trace, dsum);
 }
 
 // Y (P x l) = S (P x P) X (P x l): a warp per RPW rows, lanes stride over the
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(256)
 // rounding errors are summed separately (the compensated dot product of Ogita,
 // Rump and Oishi, "Accurate sum and dot product", 2005).  FP64 inputs use
 // plain FP64 sums.
-constexpr int GR_ROWS = 256;
+constexpr int GR_ROWS = 64;  // short per-entry chains, a wide grid
 constexpr int GR_SUB = 32;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -195,13 +200,23 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// G = sum over blocks of the partial products, in block order (FP64).
+// G = sum over blocks of the partial products (FP64), one warp per entry: each
+// lane adds its blocks in two interleaved chains, then a fixed shuffle tree
+// combines the lanes, so the result does not depend on scheduling and the
+// dependent FP64 adds (long-latency on this GPU) stay few.
 __global__ void k_gram_sum(int nb, int ne, const double* __restrict__ part, double* __restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (e >= ne) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(long long)b * ne + e];
-  G[e] = s;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = lane; b < nb; b += 64) {
+    s0 += part[(long long)b * ne + e];
+    if (b + 32 < nb) s1 += part[(long long)(b + 32) * ne + e];
+  }
+  double s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) G[e] = s;
 }
 
 template <typename TX>
@@ -210,7 +225,7 @@ fpca_status launch_cross_gram(fpca_ctx* ctx, int P, int l, const TX* A, const TX
   const int nb = (P + GR_ROWS - 1) / GR_ROWS;
   k_cross_gram<TX><<<nb, 256, 0, ctx->stream>>>(P, l, A, B, part);
   FPCA_LAUNCHED(ctx, name);
-  k_gram_sum<<<(l * l + 255) / 256, 256, 0, ctx->stream>>>(nb, l * l, part, G);
+  k_gram_sum<<<(l * l + 7) / 8, 256, 0, ctx->stream>>>(nb, l * l, part, G);
   FPCA_LAUNCHED(ctx, "gram_sum");
   return FPCA_OK;
 }
@@ -267,58 +282,85 @@ __global__ void k_chol_inv(int l, const double* __restrict__ G, double* __restri
   }
 }
 
-// Upper Cholesky G = R'R and Rinv by one warp (l <= 32): lane i holds column
-// i of R and of Rinv in registers; column j of the factor needs only
-// shuffles of row j.  Rank-deficient directions (pivot <= 1e-13 of the
-// largest diagonal) get a zero row/column.
-__global__ void __launch_bounds__(32) k_chol_inv_warp(int l, const double* __restrict__ G,
-                                                      double* __restrict__ Rinv) {
+// 1/sqrt(x) for x in [1e-36, 1e36]: an FP32 estimate refined in FP64 by one
+// Newton-Raphson step on f(y) = y^-2 - x, y <- y (3 - x y^2) / 2, which doubles
+// the number of correct bits (about 46 of FP64's 53: relative error near 1e-14,
+// far below what the Cholesky QR of an FP32 basis needs).  One step, not two:
+// every FP64 operation on this path is a long-latency link of a serial chain.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  const double y = (double)rsqrtf((float)x);
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+
+// Upper Cholesky G = R'R by one warp (l <= 32), right-looking, the matrix in
+// shared memory: lane i owns row i and updates all of it, so by symmetry its
+// entry j is entry (j, i) of the trailing matrix.  Step j: every lane forms
+// 1/sqrt(pivot), lane k > j its entry R[j][k] of row j (published through
+// shared memory), then each lane i > j updates its row.  The loops stay rolled:
+// a single warp runs this code once, so compact code (few instruction-cache
+// misses) matters more than unrolling.  Output: R (l x l row-major, zero below
+// the diagonal) and dinv[j] = 1/R[j][j].  Rank-deficient directions (pivot
+// <= 1e-13 of the largest diagonal) get a zero row and dinv 0.
+__global__ void __launch_bounds__(32) k_chol_rl(int l, const double* __restrict__ G,
+                                                double* __restrict__ R, double* __restrict__ dinv) {
+  __shared__ double Gs[32][33];
+  __shared__ double rowj[32];
   const int i = threadIdx.x;
-  double Rc[32];  // Rc[k] = R[k][i] (column i of the upper factor)
-#pragma unroll
-  for (int k = 0; k < 32; ++k) Rc[k] = 0.0;
-  double gcol[32];  // G[k][i]
-#pragma unroll
-  for (int k = 0; k < 32; ++k) gcol[k] = (k < l && i < l) ? G[k * l + i] : 0.0;
-  double dmax = (i < l) ? G[i * l + i] : 0.0;
+  for (int e = i; e < l * l; e += 32) Gs[e / l][e % l] = G[e];
+  __syncwarp();
+  double dmax = (i < l) ? Gs[i][i] : 0.0;
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (j >= l) break;
-    // R[j][i] = (G[j][i] - sum_{k<j} R[k][j] R[k][i]) / R[j][j]  for i >= j
-    double v = gcol[j];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if (k >= j) break;
-      v -= __shfl_sync(0xffffffffu, Rc[k], j) * Rc[k];
+#pragma unroll 1
+  for (int j = 0; j < l; ++j) {
+    const double piv = Gs[j][j];
+    double y = 0.0;
+    if (piv > 1e-13 * dmax) y = (piv >= 1e-36 && piv <= 1e36) ? rsqrt_newton(piv) : 1.0 / sqrt(piv);
+    double rji = 0.0;  // R[j][i]: 0 left of the diagonal, sqrt(piv) on it
+    if (i < l) rji = i > j ? Gs[i][j] * y : (i == j ? piv * y : 0.0);
+    rowj[i] = rji;
+    if (i < l) R[j * l + i] = rji;
+    if (i == j) dinv[j] = y;
+    __syncwarp();
+    if (i > j && i < l) {
+#pragma unroll 4
+      for (int k = j + 1; k < l; ++k) Gs[i][k] = fma(-rji, rowj[k], Gs[i][k]);
     }
-    // lane j's v is the pivot
-    const double piv = __shfl_sync(0xffffffffu, v, j);
-    const double rjj = piv > 1e-13 * dmax ? sqrt(piv) : 0.0;
-    if (i == j) Rc[j] = rjj;
-    else if (i > j) Rc[j] = rjj > 0.0 ? v / rjj : 0.0;
+    __syncwarp();
   }
-  // Rinv column i: back substitution  R Rinv[:, i] = e_i
-  double x[32];
+}
+
+// Q = Y R^-1 (l <= LT <= 32), one thread per row: q R = y by column-oriented
+// forward substitution in registers (q_k = v_k / R[k][k], then v_j -= q_k R[k][j]
+// for all j > k, independent FMAs), so the dependent FP64 chain is 2 l
+// operations long; R and 1/R[k][k] are read from shared memory (the same
+// address in every lane: broadcasts).  A dropped direction gives a zero column.
+template <typename TX, int LT>
+__global__ void __launch_bounds__(64) k_apply_rsolve(int P, int l, const TX* __restrict__ Y,
+                                                     const double* __restrict__ R,
+                                                     const double* __restrict__ dinv,
+                                                     TX* __restrict__ Q) {
+  __shared__ double rs[LT * LT];
+  __shared__ double di[LT];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) rs[(e / l) * LT + e % l] = R[e];
+  for (int e = threadIdx.x; e < l; e += blockDim.x) di[e] = dinv[e];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P) return;
+  double v[LT];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) x[k] = 0.0;
-  // need R[k][m] for all k, m: R[k][m] = Rc[k] of lane m
+  for (int j = 0; j < LT; ++j) v[j] = j < l ? (double)Y[(long long)r * l + j] : 0.0;
 #pragma unroll
-  for (int k = 31; k >= 0; --k) {
-    if (k >= l) continue;
-    const double rkk = __shfl_sync(0xffffffffu, Rc[k], k);
-    double acc = (k == i) ? 1.0 : 0.0;
+  for (int k = 0; k < LT; ++k) {
+    if (k < l) {
+      v[k] *= di[k];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-      if (m <= k || m >= l) continue;
-      acc -= __shfl_sync(0xffffffffu, Rc[k], m) * x[m];
+      for (int j = k + 1; j < LT; ++j)
+        if (j < l) v[j] = fma(-v[k], rs[k * LT + j], v[j]);
     }
-    x[k] = (rkk > 0.0 && k <= i) ? acc / rkk : 0.0;
   }
-  if (i < l)
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if (k < l) Rinv[k * l + i] = x[k];
+  for (int j = 0; j < LT; ++j)
+    if (j < l) Q[(long long)r * l + j] = (TX)v[j];
 }
 
 // Q = Y Rinv (row-wise).
@@ -746,7 +788,10 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
   double* S = U + nn;
   double* lam = S + nn;
   double* E = U;  // U is dead once S is formed
-  k_rr_jacobi32<<<1, 1024, 0, ctx->stream>>>(l, A, As, X);
+  // one thread per element of a step's rotations (np pairs x l): wider blocks only
+  // make the three barriers of every step dearer
+  const int jt = min(1024, max(64, ((((l + 1) & ~1) / 2 * l + 31) / 32) * 32));
+  k_rr_jacobi32<<<1, jt, 0, ctx->stream>>>(l, A, As, X);
   FPCA_LAUNCHED(ctx, "jacobi");
   for (int step = 0; step < 2; ++step) {
     k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
@@ -796,10 +841,23 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, doub
     TS* src = pass == 0 ? Y : Q;
     fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
     if (gs != FPCA_OK) return gs;
-    if (l <= 32)
-      k_chol_inv_warp<<<1, 32, 0, ctx->stream>>>(l, G, Rinv);
-    else
-      k_chol_inv<<<1, 64, 0, ctx->stream>>>(l, G, Rinv, work);
+    if (l <= 32) {
+      // Rinv holds R here, work its inverse diagonal
+      k_chol_rl<<<1, 32, 0, ctx->stream>>>(l, G, Rinv, work);
+      FPCA_LAUNCHED(ctx, "chol_inv");
+      const int nbk = (P + 63) / 64;
+      if (l <= 8)
+        k_apply_rsolve<TS, 8><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
+      else if (l <= 16)
+        k_apply_rsolve<TS, 16><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
+      else if (l <= 24)
+        k_apply_rsolve<TS, 24><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
+      else
+        k_apply_rsolve<TS, 32><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
+      FPCA_LAUNCHED(ctx, "apply_rinv");
+      continue;
+    }
+    k_chol_inv<<<1, 64, 0, ctx->stream>>>(l, G, Rinv, work);
     FPCA_LAUNCHED(ctx, "chol_inv");
     k_apply_rinv<TS><<<(P + 127) / 128, 128, sizeof(double) * l * l, ctx->stream>>>(P, l, src, Rinv, Q);
     FPCA_LAUNCHED(ctx, "apply_rinv");

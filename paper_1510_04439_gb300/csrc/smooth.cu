@@ -24,6 +24,7 @@
 
 #include "fpca_internal.cuh"
 #include "ptx.cuh"
+#include "ff.cuh"
 
 namespace {
 
@@ -163,7 +164,7 @@ __device__ __forceinline__ double fit_point(T (&A)[D][D], T (&r)[D], double none
 // FP32 fit without FP64 arithmetic on the common path: pivot tests by
 // multiplication (pivot < thr * diagonal) and FP32 divisions; the FP64
 // elimination runs only for the rare escalated systems.
-// Status code returned when the system must be re-solved in FP64.
+// Status code returned when the system must be re-solved at higher precision.
 constexpr uint8_t PT_ESCALATE = 255;
 
 template <int D, bool INLINE_FP64 = true>
@@ -186,11 +187,13 @@ __device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], 
     for (int j = 0; j < D; ++j) Ac[i][j] = A[i][j];
   }
   bool escalate = false;
+  float invp[D];  // 1 / pivot, reused by the back substitution
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const float piv = A[k][k];
     if (!(piv >= (float)ESCALATE_F32 * diag[k])) escalate = true;
     const float inv = piv > 0.f ? 1.f / piv : 0.f;
+    invp[k] = inv;
 #pragma unroll
     for (int i = k + 1; i < D; ++i) {
       const float l = A[k][i] * inv;
@@ -206,7 +209,7 @@ __device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], 
       float sacc = r[k];
 #pragma unroll
       for (int j = k + 1; j < D; ++j) sacc = fmaf(-A[k][j], x[j], sacc);
-      x[k] = sacc / A[k][k];
+      x[k] = sacc * invp[k];
     }
     st = FPCA_PT_OK;
     return x[0];
@@ -517,8 +520,9 @@ struct Epilogue {
   const T* qf;
   double* cvacc;       // [3]: err, w_in, w_out
   // Escalated fits (FP32 pivots below the escalation threshold) are queued
-  // here and solved in FP64 by a separate kernel: entry e holds the 21
-  // moment slots of the point in esc_slots[e*21 ..] and its (xs, xt).
+  // here and solved in float-float (about 48 bits) by a separate kernel:
+  // entry e holds the 21 moment slots of the point in esc_slots[e*21 ..] and
+  // its (xs, xt).
   float* esc_slots;
   int2* esc_idx;
   unsigned* esc_count;
@@ -794,6 +798,97 @@ __device__ __forceinline__ void slide_sum(const float* __restrict__ x, int strid
   for (int j = 0; j < NO; ++j) out[j] = sum[j];
 }
 
+// 8-tap partial (4 when only one chunk is left) of a compensated sliding sum:
+// plain FMAs inside the partial, then a Kahan add into the running sum (the
+// first partial starts it).
+template <int NO>
+__device__ __forceinline__ void comp_partial8(const float* win, int b, float4 w, float4 w2,
+                                              bool two, bool first, float (&sum)[NO],
+                                              float (&cmp)[NO]) {
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    float p = w.x * win[b + j];
+    p = fmaf(w.y, win[b + j + 1], p);
+    p = fmaf(w.z, win[b + j + 2], p);
+    p = fmaf(w.w, win[b + j + 3], p);
+    if (two) {
+      p = fmaf(w2.x, win[b + j + 4], p);
+      p = fmaf(w2.y, win[b + j + 5], p);
+      p = fmaf(w2.z, win[b + j + 6], p);
+      p = fmaf(w2.w, win[b + j + 7], p);
+    }
+    if (first) {
+      sum[j] = p;
+      cmp[j] = 0.f;
+    } else {
+      chunk_add<true>(sum[j], cmp[j], p);
+    }
+  }
+}
+
+// slide_sum with the chunk count NCH = nt / 4 fixed at compile time: the tap
+// loop unrolls completely, so the sliding window needs no register shifts and
+// no loop bookkeeping.  With COMP the partials span 8 taps (two chunks).
+template <int NO, int NCH, bool COMP>
+__device__ __forceinline__ void slide_sum_fixed(const float* __restrict__ x, int stride,
+                                                const float4* __restrict__ w4, float (&out)[NO]) {
+  constexpr int NW = NO + 4 * NCH;
+  float win[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) win[j] = x[j * stride];
+  float sum[NO], cmp[NO];
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    sum[j] = 0.f;
+    cmp[j] = 0.f;
+  }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int kc = 0; kc < NCH; kc += 2) {
+      const bool two = kc + 1 < NCH;
+      comp_partial8<NO>(win, 4 * kc, w4[kc], two ? w4[kc + 1] : make_float4(0.f, 0.f, 0.f, 0.f),
+                        two, kc == 0, sum, cmp);
+    }
+  }
+#pragma unroll
+  for (int kc = 0; kc < NCH; ++kc) {
+    const float4 w = w4[kc];
+    const int b = 4 * kc;
+    if constexpr (!COMP) {
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        sum[j] = fmaf(w.x, win[b + j], sum[j]);
+        sum[j] = fmaf(w.y, win[b + j + 1], sum[j]);
+        sum[j] = fmaf(w.z, win[b + j + 2], sum[j]);
+        sum[j] = fmaf(w.w, win[b + j + 3], sum[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NO; ++j) out[j] = sum[j];
+}
+
+// slide_sum for any padded tap count: the fully unrolled form up to 40 taps
+// (every bandwidth with h M < 20), the looped form beyond.
+template <int NO, bool COMP>
+__device__ __forceinline__ void slide_sum_any(const float* __restrict__ x, int stride,
+                                              const float4* __restrict__ w4, int nt,
+                                              float (&out)[NO]) {
+  switch (nt >> 2) {
+    case 1: slide_sum_fixed<NO, 1, COMP>(x, stride, w4, out); return;
+    case 2: slide_sum_fixed<NO, 2, COMP>(x, stride, w4, out); return;
+    case 3: slide_sum_fixed<NO, 3, COMP>(x, stride, w4, out); return;
+    case 4: slide_sum_fixed<NO, 4, COMP>(x, stride, w4, out); return;
+    case 5: slide_sum_fixed<NO, 5, COMP>(x, stride, w4, out); return;
+    case 6: slide_sum_fixed<NO, 6, COMP>(x, stride, w4, out); return;
+    case 7: slide_sum_fixed<NO, 7, COMP>(x, stride, w4, out); return;
+    case 8: slide_sum_fixed<NO, 8, COMP>(x, stride, w4, out); return;
+    case 9: slide_sum_fixed<NO, 9, COMP>(x, stride, w4, out); return;
+    case 10: slide_sum_fixed<NO, 10, COMP>(x, stride, w4, out); return;
+    default: slide_sum<NO, COMP>(x, stride, w4, nt, out); return;
+  }
+}
+
 // weights in padded form: wp[row][k], k = 0..nt-1 <-> offset k - T (zero beyond 2T)
 __device__ __forceinline__ void load_padded_weights(const double* __restrict__ tab, int T, int nt,
                                                     float* __restrict__ wp) {
@@ -875,8 +970,8 @@ __global__ void __launch_bounds__(NT2, 2)
     const int m = it / C, c = it - (it / C) * C;
     const int a = c_mid_array[m], pw = c_mid_pow[m];
     float out[HT];
-    slide_sum<HT, COMP>(in + (size_t)a * g.nrp * C + c, C,
-                        reinterpret_cast<const float4*>(wr + pw * g.ntr), g.ntr, out);
+    slide_sum_any<HT, COMP>(in + (size_t)a * g.nrp * C + c, C,
+                            reinterpret_cast<const float4*>(wr + pw * g.ntr), g.ntr, out);
     float* dst = mid + (size_t)m * HT * g.RS + g.Tc + c;
 #pragma unroll
     for (int j = 0; j < HT; ++j) dst[j * g.RS] = out[j];
@@ -895,16 +990,16 @@ __global__ void __launch_bounds__(NT2, 2)
     const int i = (rem / SLO) % HT;
     const int m = c_slot_mid[s], pw = c_slot_pow[s];
     float out[SEG];
-    slide_sum<SEG, COMP>(mid + ((size_t)m * HT + i) * g.RS + sg * SEG, 1,
-                         reinterpret_cast<const float4*>(wc + pw * g.ntc), g.ntc, out);
+    slide_sum_any<SEG, COMP>(mid + ((size_t)m * HT + i) * g.RS + sg * SEG, 1,
+                             reinterpret_cast<const float4*>(wc + pw * g.ntc), g.ntc, out);
     float* dst = slots + ((size_t)s * HT + i) * g.SC + sg * SEG;
 #pragma unroll
     for (int j = 0; j < SEG; ++j) dst[j] = out[j];
   }
   __syncthreads();
 
-  // phase 3: per-point solve, write, epilogue terms (FP32; FP64 only for
-  // escalated systems and for the block sums of the CV terms)
+  // phase 3: per-point solve, write, epilogue terms (FP32; escalated systems
+  // are queued for the float-float kernel; FP64 for the block sums of the CV terms)
   float cv_err = 0.f, cv_in = 0.f, cv_out = 0.f;
   constexpr int PPT3 = (HT * C + NT2 - 1) / NT2;
   float gval[PPT3];
@@ -937,7 +1032,7 @@ __global__ void __launch_bounds__(NT2, 2)
         float* dst = ep.esc_slots + (size_t)slot * NSL;
         for (int q = 0; q < NSL; ++q) dst[q] = sl[(size_t)q * HT * g.SC];
         ep.esc_idx[slot] = make_int2(xs, xt);
-        continue;  // the FP64 kernel writes this point and its epilogue terms
+        continue;  // the escalation kernel writes this point and its epilogue terms
       }
       // queue full: solve here
       float A2[5][5], r2[5];
@@ -979,26 +1074,33 @@ __global__ void __launch_bounds__(NT2, 2)
     }
   }
   if (ep.y) {
-    // y[s, :] += sum over this block's t of Gamma_hat(s, t) Omega[t, :]: warp sums by
-    // shuffles, then one pass over the warps' partials in shared memory
-    // (the warp partials reuse the mid rows: phase 3 reads only the slots)
-    float* yred = mid;  // [NT2 / 32][l]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = 0; c < ep.l; ++c) {
-      float sacc = 0.f;
+    // y[s, :] += sum over this block's t of Gamma_hat(s, t) Omega[t, :].  The block's
+    // t form one contiguous run of Omega's rows, so thread (group, column c) walks
+    // every ng-th of them with coalesced loads; the ng partials of a column are
+    // then added in shared memory (which reuses the mid rows: phase 3 reads only
+    // the slots).  EMPTY and escalated points carry 0.
+    (void)xts;
+    float* gsm = mid;             // [HT * C]
+    float* part = mid + HT * C;   // [NT2]
 #pragma unroll
-      for (int j = 0; j < PPT3; ++j)
-        if (xts[j] >= 0) sacc = fmaf(gval[j], ep.omega[(long long)xts[j] * ep.l + c], sacc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) yred[warp * ep.l + c] = sacc;
+    for (int j = 0; j < PPT3; ++j) {
+      const int e = threadIdx.x + j * NT2;
+      if (e < HT * C) gsm[e] = gval[j];
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < ep.l; c += NT2) {
+    const int l = ep.l, ng = NT2 / l;
+    const int c = threadIdx.x % l, grp = threadIdx.x / l;
+    float acc = 0.f;
+    if (grp < ng) {
+      const float* om = ep.omega + (long long)a0 * C * l + c;
+      for (int t = grp; t < th * C; t += ng) acc = fmaf(gsm[t], om[(long long)t * l], acc);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < l) {
       float tot = 0.f;
-#pragma unroll
-      for (int w = 0; w < NT2 / 32; ++w) tot += yred[w * ep.l + c];
-      atomicAdd(ep.y + (long long)xs * ep.l + c, tot);
+      for (int gi = 0; gi < ng; ++gi) tot += part[gi * l + threadIdx.x];
+      atomicAdd(ep.y + (long long)xs * l + threadIdx.x, tot);
     }
   }
 }
@@ -1062,6 +1164,76 @@ __device__ __forceinline__ void slide_sum_multi(const float* __restrict__ x, int
     for (int j = 0; j < NO; ++j) out[q][j] = sum[q][j];
 }
 
+// slide_sum_multi with NCH = nt / 4 fixed at compile time (8-tap partials with COMP).
+template <int NO, int NP, int NCH, bool COMP>
+__device__ __forceinline__ void slide_sum_multi_fixed(const float* __restrict__ x, int stride,
+                                                      const float4* const (&w4)[NP],
+                                                      float (&out)[NP][NO]) {
+  constexpr int NW = NO + 4 * NCH;
+  float win[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) win[j] = x[j * stride];
+  float sum[NP][NO], cmp[NP][NO];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      sum[q][j] = 0.f;
+      cmp[q][j] = 0.f;
+    }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int kc = 0; kc < NCH; kc += 2) {
+      const bool two = kc + 1 < NCH;
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+        comp_partial8<NO>(win, 4 * kc, w4[q][kc],
+                          two ? w4[q][kc + 1] : make_float4(0.f, 0.f, 0.f, 0.f), two, kc == 0,
+                          sum[q], cmp[q]);
+    }
+  }
+#pragma unroll
+  for (int kc = 0; kc < NCH; ++kc) {
+    const int b = 4 * kc;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float4 w = w4[q][kc];
+      if constexpr (!COMP) {
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          sum[q][j] = fmaf(w.x, win[b + j], sum[q][j]);
+          sum[q][j] = fmaf(w.y, win[b + j + 1], sum[q][j]);
+          sum[q][j] = fmaf(w.z, win[b + j + 2], sum[q][j]);
+          sum[q][j] = fmaf(w.w, win[b + j + 3], sum[q][j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) out[q][j] = sum[q][j];
+}
+
+template <int NO, int NP, bool COMP>
+__device__ __forceinline__ void slide_sum_multi_any(const float* __restrict__ x, int stride,
+                                                    const float4* const (&w4)[NP], int nt,
+                                                    float (&out)[NP][NO]) {
+  switch (nt >> 2) {
+    case 1: slide_sum_multi_fixed<NO, NP, 1, COMP>(x, stride, w4, out); return;
+    case 2: slide_sum_multi_fixed<NO, NP, 2, COMP>(x, stride, w4, out); return;
+    case 3: slide_sum_multi_fixed<NO, NP, 3, COMP>(x, stride, w4, out); return;
+    case 4: slide_sum_multi_fixed<NO, NP, 4, COMP>(x, stride, w4, out); return;
+    case 5: slide_sum_multi_fixed<NO, NP, 5, COMP>(x, stride, w4, out); return;
+    case 6: slide_sum_multi_fixed<NO, NP, 6, COMP>(x, stride, w4, out); return;
+    case 7: slide_sum_multi_fixed<NO, NP, 7, COMP>(x, stride, w4, out); return;
+    case 8: slide_sum_multi_fixed<NO, NP, 8, COMP>(x, stride, w4, out); return;
+    case 9: slide_sum_multi_fixed<NO, NP, 9, COMP>(x, stride, w4, out); return;
+    case 10: slide_sum_multi_fixed<NO, NP, 10, COMP>(x, stride, w4, out); return;
+    default: slide_sum_multi<NO, NP, COMP>(x, stride, w4, nt, out); return;
+  }
+}
+
 // s-side pass (FP32): one block = one line (Ma rows along the pass axis) x
 // 128 columns of one input array; rows padded with zeros above and below.
 constexpr int VROWS = 8;  // outputs per sliding window
@@ -1074,7 +1246,8 @@ __device__ __forceinline__ void vpass2_line(const VJob& jb, const float* tile, c
   for (int q = 0; q < NP; ++q) w4[q] = reinterpret_cast<const float4*>(wp + jb.row[q] * ntp);
   for (int x0 = 0; x0 < Ma; x0 += VROWS) {
     float out[NP][VROWS];
-    slide_sum_multi<VROWS, NP, COMP>(tile + (size_t)x0 * VCOLS + threadIdx.x, VCOLS, w4, ntp, out);
+    slide_sum_multi_any<VROWS, NP, COMP>(tile + (size_t)x0 * VCOLS + threadIdx.x, VCOLS, w4, ntp,
+                                         out);
 #pragma unroll
     for (int j = 0; j < VROWS; ++j) {
       const int x = x0 + j;
@@ -1189,30 +1362,62 @@ size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
 // slow FP64 pipe runs full warps; writes Gamma_hat, status and the epilogue
 // terms the t-side kernel skipped.
 __global__ void __launch_bounds__(256)
-    k_escalated_f64(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
-                    const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,
-                    float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep) {
+    k_escalated(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
+                const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,
+                float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep) {
   const unsigned n = min(*esc_count, (unsigned)cap);
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const float* sl = esc_slots + (size_t)e * NSL;
     const int2 id = esc_idx[e];
-    double A[5][5], r[5];
+    // the 5 x 5 system in float-float: symmetric elimination in the order of
+    // elim_solve, pivot ratios against the original diagonal, inverses of the
+    // pivots reused by the back substitution
+    ff::F2 A[5][5], r[5], inv[5];
+    float diag[5];
 #pragma unroll
     for (int i2 = 0; i2 < 5; ++i2) {
-      r[i2] = (double)sl[rslot(2, i2)];
+      r[i2] = ff::make(sl[rslot(2, i2)]);
 #pragma unroll
       for (int j2 = i2; j2 < 5; ++j2) {
-        A[i2][j2] = (double)sl[aslot(2, i2, j2)];
+        A[i2][j2] = ff::make(sl[aslot(2, i2, j2)]);
         A[j2][i2] = A[i2][j2];
       }
+      diag[i2] = A[i2][i2].hi;
     }
-    const double lc = r[0] / A[0][0];
-    double ratio;
-    double g = elim_solve<5, double>(A, r, ratio);
-    uint8_t st = FPCA_PT_OK;
-    if (ratio <= PIVOT_RTOL_F32) {
-      st = FPCA_PT_FALLBACK;
-      g = lc;
+    const double lc = (double)r[0].hi / (double)A[0][0].hi;
+    float minratio = 1e30f;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const ff::F2 piv = A[k][k];
+      const float ratio = diag[k] > 0.f ? piv.hi / diag[k] : -1.f;
+      minratio = fminf(minratio, ratio);
+      if (!(piv.hi > 0.f)) {
+        ok = false;
+        break;
+      }
+      inv[k] = ff::recip(piv);
+#pragma unroll
+      for (int i = k + 1; i < 5; ++i) {
+        const ff::F2 l = ff::mul(A[k][i], inv[k]);
+#pragma unroll
+        for (int j = i; j < 5; ++j) A[i][j] = ff::sub_mul(A[i][j], l, A[k][j]);
+        r[i] = ff::sub_mul(r[i], l, r[k]);
+      }
+    }
+    double g = lc;
+    uint8_t st = FPCA_PT_FALLBACK;
+    if (ok && (double)minratio > PIVOT_RTOL_F32) {
+      ff::F2 x[5];
+#pragma unroll
+      for (int k = 4; k >= 0; --k) {
+        ff::F2 sacc = r[k];
+#pragma unroll
+        for (int j = k + 1; j < 5; ++j) sacc = ff::sub_mul(sacc, A[k][j], x[j]);
+        x[k] = ff::mul(sacc, inv[k]);
+      }
+      g = ff::to_double(x[0]);
+      st = FPCA_PT_OK;
     }
     if (mu_raw) g -= mu_raw[id.x] * mu_raw[id.y];
     const long long o = (long long)id.x * P + id.y;
@@ -1381,9 +1586,9 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
           }
           FPCA_LAUNCHED(ctx, "cov_hpass_solve");
           if (ef.esc_count) {
-            k_escalated_f64<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(
+            k_escalated<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(
                 P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef);
-            FPCA_LAUNCHED(ctx, "cov_escalated_f64");
+            FPCA_LAUNCHED(ctx, "cov_escalated");
           }
           return FPCA_OK;
         }
