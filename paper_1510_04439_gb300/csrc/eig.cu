@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "fpca_internal.cuh"
+#include "ff.cuh"
 
 namespace {
 
@@ -282,85 +283,143 @@ __global__ void k_chol_inv(int l, const double* __restrict__ G, double* __restri
   }
 }
 
-// 1/sqrt(x) for x in [1e-36, 1e36]: an FP32 estimate refined in FP64 by one
-// Newton-Raphson step on f(y) = y^-2 - x, y <- y (3 - x y^2) / 2, which doubles
-// the number of correct bits (about 46 of FP64's 53: relative error near 1e-14,
-// far below what the Cholesky QR of an FP32 basis needs).  One step, not two:
-// every FP64 operation on this path is a long-latency link of a serial chain.
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  const double y = (double)rsqrtf((float)x);
-  return y * fma(-0.5 * x * y, y, 1.5);
+// 1/sqrt(a) in float-float for a > 0 in FP32 range: the FP32 estimate y0 and one
+// Newton-Raphson step on f(y) = y^-2 - a, y1 = y0 + y0 (1 - a y0^2) / 2, with the
+// residual 1 - a y0^2 formed in float-float (error about 1e-14 relative).
+__device__ __forceinline__ ff::F2 rsqrt_ff(ff::F2 a) {
+  const float y0 = rsqrtf(a.hi);
+  const ff::F2 ay2 = ff::mul(a, ff::two_prod(y0, y0));
+  const ff::F2 e = ff::add(ff::make(1.0f), ff::neg(ay2));
+  return ff::fast_two_sum(y0, 0.5f * y0 * e.hi);
 }
 
-// Upper Cholesky G = R'R by one warp (l <= 32), right-looking, the matrix in
-// shared memory: lane i owns row i and updates all of it, so by symmetry its
-// entry j is entry (j, i) of the trailing matrix.  Step j: every lane forms
-// 1/sqrt(pivot), lane k > j its entry R[j][k] of row j (published through
-// shared memory), then each lane i > j updates its row.  The loops stay rolled:
-// a single warp runs this code once, so compact code (few instruction-cache
-// misses) matters more than unrolling.  Output: R (l x l row-major, zero below
-// the diagonal) and dinv[j] = 1/R[j][j].  Rank-deficient directions (pivot
-// <= 1e-13 of the largest diagonal) get a zero row and dinv 0.
-__global__ void __launch_bounds__(32) k_chol_rl(int l, const double* __restrict__ G,
-                                                double* __restrict__ R, double* __restrict__ dinv) {
-  __shared__ double Gs[32][33];
-  __shared__ double rowj[32];
-  const int i = threadIdx.x;
-  for (int e = i; e < l * l; e += 32) Gs[e / l][e % l] = G[e];
-  __syncwarp();
-  double dmax = (i < l) ? Gs[i][i] : 0.0;
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+__device__ __forceinline__ ff::F2 ff_of(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+
+// Upper Cholesky G = R'R and R^-1 in float-float (l <= 32), one block of
+// CH_THREADS threads, everything in shared memory.  Float-float rather than
+// FP64: FP64 operations have long latency on this GPU and both factorisations
+// are serial chains of l steps (the Gram matrix factored here is itself
+// accurate to about 1e-14, from the compensated Gram kernel).  Each step's
+// updates are spread over all threads, so a step costs a few dependent
+// float-float operations and two barriers.
+//   Cholesky, right-looking: step j forms 1/sqrt(G_jj) and row j of R, then
+//   G_ik -= R_ji R_jk over the trailing upper triangle i <= k.
+//   Inverse, by rows from the bottom: x_ic = (delta_ic - a_ic) / R_ii for every
+//   column c >= i, then a_kc += R_ki x_ic for k < i (a starts at 0).
+// Output: R^-1 (l x l row-major, upper triangular) as hi parts Ih and lo parts
+// Il.  Rank-deficient directions (pivot <= 1e-13 of the largest diagonal) get a
+// zero row and column.
+constexpr int CH_THREADS = 128;
+__global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __restrict__ G,
+                                                        float* __restrict__ Ih,
+                                                        float* __restrict__ Il) {
+  __shared__ float Gh[32][33], Gl[32][33];  // trailing matrix, then R by rows
+  __shared__ float Ah[32][33], Al[32][33];  // sums of the inverse's back substitution
+  __shared__ float yh[32], yl[32];          // 1 / R_jj
+  __shared__ float dmax_s;
+  const int t = threadIdx.x;
+  for (int e = t; e < l * l; e += CH_THREADS) {
+    const ff::F2 g = ff_of(G[e]);
+    Gh[e / l][e % l] = g.hi;
+    Gl[e / l][e % l] = g.lo;
+    Ah[e / l][e % l] = 0.f;
+    Al[e / l][e % l] = 0.f;
+  }
+  __syncthreads();
+  if (t < 32) {
+    float dm = (t < l) ? Gh[t][t] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (t == 0) dmax_s = dm;
+  }
+  __syncthreads();
+  const float dmax = dmax_s;
 #pragma unroll 1
   for (int j = 0; j < l; ++j) {
-    const double piv = Gs[j][j];
-    double y = 0.0;
-    if (piv > 1e-13 * dmax) y = (piv >= 1e-36 && piv <= 1e36) ? rsqrt_newton(piv) : 1.0 / sqrt(piv);
-    double rji = 0.0;  // R[j][i]: 0 left of the diagonal, sqrt(piv) on it
-    if (i < l) rji = i > j ? Gs[i][j] * y : (i == j ? piv * y : 0.0);
-    rowj[i] = rji;
-    if (i < l) R[j * l + i] = rji;
-    if (i == j) dinv[j] = y;
-    __syncwarp();
-    if (i > j && i < l) {
-#pragma unroll 4
-      for (int k = j + 1; k < l; ++k) Gs[i][k] = fma(-rji, rowj[k], Gs[i][k]);
+    // row j of R (entries k >= j), every thread computing the same 1/sqrt(pivot)
+    const ff::F2 piv = {Gh[j][j], Gl[j][j]};
+    ff::F2 y = ff::make(0.f);
+    if (piv.hi > 1e-13f * dmax) y = rsqrt_ff(piv);
+    __syncthreads();  // every thread has read the pivot
+    for (int k = j + t; k < l; k += CH_THREADS) {
+      const ff::F2 r = ff::mul(k == j ? piv : ff::F2{Gh[j][k], Gl[j][k]}, y);
+      Gh[j][k] = r.hi;
+      Gl[j][k] = r.lo;
     }
-    __syncwarp();
+    if (t == 0) {
+      yh[j] = y.hi;
+      yl[j] = y.lo;
+    }
+    __syncthreads();
+    // trailing upper triangle j < i <= k < l
+    const int m = l - j - 1;
+    for (int e = t; e < m * m; e += CH_THREADS) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k < i) continue;
+      const ff::F2 g = ff::sub_mul(ff::F2{Gh[i][k], Gl[i][k]}, ff::F2{Gh[j][i], Gl[j][i]},
+                                   ff::F2{Gh[j][k], Gl[j][k]});
+      Gh[i][k] = g.hi;
+      Gl[i][k] = g.lo;
+    }
+    __syncthreads();
+  }
+  // R^-1 by rows from the bottom; row i of R^-1 goes straight to Ih/Il
+#pragma unroll 1
+  for (int i = l - 1; i >= 0; --i) {
+    const ff::F2 d = {yh[i], yl[i]};
+    for (int c = t; c < l; c += CH_THREADS) {
+      ff::F2 x = ff::make(0.f);
+      if (c >= i) x = ff::mul(ff::add(ff::make(c == i ? 1.f : 0.f), ff::neg(ff::F2{Ah[i][c], Al[i][c]})), d);
+      Ih[i * l + c] = x.hi;
+      Il[i * l + c] = x.lo;
+      Ah[i][c] = x.hi;  // row i of the sums is dead: keep x there for the update
+      Al[i][c] = x.lo;
+    }
+    __syncthreads();
+    for (int e = t; e < i * l; e += CH_THREADS) {
+      const int k = e / l, c = e % l;
+      if (c < i) continue;
+      const ff::F2 a = ff::add(ff::F2{Ah[k][c], Al[k][c]},
+                               ff::mul(ff::F2{Gh[k][i], Gl[k][i]}, ff::F2{Ah[i][c], Al[i][c]}));
+      Ah[k][c] = a.hi;
+      Al[k][c] = a.lo;
+    }
+    __syncthreads();
   }
 }
 
-// Q = Y R^-1 (l <= LT <= 32), one thread per row: q R = y by column-oriented
-// forward substitution in registers (q_k = v_k / R[k][k], then v_j -= q_k R[k][j]
-// for all j > k, independent FMAs), so the dependent FP64 chain is 2 l
-// operations long; R and 1/R[k][k] are read from shared memory (the same
-// address in every lane: broadcasts).  A dropped direction gives a zero column.
-template <typename TX, int LT>
-__global__ void __launch_bounds__(64) k_apply_rsolve(int P, int l, const TX* __restrict__ Y,
-                                                     const double* __restrict__ R,
-                                                     const double* __restrict__ dinv,
-                                                     TX* __restrict__ Q) {
-  __shared__ double rs[LT * LT];
-  __shared__ double di[LT];
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) rs[(e / l) * LT + e % l] = R[e];
-  for (int e = threadIdx.x; e < l; e += blockDim.x) di[e] = dinv[e];
-  __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= P) return;
-  double v[LT];
-#pragma unroll
-  for (int j = 0; j < LT; ++j) v[j] = j < l ? (double)Y[(long long)r * l + j] : 0.0;
-#pragma unroll
-  for (int k = 0; k < LT; ++k) {
-    if (k < l) {
-      v[k] *= di[k];
-#pragma unroll
-      for (int j = k + 1; j < LT; ++j)
-        if (j < l) v[j] = fma(-v[k], rs[k * LT + j], v[j]);
-    }
+// Q = Y R^-1 with R^-1 from k_chol_ff, one thread per entry (row r, column j):
+// q_rj = sum_{k <= j} y_rk R^-1[k][j], products and sum in float-float (R^-1 of
+// an ill-conditioned basis has large entries whose contributions cancel), so
+// the work spreads over P l threads and each chain is at most l terms long.
+template <typename TX>
+__global__ void __launch_bounds__(256) k_apply_ff(int P, int l, const TX* __restrict__ Y,
+                                                  const float* __restrict__ Ih,
+                                                  const float* __restrict__ Il,
+                                                  TX* __restrict__ Q) {
+  __shared__ float sh[32 * 32], sl[32 * 32];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    sh[e] = Ih[e];
+    sl[e] = Il[e];
   }
-#pragma unroll
-  for (int j = 0; j < LT; ++j)
-    if (j < l) Q[(long long)r * l + j] = (TX)v[j];
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)P * l) return;
+  const long long r = e / l;
+  const int j = (int)(e - r * l);
+  const TX* yr = Y + r * l;
+  ff::F2 acc = ff::make(0.f);
+  for (int k = 0; k <= j; ++k) {
+    ff::F2 yk;
+    if constexpr (sizeof(TX) == 4)
+      yk = ff::make((float)yr[k]);
+    else
+      yk = ff_of((double)yr[k]);
+    acc = ff::add(acc, ff::mul(yk, ff::F2{sh[k * l + j], sl[k * l + j]}));
+  }
+  Q[e] = (TX)ff::to_double(acc);
 }
 
 // Q = Y Rinv (row-wise).
@@ -498,10 +557,12 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
   const int ne = (n + 1) & ~1;
   const int np = ne / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, dia = 0.0;
+    // the stopping test in the working type T: an FP32 Jacobi needs no FP64
+    // sums here (serial FP64 adds are slow on this GPU)
+    T off = T(0), dia = T(0);
     for (int e = tid; e < n * n; e += nt) {
       const int r = e / n, c = e - r * n;
-      const double a = (double)A[r * ld + c];
+      const T a = A[r * ld + c];
       if (r == c) dia += a * a;
       else off += a * a;
     }
@@ -510,17 +571,17 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
       dia += __shfl_xor_sync(0xffffffffu, dia, o);
     }
     if ((tid & 31) == 0) {
-      red[2 * (tid >> 5)] = off;
-      red[2 * (tid >> 5) + 1] = dia;
+      red[2 * (tid >> 5)] = (double)off;
+      red[2 * (tid >> 5) + 1] = (double)dia;
     }
     __syncthreads();
     if (tid == 0) {
-      double ot = 0.0, dt = 0.0;
+      T ot = T(0), dt = T(0);
       for (int w = 0; w < nt / 32; ++w) {
-        ot += red[2 * w];
-        dt += red[2 * w + 1];
+        ot += (T)red[2 * w];
+        dt += (T)red[2 * w + 1];
       }
-      *done = (ot <= tol * dt) || ot == 0.0;
+      *done = ((double)ot <= tol * (double)dt) || ot == T(0);
     }
     __syncthreads();
     if (*done) break;
@@ -777,6 +838,100 @@ __global__ void k_finish(int P, int n, int k, double dv, const double* __restric
   }
 }
 
+// Both Ogita-Aishima refinement steps of k_rr_jacobi32's eigenvectors in one block
+// (l <= 32), with the l x l matrices in shared memory: per step
+// R = I - X'X, U = A X, S = X'U, lambda_i = s_ii / (1 - r_ii),
+// delta = 2 (|S - diag S| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
+// or r_ij / 2 inside clusters, X <- X + X E; then A <- diag(lambda), V <- X.
+// Each product entry is split into two half-length dot products (neighbouring
+// threads), so the serial FP64 chains (long-latency on this GPU) stay about l/2
+// long.
+constexpr int RF_THREADS = 1024;
+__device__ __forceinline__ void rf_product(int n, const double* L, bool tl, const double* M,
+                                           double* C, double diag, double sign) {
+  // C = diag I + sign op(L) M, op(L) = L' when tl; entry o by threads 2o and
+  // 2o + 1 (neighbouring lanes), each summing half of k, joined by a shuffle
+  const int h = (n + 1) / 2;
+  const int ne2 = 2 * n * n;
+  for (int base = 0; base < ne2; base += RF_THREADS) {
+    const int e = base + threadIdx.x;
+    const int o = e >> 1, part = e & 1;
+    double acc = 0.0;
+    if (e < ne2) {
+      const int i = o / n, j = o - i * n;
+      const int k0 = part * h, k1 = min(n, k0 + h);
+      for (int k = k0; k < k1; ++k) acc = fma(tl ? L[k * n + i] : L[i * n + k], M[k * n + j], acc);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (e < ne2 && part == 0) {
+      const int i = o / n, j = o - i * n;
+      C[o] = ((i == j) ? diag : 0.0) + sign * acc;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double rf_block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double x = red[lane];  // RF_THREADS / 32 == 32 partials
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[32] = x;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(RF_THREADS)
+    k_rr_refine(int n, const double* __restrict__ Asym, const double* __restrict__ X0,
+                double* __restrict__ Ag, double* __restrict__ Vg) {
+  __shared__ double A[32 * 32], X[32 * 32], R[32 * 32], U[32 * 32], S[32 * 32];
+  __shared__ double lam[32];
+  __shared__ double red[33];
+  const int t = threadIdx.x, nn = n * n;
+  for (int e = t; e < nn; e += RF_THREADS) {
+    A[e] = Asym[e];
+    X[e] = X0[e];
+  }
+  __syncthreads();
+  double an = 0.0;
+  for (int e = t; e < nn; e += RF_THREADS) an += A[e] * A[e];
+  an = rf_block_sum(an, red);
+  for (int step = 0; step < 2; ++step) {
+    rf_product(n, X, true, X, R, 1.0, -1.0);  // R = I - X'X
+    rf_product(n, A, false, X, U, 0.0, 1.0);  // U = A X
+    rf_product(n, X, true, U, S, 0.0, 1.0);   // S = X'AX
+    for (int i = t; i < n; i += RF_THREADS) lam[i] = S[i * n + i] / (1.0 - R[i * n + i]);
+    double so = 0.0, rn = 0.0;
+    for (int e = t; e < nn; e += RF_THREADS) {
+      if (e / n != e % n) so += S[e] * S[e];
+      rn += R[e] * R[e];
+    }
+    so = rf_block_sum(so, red);  // (the barriers inside also publish lam)
+    rn = rf_block_sum(rn, red);
+    const double delta = 2.0 * (sqrt(so) + sqrt(an) * sqrt(rn));
+    for (int e = t; e < nn; e += RF_THREADS) {  // E into U (dead once S is formed)
+      const int i = e / n, j = e - i * n;
+      const double gap = lam[j] - lam[i];
+      U[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lam[j] * R[e]) / gap;
+    }
+    __syncthreads();
+    rf_product(n, X, false, U, S, 0.0, 1.0);  // S = X E
+    for (int e = t; e < nn; e += RF_THREADS) X[e] += S[e];
+    __syncthreads();
+  }
+  for (int e = t; e < nn; e += RF_THREADS) {
+    const int i = e / n, j = e - i * n;
+    Ag[e] = (i == j) ? lam[i] : 0.0;
+    Vg[e] = X[e];
+  }
+}
+
 // Rayleigh-Ritz eigensolver (FP32 Jacobi + two FP64 refinement steps); scratch
 // holds 5 l^2 + l doubles.
 fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double* scratch) {
@@ -793,6 +948,11 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
   const int jt = min(1024, max(64, ((((l + 1) & ~1) / 2 * l + 31) / 32) * 32));
   k_rr_jacobi32<<<1, jt, 0, ctx->stream>>>(l, A, As, X);
   FPCA_LAUNCHED(ctx, "jacobi");
+  if (l <= 32) {
+    k_rr_refine<<<1, RF_THREADS, 0, ctx->stream>>>(l, As, X, A, V);
+    FPCA_LAUNCHED(ctx, "jacobi");
+    return FPCA_OK;
+  }
   for (int step = 0; step < 2; ++step) {
     k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
     FPCA_LAUNCHED(ctx, "jacobi");
@@ -842,18 +1002,13 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, doub
     fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
     if (gs != FPCA_OK) return gs;
     if (l <= 32) {
-      // Rinv holds R here, work its inverse diagonal
-      k_chol_rl<<<1, 32, 0, ctx->stream>>>(l, G, Rinv, work);
+      // Rinv holds R^-1 as hi and lo parts
+      float* Ih = reinterpret_cast<float*>(Rinv);
+      float* Il = Ih + l * l;
+      k_chol_ff<<<1, CH_THREADS, 0, ctx->stream>>>(l, G, Ih, Il);
       FPCA_LAUNCHED(ctx, "chol_inv");
-      const int nbk = (P + 63) / 64;
-      if (l <= 8)
-        k_apply_rsolve<TS, 8><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
-      else if (l <= 16)
-        k_apply_rsolve<TS, 16><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
-      else if (l <= 24)
-        k_apply_rsolve<TS, 24><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
-      else
-        k_apply_rsolve<TS, 32><<<nbk, 64, 0, ctx->stream>>>(P, l, src, Rinv, work, Q);
+      const long long ne = (long long)P * l;
+      k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, Q);
       FPCA_LAUNCHED(ctx, "apply_rinv");
       continue;
     }
