@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include "fpca_internal.cuh"
+#include "ff.cuh"
 
 namespace {
 
@@ -58,10 +59,12 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
                      double* __restrict__ v2) {
   __shared__ double ps[3][MB_SLICES][32];
   __shared__ int pc[MB_SLICES][32];
-  __shared__ double winv[32 * MB_SLICES];
+  __shared__ float winvh[32 * MB_SLICES], winvl[32 * MB_SLICES];
   const int p = blockIdx.x * 32 + threadIdx.x;
   int c = 0;
-  double sw = 0.0, sv = 0.0, sv2 = 0.0;
+  // per-thread sums in float-float (about 48 bits from FP32 operations: FP64
+  // adds are long-latency and low-throughput on this GPU), joined in FP64 below
+  ff::F2 fw = ff::make(0.f), fv = ff::make(0.f), fv2 = ff::make(0.f);
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int i0 = 0; i0 < n; i0 += 32 * MB_SLICES) {
     // 1/N_i for the next 32 * MB_SLICES subjects, one division per subject
@@ -69,7 +72,10 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
     {
       const int i = i0 + tid;
       const int N = i < n ? Ni[i] : 0;
-      winv[tid] = N > 0 ? 1.0 / (double)N : 0.0;
+      const double wd = N > 0 ? 1.0 / (double)N : 0.0;
+      const float hi = (float)wd;
+      winvh[tid] = hi;
+      winvl[tid] = (float)(wd - (double)hi);
     }
     __syncthreads();
     if (p < P) {
@@ -77,16 +83,27 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
       for (int i = i0 + threadIdx.y; i < iend; i += MB_SLICES) {
         const size_t idx = (size_t)i * P + p;
         if (mask && !mask[idx]) continue;
-        const double wi = winv[i - i0];
-        if (wi == 0.0) continue;
-        const double yy = load_y(y, y_prec, idx);
+        const ff::F2 wi = {winvh[i - i0], winvl[i - i0]};
+        if (wi.hi == 0.f) continue;
+        ff::F2 yy, y2;
+        if (y_prec == FPCA_F64) {
+          const double yd = static_cast<const double*>(y)[idx];
+          const float hi = (float)yd;
+          yy = {hi, (float)(yd - (double)hi)};
+          y2 = ff::mul(yy, yy);
+        } else {
+          const float yf = static_cast<const float*>(y)[idx];
+          yy = ff::make(yf);
+          y2 = ff::two_prod(yf, yf);  // exact
+        }
         c += 1;
-        sw = __dadd_rn(sw, wi);
-        sv = __dadd_rn(sv, __dmul_rn(wi, yy));
-        sv2 = __dadd_rn(sv2, __dmul_rn(wi, __dmul_rn(yy, yy)));
+        fw = ff::add(fw, wi);
+        fv = ff::add(fv, ff::mul(wi, yy));
+        fv2 = ff::add(fv2, ff::mul(wi, y2));
       }
     }
   }
+  const double sw = ff::to_double(fw), sv = ff::to_double(fv), sv2 = ff::to_double(fv2);
   ps[0][threadIdx.y][threadIdx.x] = sw;
   ps[1][threadIdx.y][threadIdx.x] = sv;
   ps[2][threadIdx.y][threadIdx.x] = sv2;

@@ -231,58 +231,6 @@ fpca_status launch_cross_gram(fpca_ctx* ctx, int P, int l, const TX* A, const TX
   return FPCA_OK;
 }
 
-// Upper Cholesky G = R'R and Rinv (one block, l <= 64, shared memory).
-// Column j: the pivot by thread 0, the rest of row j of R in parallel; then
-// each thread back-substitutes one column of Rinv.  Rank-deficient
-// directions (pivot <= 1e-13 of the largest diagonal) get a zero row/column.
-__global__ void k_chol_inv(int l, const double* __restrict__ G, double* __restrict__ Rinv,
-                           double* __restrict__ work) {
-  (void)work;
-  __shared__ double R[64 * 64];
-  __shared__ double dmax_s;
-  const int t = threadIdx.x;
-  for (int e = t; e < l * l; e += blockDim.x) R[e] = G[e];
-  __syncthreads();
-  if (t == 0) {
-    double dm = 0.0;
-    for (int i = 0; i < l; ++i) dm = fmax(dm, R[i * l + i]);
-    dmax_s = dm;
-  }
-  __syncthreads();
-  // in place: R[j][i] (i >= j) becomes the Cholesky factor; the strict lower part is zeroed
-  for (int j = 0; j < l; ++j) {
-    if (t == 0) {
-      double sdiag = R[j * l + j];
-      for (int k = 0; k < j; ++k) sdiag -= R[k * l + j] * R[k * l + j];
-      R[j * l + j] = sdiag > 1e-13 * dmax_s ? sqrt(sdiag) : 0.0;
-    }
-    __syncthreads();
-    const double rjj = R[j * l + j];
-    for (int i = j + 1 + t; i < l; i += blockDim.x) {
-      double v = R[j * l + i];
-      for (int k = 0; k < j; ++k) v -= R[k * l + j] * R[k * l + i];
-      R[j * l + i] = rjj > 0.0 ? v / rjj : 0.0;
-    }
-    __syncthreads();
-  }
-  for (int e = t; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e - (e / l) * l;
-    if (i > j) R[e] = 0.0;
-  }
-  __syncthreads();
-  for (int j = t; j < l; j += blockDim.x) {
-    for (int i = 0; i < l; ++i) Rinv[i * l + j] = 0.0;
-    if (R[j * l + j] == 0.0) continue;
-    Rinv[j * l + j] = 1.0 / R[j * l + j];
-    for (int i = j - 1; i >= 0; --i) {
-      if (R[i * l + i] == 0.0) continue;
-      double acc = 0.0;
-      for (int k = i + 1; k <= j; ++k) acc += R[i * l + k] * Rinv[k * l + j];
-      Rinv[i * l + j] = -acc / R[i * l + i];
-    }
-  }
-}
-
 // 1/sqrt(a) in float-float for a > 0 in FP32 range: the FP32 estimate y0 and one
 // Newton-Raphson step on f(y) = y^-2 - a, y1 = y0 + y0 (1 - a y0^2) / 2, with the
 // residual 1 - a y0^2 formed in float-float (error about 1e-14 relative).
@@ -298,7 +246,7 @@ __device__ __forceinline__ ff::F2 ff_of(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 
-// Upper Cholesky G = R'R and R^-1 in float-float (l <= 32), one block of
+// Upper Cholesky G = R'R and R^-1 in float-float (l <= 64), one block of
 // CH_THREADS threads, everything in shared memory.  Float-float rather than
 // FP64: FP64 operations have long latency on this GPU and both factorisations
 // are serial chains of l steps (the Gram matrix factored here is itself
@@ -312,41 +260,50 @@ __device__ __forceinline__ ff::F2 ff_of(double x) {
 // Output: R^-1 (l x l row-major, upper triangular) as hi parts Ih and lo parts
 // Il.  Rank-deficient directions (pivot <= 1e-13 of the largest diagonal) get a
 // zero row and column.
-constexpr int CH_THREADS = 128;
+constexpr int CH_THREADS = 256;
+inline size_t chol_ff_smem(int l) { return sizeof(float) * (4 * (size_t)l * (l + 1) + 2 * l + 1); }
+
 __global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __restrict__ G,
                                                         float* __restrict__ Ih,
                                                         float* __restrict__ Il) {
-  __shared__ float Gh[32][33], Gl[32][33];  // trailing matrix, then R by rows
-  __shared__ float Ah[32][33], Al[32][33];  // sums of the inverse's back substitution
-  __shared__ float yh[32], yl[32];          // 1 / R_jj
-  __shared__ float dmax_s;
+  extern __shared__ float chs[];
+  const int ld = l + 1;
+  float* Gh = chs;              // [l][ld] trailing matrix, then R by rows
+  float* Gl = Gh + l * ld;
+  float* Ah = Gl + l * ld;      // [l][ld] sums of the inverse's back substitution
+  float* Al = Ah + l * ld;
+  float* yh = Al + l * ld;      // [l] 1 / R_jj
+  float* yl = yh + l;
+  float* dmax_s = yl + l;
   const int t = threadIdx.x;
   for (int e = t; e < l * l; e += CH_THREADS) {
+    const int i = e / l, k = e - i * l;
     const ff::F2 g = ff_of(G[e]);
-    Gh[e / l][e % l] = g.hi;
-    Gl[e / l][e % l] = g.lo;
-    Ah[e / l][e % l] = 0.f;
-    Al[e / l][e % l] = 0.f;
+    Gh[i * ld + k] = g.hi;
+    Gl[i * ld + k] = g.lo;
+    Ah[i * ld + k] = 0.f;
+    Al[i * ld + k] = 0.f;
   }
   __syncthreads();
   if (t < 32) {
-    float dm = (t < l) ? Gh[t][t] : 0.f;
+    float dm = 0.f;
+    for (int i = t; i < l; i += 32) dm = fmaxf(dm, Gh[i * ld + i]);
     for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    if (t == 0) dmax_s = dm;
+    if (t == 0) *dmax_s = dm;
   }
   __syncthreads();
-  const float dmax = dmax_s;
+  const float dmax = *dmax_s;
 #pragma unroll 1
   for (int j = 0; j < l; ++j) {
     // row j of R (entries k >= j), every thread computing the same 1/sqrt(pivot)
-    const ff::F2 piv = {Gh[j][j], Gl[j][j]};
+    const ff::F2 piv = {Gh[j * ld + j], Gl[j * ld + j]};
     ff::F2 y = ff::make(0.f);
     if (piv.hi > 1e-13f * dmax) y = rsqrt_ff(piv);
     __syncthreads();  // every thread has read the pivot
     for (int k = j + t; k < l; k += CH_THREADS) {
-      const ff::F2 r = ff::mul(k == j ? piv : ff::F2{Gh[j][k], Gl[j][k]}, y);
-      Gh[j][k] = r.hi;
-      Gl[j][k] = r.lo;
+      const ff::F2 r = ff::mul(k == j ? piv : ff::F2{Gh[j * ld + k], Gl[j * ld + k]}, y);
+      Gh[j * ld + k] = r.hi;
+      Gl[j * ld + k] = r.lo;
     }
     if (t == 0) {
       yh[j] = y.hi;
@@ -358,10 +315,11 @@ __global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __r
     for (int e = t; e < m * m; e += CH_THREADS) {
       const int i = j + 1 + e / m, k = j + 1 + e % m;
       if (k < i) continue;
-      const ff::F2 g = ff::sub_mul(ff::F2{Gh[i][k], Gl[i][k]}, ff::F2{Gh[j][i], Gl[j][i]},
-                                   ff::F2{Gh[j][k], Gl[j][k]});
-      Gh[i][k] = g.hi;
-      Gl[i][k] = g.lo;
+      const ff::F2 g = ff::sub_mul(ff::F2{Gh[i * ld + k], Gl[i * ld + k]},
+                                   ff::F2{Gh[j * ld + i], Gl[j * ld + i]},
+                                   ff::F2{Gh[j * ld + k], Gl[j * ld + k]});
+      Gh[i * ld + k] = g.hi;
+      Gl[i * ld + k] = g.lo;
     }
     __syncthreads();
   }
@@ -371,20 +329,23 @@ __global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __r
     const ff::F2 d = {yh[i], yl[i]};
     for (int c = t; c < l; c += CH_THREADS) {
       ff::F2 x = ff::make(0.f);
-      if (c >= i) x = ff::mul(ff::add(ff::make(c == i ? 1.f : 0.f), ff::neg(ff::F2{Ah[i][c], Al[i][c]})), d);
+      if (c >= i)
+        x = ff::mul(ff::add(ff::make(c == i ? 1.f : 0.f), ff::neg(ff::F2{Ah[i * ld + c], Al[i * ld + c]})),
+                    d);
       Ih[i * l + c] = x.hi;
       Il[i * l + c] = x.lo;
-      Ah[i][c] = x.hi;  // row i of the sums is dead: keep x there for the update
-      Al[i][c] = x.lo;
+      Ah[i * ld + c] = x.hi;  // row i of the sums is dead: keep x there for the update
+      Al[i * ld + c] = x.lo;
     }
     __syncthreads();
     for (int e = t; e < i * l; e += CH_THREADS) {
       const int k = e / l, c = e % l;
       if (c < i) continue;
-      const ff::F2 a = ff::add(ff::F2{Ah[k][c], Al[k][c]},
-                               ff::mul(ff::F2{Gh[k][i], Gl[k][i]}, ff::F2{Ah[i][c], Al[i][c]}));
-      Ah[k][c] = a.hi;
-      Al[k][c] = a.lo;
+      const ff::F2 a = ff::add(ff::F2{Ah[k * ld + c], Al[k * ld + c]},
+                               ff::mul(ff::F2{Gh[k * ld + i], Gl[k * ld + i]},
+                                       ff::F2{Ah[i * ld + c], Al[i * ld + c]}));
+      Ah[k * ld + c] = a.hi;
+      Al[k * ld + c] = a.lo;
     }
     __syncthreads();
   }
@@ -399,7 +360,7 @@ __global__ void __launch_bounds__(256) k_apply_ff(int P, int l, const TX* __rest
                                                   const float* __restrict__ Ih,
                                                   const float* __restrict__ Il,
                                                   TX* __restrict__ Q) {
-  __shared__ float sh[32 * 32], sl[32 * 32];
+  __shared__ float sh[64 * 64], sl[64 * 64];
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     sh[e] = Ih[e];
     sl[e] = Il[e];
@@ -420,24 +381,6 @@ __global__ void __launch_bounds__(256) k_apply_ff(int P, int l, const TX* __rest
     acc = ff::add(acc, ff::mul(yk, ff::F2{sh[k * l + j], sl[k * l + j]}));
   }
   Q[e] = (TX)ff::to_double(acc);
-}
-
-// Q = Y Rinv (row-wise).
-template <typename TX>
-__global__ void k_apply_rinv(int P, int l, const TX* __restrict__ Y, const double* __restrict__ Rinv,
-                             TX* __restrict__ Q) {
-  extern __shared__ double rs[];
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) rs[e] = Rinv[e];
-  __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= P) return;
-  double yr[128];
-  for (int i = 0; i < l; ++i) yr[i] = (double)Y[(long long)r * l + i];
-  for (int j = 0; j < l; ++j) {
-    double s = 0.0;
-    for (int i = 0; i <= j; ++i) s += yr[i] * rs[i * l + j];
-    Q[(long long)r * l + j] = (TX)s;
-  }
 }
 
 // Cyclic parallel Jacobi (one block) on the symmetric n x n matrix A (global,
@@ -645,7 +588,7 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
 }
 
 // Symmetric eigendecomposition of the n x n (n <= 64) Rayleigh-Ritz matrix with an
-// FP64 result at a fraction of the FP64 work (GB300 runs FP64 at 1/64 of FP32):
+// FP64 result at a fraction of the FP64 work (FP64 is slow on this GPU):
 //  1. cyclic Jacobi in FP32 on (A + A')/2 (off-diagonal to 3e-5 of the diagonal, at
 //     most 10 sweeps: FP32 rounding stalls it near 1e-7), one block;
 //  2. two steps of the iterative refinement of Ogita and Aishima ("Iterative
@@ -654,7 +597,7 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
 //     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs and
 //     r_ij / 2 inside clusters (gap <= delta = 2(|S - diag S| + |A| |R|), Frobenius
 //     norms), X <- X + X E.  Each step squares the error, so two steps reach FP64.
-//     The n x n x n FP64 products run one output row per block.
+//     Both steps run in one block (k_rr_refine).
 // Outputs: A <- diag(lambda), V <- eigenvectors (columns, FP64).
 __global__ void __launch_bounds__(1024)
     k_rr_jacobi32(int n, double* __restrict__ Ag, double* __restrict__ Asym,
@@ -675,82 +618,6 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
   jacobi_sweeps<float>(n, n + 1, A32, V32, 10, 1e-9, cs32, pr, red, &done);
   for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * (n + 1) + e % n];
-}
-
-// Row i (block) of C = op(L) M (+ D): op(L) = L' when tl, else L; one thread per column.
-__global__ void k_rr_rowmm(int n, const double* __restrict__ L, int tl, const double* __restrict__ M,
-                           double* __restrict__ C, double diag, double sign) {
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (j >= n) return;
-  double s = 0.0;
-  for (int k = 0; k < n; ++k) s += (tl ? L[k * n + i] : L[i * n + k]) * M[k * n + j];
-  C[i * n + j] = ((i == j) ? diag : 0.0) + sign * s;
-}
-
-// lambda, the cluster threshold and E (one block).
-__global__ void __launch_bounds__(1024)
-    k_rr_correction(int n, const double* __restrict__ A, const double* __restrict__ R,
-                    const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam) {
-  __shared__ double red[32][3];
-  __shared__ double lm[64];
-  __shared__ double delta;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) lm[i] = S[i * n + i] / (1.0 - R[i * n + i]);
-  double so = 0.0, an = 0.0, rn = 0.0;
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e - (e / n) * n;
-    if (i != j) so += S[e] * S[e];
-    an += A[e] * A[e];
-    rn += R[e] * R[e];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    so += __shfl_xor_sync(0xffffffffu, so, o);
-    an += __shfl_xor_sync(0xffffffffu, an, o);
-    rn += __shfl_xor_sync(0xffffffffu, rn, o);
-  }
-  if ((tid & 31) == 0) {
-    red[tid >> 5][0] = so;
-    red[tid >> 5][1] = an;
-    red[tid >> 5][2] = rn;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int w = 0; w < nt / 32; ++w) {
-      a += red[w][0];
-      b += red[w][1];
-      c += red[w][2];
-    }
-    delta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e - (e / n) * n;
-    const double gap = lm[j] - lm[i];
-    E[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lm[j] * R[e]) / gap;
-  }
-  for (int i = tid; i < n; i += nt) lam[i] = lm[i];
-}
-
-// X <- X + X E (row i per block; the row is read before it is written).
-__global__ void k_rr_update(int n, double* __restrict__ X, const double* __restrict__ E) {
-  __shared__ double row[64];
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (j < n) row[j] = X[i * n + j];
-  __syncthreads();
-  if (j >= n) return;
-  double s = row[j];
-  for (int k = 0; k < n; ++k) s += row[k] * E[k * n + j];
-  X[i * n + j] = s;
-}
-
-__global__ void k_rr_out(int n, const double* __restrict__ lam, const double* __restrict__ X,
-                         double* __restrict__ Ag, double* __restrict__ Vg) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
-    const int i = e / n, j = e - (e / n) * n;
-    Ag[e] = (i == j) ? lam[i] : 0.0;
-    Vg[e] = X[e];
-  }
 }
 
 // Rank of each eigenvalue (descending; ties by index) -> order[rank] = index.
@@ -839,7 +706,7 @@ __global__ void k_finish(int P, int n, int k, double dv, const double* __restric
 }
 
 // Both Ogita-Aishima refinement steps of k_rr_jacobi32's eigenvectors in one block
-// (l <= 32), with the l x l matrices in shared memory: per step
+// (l <= 64), with the l x l matrices in shared memory: per step
 // R = I - X'X, U = A X, S = X'U, lambda_i = s_ii / (1 - r_ii),
 // delta = 2 (|S - diag S| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
 // or r_ij / 2 inside clusters, X <- X + X E; then A <- diag(lambda), V <- X.
@@ -887,12 +754,19 @@ __device__ __forceinline__ double rf_block_sum(double v, double* red) {
   return r;
 }
 
+inline size_t rr_refine_smem(int n) { return sizeof(double) * (5 * (size_t)n * n + n + 33); }
+
 __global__ void __launch_bounds__(RF_THREADS)
     k_rr_refine(int n, const double* __restrict__ Asym, const double* __restrict__ X0,
                 double* __restrict__ Ag, double* __restrict__ Vg) {
-  __shared__ double A[32 * 32], X[32 * 32], R[32 * 32], U[32 * 32], S[32 * 32];
-  __shared__ double lam[32];
-  __shared__ double red[33];
+  extern __shared__ double rfs[];
+  double* A = rfs;
+  double* X = A + n * n;
+  double* R = X + n * n;
+  double* U = R + n * n;
+  double* S = U + n * n;
+  double* lam = S + n * n;
+  double* red = lam + n;  // [33]
   const int t = threadIdx.x, nn = n * n;
   for (int e = t; e < nn; e += RF_THREADS) {
     A[e] = Asym[e];
@@ -936,36 +810,16 @@ __global__ void __launch_bounds__(RF_THREADS)
 // holds 5 l^2 + l doubles.
 fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double* scratch) {
   const size_t nn = (size_t)l * l;
-  double* As = scratch;
-  double* X = As + nn;
-  double* R = X + nn;
-  double* U = R + nn;
-  double* S = U + nn;
-  double* lam = S + nn;
-  double* E = U;  // U is dead once S is formed
+  double* As = scratch;   // symmetrised input
+  double* X = As + nn;    // FP32 Jacobi eigenvectors, refined in place by k_rr_refine
   // one thread per element of a step's rotations (np pairs x l): wider blocks only
   // make the three barriers of every step dearer
   const int jt = min(1024, max(64, ((((l + 1) & ~1) / 2 * l + 31) / 32) * 32));
   k_rr_jacobi32<<<1, jt, 0, ctx->stream>>>(l, A, As, X);
   FPCA_LAUNCHED(ctx, "jacobi");
-  if (l <= 32) {
-    k_rr_refine<<<1, RF_THREADS, 0, ctx->stream>>>(l, As, X, A, V);
-    FPCA_LAUNCHED(ctx, "jacobi");
-    return FPCA_OK;
-  }
-  for (int step = 0; step < 2; ++step) {
-    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
-    FPCA_LAUNCHED(ctx, "jacobi");
-    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, As, 0, X, U, 0.0, 1.0);   // U = A X
-    FPCA_LAUNCHED(ctx, "jacobi");
-    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, U, S, 0.0, 1.0);    // S = X' A X
-    FPCA_LAUNCHED(ctx, "jacobi");
-    k_rr_correction<<<1, 1024, 0, ctx->stream>>>(l, As, R, S, E, lam);
-    FPCA_LAUNCHED(ctx, "jacobi");
-    k_rr_update<<<l, 64, 0, ctx->stream>>>(l, X, E);
-    FPCA_LAUNCHED(ctx, "jacobi");
-  }
-  k_rr_out<<<(int)((nn + 255) / 256), 256, 0, ctx->stream>>>(l, lam, X, A, V);
+  cudaFuncSetAttribute(k_rr_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)rr_refine_smem(l));
+  k_rr_refine<<<1, RF_THREADS, rr_refine_smem(l), ctx->stream>>>(l, As, X, A, V);
   FPCA_LAUNCHED(ctx, "jacobi");
   return FPCA_OK;
 }
@@ -997,24 +851,20 @@ fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, T
 template <typename TS>
 fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, double* Rinv,
                       double* work, double* part, int passes = 2) {
+  (void)work;
   for (int pass = 0; pass < passes; ++pass) {
     TS* src = pass == 0 ? Y : Q;
     fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
     if (gs != FPCA_OK) return gs;
-    if (l <= 32) {
-      // Rinv holds R^-1 as hi and lo parts
-      float* Ih = reinterpret_cast<float*>(Rinv);
-      float* Il = Ih + l * l;
-      k_chol_ff<<<1, CH_THREADS, 0, ctx->stream>>>(l, G, Ih, Il);
-      FPCA_LAUNCHED(ctx, "chol_inv");
-      const long long ne = (long long)P * l;
-      k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, Q);
-      FPCA_LAUNCHED(ctx, "apply_rinv");
-      continue;
-    }
-    k_chol_inv<<<1, 64, 0, ctx->stream>>>(l, G, Rinv, work);
+    // Rinv holds R^-1 as hi and lo parts (l <= 64)
+    float* Ih = reinterpret_cast<float*>(Rinv);
+    float* Il = Ih + l * l;
+    cudaFuncSetAttribute(k_chol_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)chol_ff_smem(l));
+    k_chol_ff<<<1, CH_THREADS, chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
     FPCA_LAUNCHED(ctx, "chol_inv");
-    k_apply_rinv<TS><<<(P + 127) / 128, 128, sizeof(double) * l * l, ctx->stream>>>(P, l, src, Rinv, Q);
+    const long long ne = (long long)P * l;
+    k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, Q);
     FPCA_LAUNCHED(ctx, "apply_rinv");
   }
   return FPCA_OK;
