@@ -98,6 +98,9 @@ typedef struct {
   const void* w;           /* sum of subject weights 1/(N_i(N_i-1)) */
   const void* v;           /* sum of weighted response products */
   const void* q;           /* sum of weighted squared products (CV), or NULL */
+  int asym;                /* 0: cnt, w, v, q are symmetric in (s, t), as fpca_bin_cov
+                              makes them, and the smoother may evaluate t >= s only
+                              and mirror; nonzero: arbitrary bins, every pair fitted */
 } fpca_covbins;
 
 typedef struct fpca_ctx fpca_ctx;

@@ -72,6 +72,7 @@ class CovBins(ctypes.Structure):
         ("w", ctypes.c_void_p),
         ("v", ctypes.c_void_p),
         ("q", ctypes.c_void_p),
+        ("asym", ctypes.c_int),
     ]
 
 
@@ -336,8 +337,10 @@ class Context:
                                           _ptr(cnt), _ptr(w), _ptr(v), _ptr(q)))
 
     def smooth_cov_project(self, m, cnt, w, v, h, prec, q=None, nfold=0, mu_raw=None, omega=None,
-                           gamma=None, status=None, y=None, cv=None):
+                           gamma=None, status=None, y=None, cv=None, symmetric=True):
+        """symmetric=False for bins that are not symmetric in (s, t) (fpca_bin_cov's are)."""
         bins = CovBins()
+        bins.asym = 0 if symmetric else 1
         bins.nfold = int(nfold)
         bins.prec = F64 if w.dtype.itemsize == 8 else F32
         bins.cnt, bins.w, bins.v = cnt.data_ptr(), w.data_ptr(), v.data_ptr()

@@ -730,6 +730,7 @@ struct Hs2Geom {
   int nrp;           // input rows held per block: HT + ntr (the window preloads one spare row)
   int RS;            // mid row stride (odd, >= C + ntc)
   int SC;            // slot row stride (odd, >= C)
+  int half;          // evaluate only t >= s (flat node order); see k_mirror_lower
 };
 
 template <bool COMP>
@@ -920,6 +921,9 @@ __global__ void __launch_bounds__(NT2, 2)
   const int a0 = blockIdx.x * HT;
   const int th = min(HT, R - a0);
   const long long PP = (long long)P * P;
+  // Gamma_hat(s, t) = Gamma_hat(t, s) exactly (one bandwidth for s and t, symmetric
+  // bins), so in half mode a block whose t-rows all lie before s has nothing to do
+  if (g.half && (a0 + th) * C <= xs) return;
 
   // input rows a0 - Tr .. a0 - Tr + nrp - 1 of the t-plane, zero outside [0, R):
   // the in-grid rows of each array are one contiguous run in global memory,
@@ -1011,6 +1015,7 @@ __global__ void __launch_bounds__(NT2, 2)
     xts[j] = -1;
     if (e >= th * C) continue;
     const int i = e / C, c = e % C;
+    if (g.half && (a0 + i) * C + c < xs) continue;  // taken from the mirror (t, s)
     const float* sl = slots + (size_t)i * g.SC + c;
     float A[5][5], rv[5];
 #pragma unroll
@@ -1054,12 +1059,14 @@ __global__ void __launch_bounds__(NT2, 2)
     xts[j] = xt;
     gval[j] = st == FPCA_PT_EMPTY ? 0.f : gv;
     if (ep.cvacc) {
+      // in half mode (s, t) also stands for (t, s): the CV bins are symmetric
+      const float mul = (g.half && xt != xs) ? 2.f : 1.f;
       const float wf = ep.wf[o];
       if (st == FPCA_PT_EMPTY) {
-        cv_out += wf;
+        cv_out += mul * wf;
       } else {
-        cv_err += ep.qf[o] - 2.f * gv * ep.vf[o] + gv * gv * wf;
-        cv_in += wf;
+        cv_err += mul * (ep.qf[o] - 2.f * gv * ep.vf[o] + gv * gv * wf);
+        cv_in += mul * wf;
       }
     }
   }
@@ -1364,7 +1371,8 @@ size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
 __global__ void __launch_bounds__(256)
     k_escalated(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
                 const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,
-                float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep) {
+                float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep,
+                int half) {
   const unsigned n = min(*esc_count, (unsigned)cap);
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const float* sl = esc_slots + (size_t)e * NSL;
@@ -1425,13 +1433,39 @@ __global__ void __launch_bounds__(256)
     if (gamma) gamma[o] = gv;
     if (status) status[o] = st;
     if (ep.cvacc) {
+      const double mul = (half && id.y != id.x) ? 2.0 : 1.0;  // (s, t) stands for (t, s) too
       const double wf = (double)ep.wf[o];
-      atomicAdd(ep.cvacc + 0, (double)ep.qf[o] - 2.0 * g * (double)ep.vf[o] + g * g * wf);
-      atomicAdd(ep.cvacc + 1, wf);
+      atomicAdd(ep.cvacc + 0, mul * ((double)ep.qf[o] - 2.0 * g * (double)ep.vf[o] + g * g * wf));
+      atomicAdd(ep.cvacc + 1, mul * wf);
     }
     if (ep.y)
       for (int c = 0; c < ep.l; ++c)
         atomicAdd(ep.y + (long long)id.x * ep.l + c, gv * ep.omega[(long long)id.y * ep.l + c]);
+  }
+}
+
+// Lower triangle (t < s in flat node order) of Gamma_hat and of its status from
+// the upper one after a half-mode t-side sweep (Gamma_hat(t, s) = Gamma_hat(s, t)):
+// 32 x 32 tiles transposed through shared memory.
+__global__ void k_mirror_lower(int P, float* __restrict__ gamma, uint8_t* __restrict__ status) {
+  __shared__ float tg[32][33];
+  __shared__ uint8_t ts[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // destination rows bi*32.., columns bj*32..
+  if (bj > bi) return;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int sr = bj * 32 + r, sc = bi * 32 + threadIdx.x;  // source tile (bj, bi)
+    if (sr < P && sc < P) {
+      if (gamma) tg[r][threadIdx.x] = gamma[(long long)sr * P + sc];
+      if (status) ts[r][threadIdx.x] = status[(long long)sr * P + sc];
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int dr = bi * 32 + r, dc = bj * 32 + threadIdx.x;
+    if (dr < P && dc < dr) {
+      if (gamma) gamma[(long long)dr * P + dc] = tg[threadIdx.x][r];
+      if (status) status[(long long)dr * P + dc] = ts[threadIdx.x][r];
+    }
   }
 }
 
@@ -1539,7 +1573,8 @@ template <typename T, bool COMP>
 fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const T* w,
                            const T* v, const int32_t* sub_cnt, const T* sub_w, const T* sub_v,
                            const double* h, const double* tab, T* mids, T* varr,
-                           const double* mu_raw, T* gamma, uint8_t* status, Epilogue<T> ep) {
+                           const double* mu_raw, T* gamma, uint8_t* status, Epilogue<T> ep,
+                           bool symmetric) {
   const int d = g->d;
   const int P = grid_P(g);
   const long long PP = (long long)P * P;
@@ -1570,13 +1605,16 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     // t-side + solve
     if constexpr (sizeof(T) == 4) {
       if (M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) {
-        const Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
+        Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
         const size_t sm2 = hs2_smem(hg);
         if (sm2 <= ctx->smem_optin) {
           const dim3 grid((M1 + HT - 1) / HT, P);
           const float* va = reinterpret_cast<const float*>(varr);
           float* gm = reinterpret_cast<float*>(gamma);
           const Epilogue<float>& ef = *reinterpret_cast<const Epilogue<float>*>(&ep);
+          // symmetric bins: t >= s only, the rest mirrored (the fused y = Gamma_hat Omega
+          // needs every row)
+          hg.half = (symmetric && !ef.y) ? 1 : 0;
           if (ef.esc_count) cudaMemsetAsync(ef.esc_count, 0, sizeof(unsigned), ctx->stream);
           switch (M2) {
             case 8: launch_hsolve2<COMP, 8>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
@@ -1587,8 +1625,14 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
           FPCA_LAUNCHED(ctx, "cov_hpass_solve");
           if (ef.esc_count) {
             k_escalated<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-                P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef);
+                P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef,
+                hg.half);
             FPCA_LAUNCHED(ctx, "cov_escalated");
+          }
+          if (hg.half && (gm || status)) {
+            const int nt = (P + 31) / 32;
+            k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>(P, gm, status);
+            FPCA_LAUNCHED(ctx, "cov_mirror");
           }
           return FPCA_OK;
         }
@@ -1707,7 +1751,7 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
       fpca_status s = cov_smooth_one<T, COMP>(
           ctx, g, cnt, w, v, nullptr, nullptr, nullptr, hh, tab, mids, varr, mu_raw,
           gamma ? gamma + (size_t)ih * PP : nullptr, status ? status + (size_t)ih * PP : nullptr,
-          ep);
+          ep, bins->asym == 0);
       if (s != FPCA_OK) return s;
     }
     // K-fold CV: fit on the other folds, score the held-out fold
@@ -1724,7 +1768,8 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
         ep.cvacc = cvacc + 3 * ((size_t)ih * F + f);
         fpca_status s = cov_smooth_one<T, COMP>(
             ctx, g, cnt, w, v, bins->cnt + (size_t)f * PP, fw + (size_t)f * PP,
-            fv + (size_t)f * PP, hh, tab, mids, varr, mu_raw, nullptr, nullptr, ep);
+            fv + (size_t)f * PP, hh, tab, mids, varr, mu_raw, nullptr, nullptr, ep,
+            bins->asym == 0);
         if (s != FPCA_OK) return s;
       }
     }

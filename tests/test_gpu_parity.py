@@ -240,16 +240,21 @@ def test_smooth_cov_affine_and_symmetry_through_abi(ctx, B):
     W = A + A.T
     np.fill_diagonal(W, 0.0)
     C = (W > 0).astype(np.int32)
-    truth = 0.4 + (c @ np.array([1.0, -2.0]))[:, None] + (c @ np.array([0.5, 0.3]))[None, :]
+    # an affine surface that is not symmetric in (s, t) (bins flagged as such: every
+    # pair fitted) and a symmetric one (t >= s fitted, the rest mirrored)
+    truth_a = 0.4 + (c @ np.array([1.0, -2.0]))[:, None] + (c @ np.array([0.5, 0.3]))[None, :]
+    truth_s = 0.4 + (c @ np.array([1.0, -2.0]))[:, None] + (c @ np.array([1.0, -2.0]))[None, :]
     h = (0.3, 0.35)
-    for prec, dt, tol in ((B.F64, torch.float64, 1e-10), (B.F32, torch.float32, 2e-4)):
-        G = torch.empty(P, P, dtype=dt, device=DEV)
-        st = torch.empty(P, P, dtype=torch.uint8, device=DEV)
-        ctx.smooth_cov_project(m, dev(C), dev(W, dt), dev(W * truth, dt), [h], prec, gamma=G, status=st)
-        ctx.sync()
-        ok = host(st) == sm.STATUS_OK
-        assert ok.mean() > 0.9
-        assert np.max(np.abs(host(G).astype(np.float64)[ok] - truth[ok])) <= tol * np.abs(truth).max()
+    for truth, symmetric in ((truth_a, False), (truth_s, True)):
+        for prec, dt, tol in ((B.F64, torch.float64, 1e-10), (B.F32, torch.float32, 2e-4)):
+            G = torch.empty(P, P, dtype=dt, device=DEV)
+            st = torch.empty(P, P, dtype=torch.uint8, device=DEV)
+            ctx.smooth_cov_project(m, dev(C), dev(W, dt), dev(W * truth, dt), [h], prec, gamma=G,
+                                   status=st, symmetric=symmetric)
+            ctx.sync()
+            ok = host(st) == sm.STATUS_OK
+            assert ok.mean() > 0.9
+            assert np.max(np.abs(host(G).astype(np.float64)[ok] - truth[ok])) <= tol * np.abs(truth).max()
     # symmetric responses give a symmetric surface
     Bm = rng.standard_normal((P, P))
     Vs = W * (Bm + Bm.T)
