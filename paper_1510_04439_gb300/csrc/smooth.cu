@@ -1248,6 +1248,7 @@ template <int NP, bool COMP>
 __device__ __forceinline__ void vpass2_line(const VJob& jb, const float* tile, const float* wp,
                                             int ntp, int Ma, int stride, long long base, int P,
                                             int col) {
+  // Ma: the rows of the line computed here (a prefix of it, see SBand)
   const float4* w4[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) w4[q] = reinterpret_cast<const float4*>(wp + jb.row[q] * ntp);
@@ -1267,10 +1268,22 @@ __device__ __forceinline__ void vpass2_line(const VJob& jb, const float* tile, c
   }
 }
 
+// The part of the s-side outputs that a half-mode t-side sweep (t >= s) reads, for
+// d = 2: entry (s1, s2; t1, t2) is read iff t1 >= HT floor(s1 / HT) - T0 (the blocks
+// of t-rows that reach past s, widened by the t1 window).  For a column block whose
+// largest t1 is t1max that means s1 < need = HT (floor((t1max + T0) / HT) + 1).
+// mode 1 (the s2 pass, one line per s1): a line is skipped when s1 >= need + T0 (the
+// s1 pass reads s1 +- T0); mode 2 (the s1 pass, lines along s1): rows s1 < need are
+// computed from the rows s1 < need + T0.
+struct SBand {
+  int mode;  // 0: every row
+  int R, C, T0;
+};
+
 template <bool COMP>
 __global__ void __launch_bounds__(VCOLS)
     k_vpass2(VJobs jobs, int P, int Ma, int stride, int taps, int ntp,
-             const double* __restrict__ tab, int bulk, int* __restrict__ err) {
+             const double* __restrict__ tab, int bulk, SBand band, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char vsm2[];
   __shared__ __align__(8) uint64_t vbar;
   float* wp = reinterpret_cast<float*>(vsm2);  // [TROWS][ntp]
@@ -1282,6 +1295,17 @@ __global__ void __launch_bounds__(VCOLS)
   const int col = col0 + threadIdx.x;
   const int L = blockIdx.y;
   const long long base = (long long)(L / stride) * Ma * stride + (L % stride);
+  int Mcomp = Ma, Mload = Ma;  // rows computed, rows read
+  if (band.mode) {
+    const int t1max = min(band.R - 1, (min(P, col0 + VCOLS) - 1) / band.C);
+    const int need = min(band.R, ((t1max + band.T0) / HT + 1) * HT);
+    if (band.mode == 1) {
+      if (L >= min(band.R, need + band.T0)) return;  // this line's s1 is never read
+    } else {
+      Mcomp = min(Ma, need);
+      Mload = min(Ma, need + band.T0);
+    }
+  }
   if (bulk) {
     // one bulk copy per tile row (and per fold row), all on one mbarrier
     const int ncols = min(VCOLS, P - col0);
@@ -1293,10 +1317,10 @@ __global__ void __launch_bounds__(VCOLS)
     }
     __syncthreads();
     const int nsrc = jb.sub ? 2 : 1;
-    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(bar, rbytes * (uint32_t)(Ma * nsrc));
+    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(bar, rbytes * (uint32_t)(Mload * nsrc));
     __syncwarp();
     if (threadIdx.x < 32) {
-      for (int x = threadIdx.x; x < Ma; x += 32) {
+      for (int x = threadIdx.x; x < Mload; x += 32) {
         const long long e = (base + (long long)x * stride) * P + col0;
         ptx::bulk_load(ptx::smem_u32(tile + (size_t)(x + taps) * VCOLS),
                        static_cast<const float*>(jb.in) + e, rbytes, bar);
@@ -1307,11 +1331,11 @@ __global__ void __launch_bounds__(VCOLS)
     }
     load_padded_weights(tab, taps, ntp, wp);
     for (int r = 0; r < nrow; ++r)
-      if (r < taps || r >= taps + Ma) tile[(size_t)r * VCOLS + threadIdx.x] = 0.f;
+      if (r < taps || r >= taps + Mload) tile[(size_t)r * VCOLS + threadIdx.x] = 0.f;
     const bool landed = ptx::mbar_wait(bar, 0, err);
     if (__syncthreads_or(!landed)) return;
     if (jb.in_int || jb.sub) {
-      for (int x = 0; x < Ma; ++x) {
+      for (int x = 0; x < Mload; ++x) {
         float* tv = tile + (size_t)(x + taps) * VCOLS + threadIdx.x;
         if (jb.in_int) {
           int c = __float_as_int(*tv);
@@ -1331,7 +1355,7 @@ __global__ void __launch_bounds__(VCOLS)
       for (int u = 0; u < 8; ++u) {
         const int x = r0 + u - taps;
         float val = 0.f;
-        if (col < P && x >= 0 && x < Ma && r0 + u < nrow) {
+        if (col < P && x >= 0 && x < Mload && r0 + u < nrow) {
           const long long e = (base + (long long)x * stride) * P + col;
           if (jb.in_int) {
             int c = __ldg(static_cast<const int32_t*>(jb.in) + e);
@@ -1352,11 +1376,11 @@ __global__ void __launch_bounds__(VCOLS)
   __syncthreads();
   if (col >= P) return;
   if (jb.npow == 3)
-    vpass2_line<3, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+    vpass2_line<3, COMP>(jb, tile, wp, ntp, Mcomp, stride, base, P, col);
   else if (jb.npow == 2)
-    vpass2_line<2, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+    vpass2_line<2, COMP>(jb, tile, wp, ntp, Mcomp, stride, base, P, col);
   else
-    vpass2_line<1, COMP>(jb, tile, wp, ntp, Ma, stride, base, P, col);
+    vpass2_line<1, COMP>(jb, tile, wp, ntp, Mcomp, stride, base, P, col);
 }
 
 size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
@@ -1538,7 +1562,7 @@ void launch_hsolve2(fpca_ctx* ctx, dim3 grid, size_t smem, const float* varr, co
 // stride `stride`, `lines` lines.  FP32 uses the sliding-window kernel.
 template <typename T, bool COMP>
 bool launch_vpass(fpca_ctx* ctx, const VJobs& jobs, int njobs, int P, int Ma, int stride, int lines,
-                  int taps, const double* tab) {
+                  int taps, const double* tab, SBand band = SBand{}) {
   const dim3 grid((P + VCOLS - 1) / VCOLS, lines, njobs);
   if constexpr (sizeof(T) == 4) {
     const int ntp = ((2 * taps + 1) + 3) / 4 * 4;
@@ -1554,7 +1578,7 @@ bool launch_vpass(fpca_ctx* ctx, const VJobs& jobs, int njobs, int P, int Ma, in
       attr = true;
     }
     k_vpass2<COMP><<<grid, VCOLS, sm, ctx->stream>>>(jobs, P, Ma, stride, taps, ntp, tab, bulk,
-                                                     ctx->d_err);
+                                                     band, ctx->d_err);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -1582,12 +1606,21 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
   auto tabk = [&](int k) { return tab + (size_t)k * TROWS * TW; };
   if (d == 2) {
     const int M1 = g->m[0], M2 = g->m[1];
+    // Will the t-side run in half mode (FP32 sweep kernel, symmetric bins, no fused
+    // y)?  Then the s-side passes only produce the band it reads (SBand).
+    bool half2 = false;
+    if constexpr (sizeof(T) == 4) {
+      if ((M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) && symmetric && !ep.y)
+        half2 = hs2_smem(hs2_geometry(P, M1, M2, Tax[0], Tax[1])) <= ctx->smem_optin;
+    }
+    const SBand band1{half2 ? 1 : 0, M1, M2, Tax[0]};
+    const SBand band2{half2 ? 2 : 0, M1, M2, Tax[0]};
     // pass along s2 (axis 1): rows L*M2 + a
     VJobs j1{};
     j1.j[0] = VJob{w, sub_w, 0, 3, {0, 1, 2}, {mids + 0 * PP, mids + 1 * PP, mids + 2 * PP}};
     j1.j[1] = VJob{v, sub_v, 0, 2, {0, 1, 0}, {mids + 3 * PP, mids + 4 * PP, nullptr}};
     j1.j[2] = VJob{cnt, sub_cnt, 1, 1, {3, 0, 0}, {mids + 5 * PP, nullptr, nullptr}};
-    if (!launch_vpass<T, COMP>(ctx, j1, 3, P, M2, 1, M1, Tax[1], tabk(1)))
+    if (!launch_vpass<T, COMP>(ctx, j1, 3, P, M2, 1, M1, Tax[1], tabk(1), band1))
       return fpca_check_launch(ctx, "cov_vpass_s2");
     FPCA_LAUNCHED(ctx, "cov_vpass_s2");
     // pass along s1 (axis 0): rows L + a*M2
@@ -1599,7 +1632,7 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     j2.j[3] = VJob{mids + 3 * PP, nullptr, 0, 2, {0, 1, 0}, {varr + 6 * PP, varr + 7 * PP, nullptr}};
     j2.j[4] = VJob{mids + 4 * PP, nullptr, 0, 1, {0, 0, 0}, {varr + 8 * PP, nullptr, nullptr}};
     j2.j[5] = VJob{mids + 5 * PP, nullptr, 0, 1, {3, 0, 0}, {varr + 9 * PP, nullptr, nullptr}};
-    if (!launch_vpass<T, COMP>(ctx, j2, 6, P, M1, M2, M2, Tax[0], tabk(0)))
+    if (!launch_vpass<T, COMP>(ctx, j2, 6, P, M1, M2, M2, Tax[0], tabk(0), band2))
       return fpca_check_launch(ctx, "cov_vpass_s1");
     FPCA_LAUNCHED(ctx, "cov_vpass_s1");
     // t-side + solve
@@ -1613,8 +1646,8 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
           float* gm = reinterpret_cast<float*>(gamma);
           const Epilogue<float>& ef = *reinterpret_cast<const Epilogue<float>*>(&ep);
           // symmetric bins: t >= s only, the rest mirrored (the fused y = Gamma_hat Omega
-          // needs every row)
-          hg.half = (symmetric && !ef.y) ? 1 : 0;
+          // needs every row); decided above with the s-side band
+          hg.half = half2 ? 1 : 0;
           if (ef.esc_count) cudaMemsetAsync(ef.esc_count, 0, sizeof(unsigned), ctx->stream);
           switch (M2) {
             case 8: launch_hsolve2<COMP, 8>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
