@@ -141,9 +141,10 @@ def bench_fused3(torch, np, fs, B, ctx, dev, stream, flush, shape=(32, 2000)):
 
 
 def bench_scores(torch, np, B, ctx, D, bufs, y, mask, stream, flush, reps=5):
-    """Noise variance (Eq. 2.5-2.6), PACE scores (Eq. 2.7), scores by integration
-    and reconstruction on the dense workload's own fit (mu, Gamma_hat diagonal,
-    the k eigenpairs), each timed per launch with the profiler."""
+    """Noise variance (Eq. 2.5-2.6), PACE scores (Eq. 2.7), scores by integration,
+    reconstruction and its MISE against the observations (the true curves are
+    not kept) on the dense workload's own fit (mu, Gamma_hat diagonal, the k
+    eigenpairs), each timed per launch with the profiler."""
     P, n = D.P, D.n
     dev = y.device
     sig_t = torch.empty(P, dtype=torch.float64, device=dev)
@@ -159,7 +160,9 @@ def bench_scores(torch, np, B, ctx, D, bufs, y, mask, stream, flush, reps=5):
         ctx.scores_pace(data, D.m, bufs.mu, bufs.evals, bufs.evecs, K_EIG, s2, pace)
         ctx.scores_integral(data, D.m, bufs.mu, bufs.evecs, K_EIG, integ)
         ctx.reconstruct(D.m, bufs.mu, bufs.evecs, K_EIG, pace, n, xhat)
+        ctx.mise(D.m, xhat, y, n, mise)
 
+    mise = torch.empty(1, dtype=torch.float64, device=dev)
     run()
     ctx.sync()
     ctx.profile(True)
@@ -174,7 +177,8 @@ def bench_scores(torch, np, B, ctx, D, bufs, y, mask, stream, flush, reps=5):
     # algorithmic bytes: y (FP32) and mask read once; xhat written once (FP32)
     yb = n * P * (y.element_size() + mask.element_size())
     out = {"workload": f"dense_2d_disk_64x64_n{n}_L{K_EIG}", "sigma2": float(s2.item()),
-           "sigma2_true": D.sigma ** 2, "ms_per_launch": per}
+           "sigma2_true": D.sigma ** 2, "ms_per_launch": per,
+           "mise_vs_observations": float(mise.item())}
     if "scores_integral" in per:
         out["scores_integral_gbs"] = yb / (per["scores_integral"] * 1e-3) / 1e9
     if "scores_pace" in per:

@@ -323,7 +323,9 @@ fpca_status fpca_sigma2(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt
  *   A_i = Lambda Phi_i' (Phi_i Lambda Phi_i' + sigma^2 I)^{-1} (Y_i - mu(t_i)),
  * evaluated through the push-through identity as the L x L system
  *   (sigma^2 Lambda^{-1} + Phi_i' Phi_i) A_i = Phi_i' (Y_i - mu(t_i))
- * (FP64 accumulation, FP64 Cholesky).  Gridded data (mask or all nodes) and
+ * (sums in compensated FP32 -- error-free products and additions on
+ * float-float inputs, about FP64 accuracy -- then an FP64 Cholesky).  Gridded
+ * data (mask or all nodes) and
  * scattered data (offs, t) are both accepted.  A subject without observations
  * gets A_i = 0 (the prior mean).  sigma2 is ONE device double (e.g. the output
  * of fpca_sigma2, so no host round trip separates the two calls); it must be
@@ -334,10 +336,14 @@ fpca_status fpca_sigma2(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt
  *
  * fpca_scores_integral: the integral of (Y_i - mu) phi_l over Omega as the
  * Riemann sum over the subject's observed nodes, cell volume dV = 1/P (gridded
- * data only; FP64).
+ * data only; compensated FP32 sums, about FP64 accuracy).
  *
  * fpca_reconstruct: X_i(t_p) = mu(t_p) + sum_l A_il phi_l(t_p) at every node,
- * n x P row-major FP32 out (FP64 arithmetic). */
+ * n x P row-major FP32 out (compensated sum, rounded once; n < 2^20).
+ *
+ * Each of the three splits mu and the first L eigenfunctions into float-float
+ * in the context's workspace first (which may synchronise the stream the first
+ * time it grows). */
 fpca_status fpca_scores_pace(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
                              const double* mu, const double* evals, const double* evecs, int L,
                              const double* sigma2, double* scores);
@@ -346,6 +352,15 @@ fpca_status fpca_scores_integral(fpca_ctx* ctx, const fpca_data* data, const fpc
 fpca_status fpca_reconstruct(fpca_ctx* ctx, const fpca_grid* grid, const double* mu,
                              const double* evecs, int L, const double* scores, int n,
                              float* xhat);
+
+/* MISE of a reconstruction (Section 4, Simulation I): (1/n) sum_i of the
+ * integral over Omega of (xhat_i - x_i)^2, as the Riemann sum over all P grid
+ * nodes with dV = 1/P.  xhat: n x P FP32 (fpca_reconstruct); x: n x P, FP64
+ * (x_prec FPCA_F64) or FP32 (FPCA_F32), e.g. the noise-free curves of a
+ * simulation; mise: one device double out.  Compensated FP32 sums per thread,
+ * FP64 trees across threads and blocks (deterministic). */
+fpca_status fpca_mise(fpca_ctx* ctx, const fpca_grid* grid, const float* xhat, const void* x,
+                      int x_prec, int n, double* mise);
 
 /* ---- d = 3: covariance smoothing fused into its projection ----------------
  *

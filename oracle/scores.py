@@ -12,6 +12,9 @@ Definitions followed
   (Y_i(t) - mu(t)) phi_l(t) dt, as the Riemann sum over the observed nodes with
   the cell volume dV = prod_k 1/M_k.
 * Reconstruction (Section 2.1): X_i(t) = mu(t) + sum_l A_il phi_l(t).
+* MISE of a reconstruction (Section 4, Simulation I): (1/n) sum_i of the integral
+  over Omega of (Xhat_i(t) - X_i(t))^2, the integral as the Riemann sum over all
+  grid nodes with dV = prod_k 1/M_k.
 
 Readings
 --------
@@ -72,3 +75,10 @@ def integral_scores(y, mask, mu, phi, m):
 def reconstruct(mu, phi, scores):
     """X_i = mu + sum_l A_il phi_l at the grid nodes (n x P)."""
     return mu[None, :] + np.asarray(scores) @ np.asarray(phi).T
+
+
+def mise(xhat, x, m):
+    """Mean over subjects of the Riemann sum of (xhat - x)^2 (n x P arrays)."""
+    d = np.asarray(xhat, dtype=np.float64) - np.asarray(x, dtype=np.float64)
+    dv = 1.0 / float(np.prod(m))
+    return float(np.mean(np.sum(d * d, axis=1)) * dv)

@@ -31,6 +31,7 @@ SYMBOLS = (
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
+    "fpca_mise",
 )
 
 
@@ -129,6 +130,7 @@ def load(path=LIB_PATH):
     lib.fpca_scores_integral.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp,
                                          i32, vp]
     lib.fpca_reconstruct.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i32, vp, i32, vp]
+    lib.fpca_mise.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i32, i32, vp]
     lib.fpca_sigma2.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp, i32,
                                 ctypes.c_longlong, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
@@ -247,6 +249,12 @@ class Context:
         self._check(self.lib.fpca_scores_integral(self.h, ctypes.byref(data),
                                                   ctypes.byref(Grid.of(m)), _ptr(mu), _ptr(evecs),
                                                   int(L), _ptr(scores)))
+
+    def mise(self, m, xhat, x, n, out):
+        """out: one-element float64 device tensor; x float64 or float32, n x P."""
+        xp = F64 if x.dtype.itemsize == 8 else F32
+        self._check(self.lib.fpca_mise(self.h, ctypes.byref(Grid.of(m)), _ptr(xhat), _ptr(x), xp,
+                                       int(n), _ptr(out)))
 
     def reconstruct(self, m, mu, evecs, L, scores, n, xhat):
         self._check(self.lib.fpca_reconstruct(self.h, ctypes.byref(Grid.of(m)), _ptr(mu),

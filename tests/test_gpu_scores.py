@@ -208,3 +208,38 @@ def test_scores_refusals(ctx):
         assert e.value.status == B.E_NUMERIC
         assert np.all(np.isnan(host(out4)))
     ctx.sync()   # the error word was cleared
+
+
+def test_mise_matches_oracle(ctx):
+    m, n = (16, 12), 37
+    rng = np.random.default_rng(37)
+    x = rng.standard_normal((n, 192))
+    xhat = (x + 0.1 * rng.standard_normal((n, 192))).astype(np.float32)
+    out = torch.empty(1, dtype=torch.float64, device=DEV)
+    for xd in (torch.float64, torch.float32):
+        ref = osc.mise(xhat, x.astype(np.float32).astype(np.float64) if xd == torch.float32 else x, m)
+        ctx.mise(m, dev(xhat), dev(x, xd), n, out)
+        ctx.sync()
+        assert np.isclose(float(host(out)[0]), ref, rtol=1e-12), (float(host(out)[0]), ref)
+    # constant offset: exactly c^2 on the full grid
+    ctx.mise(m, dev(np.full((n, 192), 0.25, dtype=np.float32)), dev(np.zeros((n, 192))), n, out)
+    ctx.sync()
+    assert np.isclose(float(host(out)[0]), 0.0625, rtol=1e-14)
+
+
+def test_reconstruct_then_mise_of_true_scores_is_zero(ctx):
+    """mu + sum A phi reconstructed from the true scores equals the noise-free
+    curves up to FP32 rounding of the output."""
+    m, L, n = (20, 20), 5, 25
+    phi = basis(m, L)
+    rng = np.random.default_rng(38)
+    a = rng.standard_normal((n, L))
+    mu = rng.standard_normal(400)
+    x = mu[None, :] + a @ phi.T
+    xh = torch.empty((n, 400), dtype=torch.float32, device=DEV)
+    ctx.reconstruct(m, dev(mu), dev(phi.T), L, dev(a), n, xh)
+    out = torch.empty(1, dtype=torch.float64, device=DEV)
+    ctx.mise(m, xh, dev(x), n, out)
+    ctx.sync()
+    # every entry is the FP32 rounding of x (compensated sum): error within an ulp
+    assert float(host(out)[0]) <= np.mean(np.sum((np.abs(x) * 2.0 ** -23) ** 2, axis=1)) / 400

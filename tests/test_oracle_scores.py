@@ -88,3 +88,15 @@ def test_integral_scores_and_reconstruction_are_exact_on_the_grid():
     est = osc.integral_scores(y, np.ones_like(y, dtype=bool), mu, phi, m)
     assert np.allclose(est, a, rtol=0, atol=1e-12)
     assert np.allclose(osc.reconstruct(mu, phi, est), y, rtol=0, atol=1e-12)
+
+
+def test_mise_closed_forms():
+    """A constant offset c over the full grid integrates to c^2; an error a*phi_l
+    along an orthonormal eigenfunction integrates to a^2; the mean runs over
+    subjects."""
+    m = (12, 10)
+    phi = _basis(m, 3)
+    x = np.random.default_rng(5).standard_normal((4, 120))
+    assert np.isclose(osc.mise(x + 0.3, x, m), 0.09, rtol=1e-13)
+    err = np.stack([0.5 * phi[:, 0], -2.0 * phi[:, 2], np.zeros(120), phi[:, 1]])
+    assert np.isclose(osc.mise(x + err, x, m), (0.25 + 4.0 + 0.0 + 1.0) / 4, rtol=1e-12)
