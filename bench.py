@@ -581,9 +581,20 @@ def main():
         ms_cv = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
         scores = sb.scores.cpu().numpy()
         fits = len(hs) * Ds.nfold
+        # Section 3.3's trust-region search over the (anisotropic) bandwidth vector on
+        # the same bins, started at the grid's middle bandwidth, beside the grid
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h_tr, cv_tr, tr = ctx.bw_trust_region(Ds.m, sb.ccnt, sb.cw, sb.cv_, sb.cq, Ds.nfold, B.F32C,
+                                              (hs[len(hs) // 2],) * 2)
+        t_tr = time.perf_counter() - t0
         cvx = {"workload": f"sparse_2d_64x64_n{Ds.n}_5fold_16h", "ms_per_grid": ms_cv,
                "fits": fits, "value": fits * float(Ps) * Ps / (ms_cv * 1e-3), "unit": UNIT,
-               "best_h": hs[int(np.argmin(scores))],
+               "best_h": hs[int(np.argmin(scores))], "best_cv": float(np.min(scores)),
+               "trust_region": {"h": list(h_tr), "cv": cv_tr, "evaluations": len(tr),
+                                "wall_ms": t_tr * 1e3,
+                                "start_h": hs[len(hs) // 2],
+                                "grid_2d_16x16_ms_estimate": ms_cv * len(hs)},
                "kernels": {k: {"ms_total": v[0] / 3, "launches": v[1] // 3}
                            for k, v in sorted(prof_cv.items(), key=lambda kv: -kv[1][0])[:6]}}
 

@@ -288,6 +288,34 @@ fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, const void* y,
                                  const uint8_t* mask, int32_t* cnt, double* w, double* v,
                                  double* v2);
 
+/* ---- trust-region bandwidth search (Section 3.3) ----------------------------
+ *
+ * Section 3.3 replaces the grid search by a derivative-free trust-region
+ * method (Marazzi and Nocedal) whose local quadratic model is fitted by
+ * least-squares regression, since the CV score is noisy.  Built for d <= 2 on
+ * the CV of fpca_smooth_cov_project (bins with nfold >= 2 and q; prec as
+ * there).  The reading of each step (variables log h, box trust region, 3^d
+ * sample stencil, exact box-constrained model minimiser, ratio test, best point
+ * evaluated) is documented with the implementation and mirrored by the FP64
+ * oracle.  Host-driven: each iteration launches the CV of its new sample
+ * bandwidths and reads the scores back (synchronising the stream).
+ *  h0        host, d doubles: the starting bandwidths (e.g. the learned proposal);
+ *            their CV score must be finite.
+ *  opt       NULL for the defaults {0.4, 0.01, 1.0, 0.02, 0.6, 20}.
+ *  h_best    host, d doubles out; cv_best, n_evals host out (may be NULL).
+ *  trace     host, trace_cap x (d + 1) doubles out (may be NULL): every
+ *            evaluated bandwidth vector and its CV score in evaluation order. */
+typedef struct {
+  double delta0, delta_min, delta_max;  /* trust-region half-width in log h */
+  double h_lo, h_hi;                    /* bounds of every bandwidth */
+  int max_iter;
+} fpca_tr_options;
+
+fpca_status fpca_bw_trust_region(fpca_ctx* ctx, const fpca_grid* grid, const fpca_covbins* bins,
+                                 int prec, const double* h0, const fpca_tr_options* opt,
+                                 double* h_best, double* cv_best, int* n_evals, double* trace,
+                                 int trace_cap);
+
 /* ---- noise variance (Eq. 2.5-2.6) ------------------------------------------
  *
  * sigma2_hat(t) = b0(t) - Gamma_hat(t, t) - mu_hat(t)^2 at every grid node, where

@@ -31,7 +31,7 @@ SYMBOLS = (
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
-    "fpca_mise",
+    "fpca_mise", "fpca_bw_trust_region",
 )
 
 
@@ -62,6 +62,17 @@ class Data(ctypes.Structure):
         ("mask", ctypes.c_void_p),
         ("offs", ctypes.c_void_p),
         ("t", ctypes.c_void_p),
+    ]
+
+
+class TrOptions(ctypes.Structure):
+    _fields_ = [
+        ("delta0", ctypes.c_double),
+        ("delta_min", ctypes.c_double),
+        ("delta_max", ctypes.c_double),
+        ("h_lo", ctypes.c_double),
+        ("h_hi", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
     ]
 
 
@@ -131,6 +142,9 @@ def load(path=LIB_PATH):
                                          i32, vp]
     lib.fpca_reconstruct.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i32, vp, i32, vp]
     lib.fpca_mise.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i32, i32, vp]
+    lib.fpca_bw_trust_region.argtypes = [vp, ctypes.POINTER(Grid), ctypes.POINTER(CovBins), i32,
+                                         dbl_p, ctypes.POINTER(TrOptions), dbl_p, dbl_p,
+                                         ctypes.POINTER(ctypes.c_int), dbl_p, i32]
     lib.fpca_sigma2.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp, i32,
                                 ctypes.c_longlong, vp, vp, vp, vp]
     lib.fpca_profile_enable.argtypes = [vp, i32]
@@ -359,6 +373,33 @@ class Context:
         self._check(self.lib.fpca_smooth_cov_project(
             self.h, ctypes.byref(Grid.of(m)), ctypes.byref(bins), _doubles(hs), nh, int(prec),
             _ptr(mu_raw), _ptr(omega), l, _ptr(gamma), _ptr(status), _ptr(y), _ptr(cv)))
+
+    def bw_trust_region(self, m, cnt, w, v, q, nfold, prec, h0, options=None, trace_cap=256):
+        """Section 3.3 trust-region search on the CV of the given fold bins.
+        Returns (h_best, cv_best, trace) with trace a list of (h tuple, cv)."""
+        bins = CovBins()
+        bins.nfold = int(nfold)
+        bins.prec = F64 if w.dtype.itemsize == 8 else F32
+        bins.cnt, bins.w, bins.v, bins.q = cnt.data_ptr(), w.data_ptr(), v.data_ptr(), q.data_ptr()
+        d = len(m)
+        opt = None
+        if options is not None:
+            opt = TrOptions()
+            base = dict(delta0=0.4, delta_min=0.01, delta_max=1.0, h_lo=0.02, h_hi=0.6, max_iter=20)
+            base.update(options)
+            for k, val in base.items():
+                setattr(opt, k, val)
+        hb = (ctypes.c_double * d)()
+        cvb = ctypes.c_double()
+        ne = ctypes.c_int()
+        tr = (ctypes.c_double * (trace_cap * (d + 1)))()
+        self._check(self.lib.fpca_bw_trust_region(
+            self.h, ctypes.byref(Grid.of(m)), ctypes.byref(bins), int(prec), _doubles(h0),
+            None if opt is None else ctypes.byref(opt), hb, ctypes.byref(cvb), ctypes.byref(ne),
+            tr, int(trace_cap)))
+        trace = [(tuple(tr[i * (d + 1):i * (d + 1) + d]), tr[i * (d + 1) + d])
+                 for i in range(min(ne.value, trace_cap))]
+        return tuple(hb), cvb.value, trace
 
     def rproj_eig(self, m, gamma, k, evals, evecs, fve=None, domain=None, omega=None,
                   power_iters=0, full=False):
