@@ -26,26 +26,30 @@ __device__ __forceinline__ int bin_index(const double* t, int d, const int* m) {
   return flat;
 }
 
-// N_i: observed nodes of subject i (mask row sum), one block per subject.
+// N_i: observed nodes of subject i (mask row sum), one warp per subject; rows
+// are read 16 bytes at a time when they are 16-byte aligned.
 __global__ void k_subject_counts(int n, int P, const uint8_t* __restrict__ mask,
                                  int32_t* __restrict__ Ni) {
-  const int i = blockIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
   int c = 0;
-  if (mask) {
-    const uint8_t* row = mask + (size_t)i * P;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) c += row[p] != 0;
+  if (!mask) {
+    c = lane == 0 ? P : 0;
+  } else if (P % 16 == 0 && (reinterpret_cast<uintptr_t>(mask) & 15) == 0) {
+    const uint4* row = reinterpret_cast<const uint4*>(mask + (size_t)i * P);
+    for (int q = lane; q < P / 16; q += 32) {
+      const uint4 v = row[q];
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)  // count the nonzero bytes of w[k]
+        c += __popc(__vcmpne4(w[k], 0u)) >> 3;
+    }
   } else {
-    for (int p = threadIdx.x; p < P; p += blockDim.x) c += 1;
+    const uint8_t* row = mask + (size_t)i * P;
+    for (int p = lane; p < P; p += 32) c += row[p] != 0;
   }
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  __shared__ int part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) Ni[i] = s;
-  }
+  if (lane == 0) Ni[i] = c;
 }
 
 // Dense mean bins: a block covers 32 nodes; its MB_SLICES thread rows take
@@ -162,15 +166,20 @@ __global__ void k_cov_operands_bf16(int n, int P, int Kpad, const void* __restri
                                     const int32_t* __restrict__ Ni, const double* __restrict__ mu,
                                     int mode, __nv_bfloat16* __restrict__ ops) {
   __shared__ float tm[32][33], tw[32][33], tr[32][33];
-  __shared__ float wsub[32], swsub[32];
+  __shared__ float wsub[32], swsub[32], muf[32];
   const int i0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-  // per-subject weights w_i = 1/(N_i (N_i - 1)) and sqrt(w_i), once per subject
+  // per-subject weights w_i = 1/(N_i (N_i - 1)) and sqrt(w_i), and the mean at the
+  // block's 32 nodes, once per block and in FP32: the operands are rounded to
+  // BF16, so FP32 is ample (and FP64 operations are slow on this GPU)
   if (threadIdx.y == 0) {
     const int i = i0 + threadIdx.x;
     const int N = i < n ? Ni[i] : 0;
-    const double wi = N >= 2 ? 1.0 / ((double)N * (double)(N - 1)) : 0.0;
-    wsub[threadIdx.x] = (float)wi;
-    swsub[threadIdx.x] = (float)sqrt(wi);
+    const float wi = N >= 2 ? 1.f / ((float)N * (float)(N - 1)) : 0.f;
+    wsub[threadIdx.x] = wi;
+    swsub[threadIdx.x] = sqrtf(wi);
+  } else if (threadIdx.y == 1) {
+    const int p = p0 + threadIdx.x;
+    muf[threadIdx.x] = (p < P && mode == FPCA_COV_RESIDUAL) ? (float)mu[p] : 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -180,14 +189,9 @@ __global__ void k_cov_operands_bf16(int n, int P, int Kpad, const void* __restri
       const size_t idx = (size_t)i * P + p;
       const bool obs = mask ? mask[idx] != 0 : true;
       if (obs) {
-        float rr;
-        if (y_prec == FPCA_F64) {
-          const double yy = static_cast<const double*>(y)[idx];
-          rr = (float)(mode == FPCA_COV_RESIDUAL ? yy - mu[p] : yy);
-        } else {
-          const float yy = static_cast<const float*>(y)[idx];
-          rr = mode == FPCA_COV_RESIDUAL ? (float)((double)yy - mu[p]) : yy;
-        }
+        const float yy = y_prec == FPCA_F64 ? (float)static_cast<const double*>(y)[idx]
+                                            : static_cast<const float*>(y)[idx];
+        const float rr = yy - muf[threadIdx.x];
         fm = 1.f;
         fw = wsub[r];
         fr = swsub[r] * rr;
@@ -338,7 +342,7 @@ __global__ void k_cov_sparse(long long N, int P, const int64_t* __restrict__ off
 
 fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8_t* mask,
                                         int32_t* Ni) {
-  k_subject_counts<<<n, 256, 0, ctx->stream>>>(n, P, mask, Ni);
+  k_subject_counts<<<(n + 7) / 8, 256, 0, ctx->stream>>>(n, P, mask, Ni);
   FPCA_LAUNCHED(ctx, "subject_counts");
   return FPCA_OK;
 }
