@@ -18,7 +18,7 @@
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;  // BK bf16 = 128 bytes = one swizzle row
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;  // three stages: two CTAs per SM, one's epilogue overlapping the other's MMAs
 constexpr int TILE_BYTES = BM * BK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr uint32_t TMEM_COLS = 128;
@@ -34,7 +34,7 @@ struct GramJobs {
   GramJob j[3];
 };
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     k_gram_tc(const __grid_constant__ CUtensorMap tmap, int P, int Kpad, GramJobs jobs, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
