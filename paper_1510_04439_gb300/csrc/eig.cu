@@ -597,7 +597,8 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
 //     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs and
 //     r_ij / 2 inside clusters (gap <= delta = 2(|S - diag S| + |A| |R|), Frobenius
 //     norms), X <- X + X E.  Each step squares the error, so two steps reach FP64.
-//     Both steps run in one block (k_rr_refine).
+//     Both steps run in one block (k_rr_refine) for n <= 32, as separate launches
+//     spread over n blocks beyond.
 // Outputs: A <- diag(lambda), V <- eigenvectors (columns, FP64).
 __global__ void __launch_bounds__(1024)
     k_rr_jacobi32(int n, double* __restrict__ Ag, double* __restrict__ Asym,
@@ -618,6 +619,84 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
   jacobi_sweeps<float>(n, n + 1, A32, V32, 10, 1e-9, cs32, pr, red, &done);
   for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * (n + 1) + e % n];
+}
+
+// The refinement for l > 32 (one SM's FP64 throughput is too low for the fused
+// k_rr_refine at that size): the n x n x n products spread over n blocks.
+// Row i (block) of C = op(L) M (+ D): op(L) = L' when tl, else L; one thread per column.
+__global__ void k_rr_rowmm(int n, const double* __restrict__ L, int tl, const double* __restrict__ M,
+                           double* __restrict__ C, double diag, double sign) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += (tl ? L[k * n + i] : L[i * n + k]) * M[k * n + j];
+  C[i * n + j] = ((i == j) ? diag : 0.0) + sign * s;
+}
+
+// lambda, the cluster threshold and E (one block).
+__global__ void __launch_bounds__(1024)
+    k_rr_correction(int n, const double* __restrict__ A, const double* __restrict__ R,
+                    const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam) {
+  __shared__ double red[32][3];
+  __shared__ double lm[64];
+  __shared__ double delta;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lm[i] = S[i * n + i] / (1.0 - R[i * n + i]);
+  double so = 0.0, an = 0.0, rn = 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (i != j) so += S[e] * S[e];
+    an += A[e] * A[e];
+    rn += R[e] * R[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    an += __shfl_xor_sync(0xffffffffu, an, o);
+    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+  }
+  if ((tid & 31) == 0) {
+    red[tid >> 5][0] = so;
+    red[tid >> 5][1] = an;
+    red[tid >> 5][2] = rn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < nt / 32; ++w) {
+      a += red[w][0];
+      b += red[w][1];
+      c += red[w][2];
+    }
+    delta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    const double gap = lm[j] - lm[i];
+    E[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lm[j] * R[e]) / gap;
+  }
+  for (int i = tid; i < n; i += nt) lam[i] = lm[i];
+}
+
+// X <- X + X E (row i per block; the row is read before it is written).
+__global__ void k_rr_update(int n, double* __restrict__ X, const double* __restrict__ E) {
+  __shared__ double row[64];
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j < n) row[j] = X[i * n + j];
+  __syncthreads();
+  if (j >= n) return;
+  double s = row[j];
+  for (int k = 0; k < n; ++k) s += row[k] * E[k * n + j];
+  X[i * n + j] = s;
+}
+
+__global__ void k_rr_out(int n, const double* __restrict__ lam, const double* __restrict__ X,
+                         double* __restrict__ Ag, double* __restrict__ Vg) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    Ag[e] = (i == j) ? lam[i] : 0.0;
+    Vg[e] = X[e];
+  }
 }
 
 // Rank of each eigenvalue (descending; ties by index) -> order[rank] = index.
@@ -706,7 +785,7 @@ __global__ void k_finish(int P, int n, int k, double dv, const double* __restric
 }
 
 // Both Ogita-Aishima refinement steps of k_rr_jacobi32's eigenvectors in one block
-// (l <= 64), with the l x l matrices in shared memory: per step
+// (l <= 32), with the l x l matrices in shared memory: per step
 // R = I - X'X, U = A X, S = X'U, lambda_i = s_ii / (1 - r_ii),
 // delta = 2 (|S - diag S| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
 // or r_ij / 2 inside clusters, X <- X + X E; then A <- diag(lambda), V <- X.
@@ -811,15 +890,35 @@ __global__ void __launch_bounds__(RF_THREADS)
 fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double* scratch) {
   const size_t nn = (size_t)l * l;
   double* As = scratch;   // symmetrised input
-  double* X = As + nn;    // FP32 Jacobi eigenvectors, refined in place by k_rr_refine
+  double* X = As + nn;    // FP32 Jacobi eigenvectors, refined in place
+  double* R = X + nn;
+  double* U = R + nn;
+  double* S = U + nn;
+  double* lam = S + nn;
+  double* E = U;  // U is dead once S is formed
   // one thread per element of a step's rotations (np pairs x l): wider blocks only
   // make the three barriers of every step dearer
   const int jt = min(1024, max(64, ((((l + 1) & ~1) / 2 * l + 31) / 32) * 32));
   k_rr_jacobi32<<<1, jt, 0, ctx->stream>>>(l, A, As, X);
   FPCA_LAUNCHED(ctx, "jacobi");
-  cudaFuncSetAttribute(k_rr_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)rr_refine_smem(l));
-  k_rr_refine<<<1, RF_THREADS, rr_refine_smem(l), ctx->stream>>>(l, As, X, A, V);
+  if (l <= 32) {
+    k_rr_refine<<<1, RF_THREADS, rr_refine_smem(l), ctx->stream>>>(l, As, X, A, V);
+    FPCA_LAUNCHED(ctx, "jacobi");
+    return FPCA_OK;
+  }
+  for (int step = 0; step < 2; ++step) {
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, As, 0, X, U, 0.0, 1.0);   // U = A X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_rowmm<<<l, 64, 0, ctx->stream>>>(l, X, 1, U, S, 0.0, 1.0);    // S = X' A X
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_correction<<<1, 1024, 0, ctx->stream>>>(l, As, R, S, E, lam);
+    FPCA_LAUNCHED(ctx, "jacobi");
+    k_rr_update<<<l, 64, 0, ctx->stream>>>(l, X, E);
+    FPCA_LAUNCHED(ctx, "jacobi");
+  }
+  k_rr_out<<<(int)((nn + 255) / 256), 256, 0, ctx->stream>>>(l, lam, X, A, V);
   FPCA_LAUNCHED(ctx, "jacobi");
   return FPCA_OK;
 }

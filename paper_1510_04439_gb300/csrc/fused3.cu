@@ -543,6 +543,51 @@ __device__ void f3_tdiag_direct(const Geo3& g, const Tab3* __restrict__ tab,
   }
 }
 
+// f3_tdiag_direct with the (p0, p1) rows of the window dealt over the 32 lanes of
+// a warp and the four sums joined by shuffles (every lane returns them).
+__device__ void f3_tdiag_warp(const Geo3& g, const Tab3* __restrict__ tab,
+                              const float* __restrict__ Dp, const int sc[3], const int tc[3],
+                              int lane, float& Q0, float Qs[3]) {
+  int lo[3], hi[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lo[j] = max(max(sc[j], tc[j]) - g.T[j], 0);
+    hi[j] = min(min(sc[j], tc[j]) + g.T[j], g.m[j] - 1);
+  }
+  const int n1 = hi[1] - lo[1] + 1;
+  const int nrow = (hi[0] - lo[0] + 1) * n1;
+  float q0 = 0.f, qs0 = 0.f, qs1 = 0.f, qs2 = 0.f;
+  for (int r = lane; r < nrow; r += 32) {
+    const int p0 = lo[0] + r / n1, p1 = lo[1] + r % n1;
+    const float a = tab->tapK[0][p0 - sc[0] + F3_TMAX] * tab->tapK[0][p0 - tc[0] + F3_TMAX] *
+                    tab->tapK[1][p1 - sc[1] + F3_TMAX] * tab->tapK[1][p1 - tc[1] + F3_TMAX];
+    const float u0 = (p0 - sc[0]) * tab->inv_hM[0];
+    const float u1 = (p1 - sc[1]) * tab->inv_hM[1];
+    const float* drow = Dp + ((long long)p0 * g.m[1] + p1) * g.m[2];
+    float e0 = 0.f, e2 = 0.f;
+    for (int p2 = lo[2]; p2 <= hi[2]; ++p2) {
+      const float w2 = tab->tapK[2][p2 - sc[2] + F3_TMAX] * tab->tapK[2][p2 - tc[2] + F3_TMAX];
+      const float dv = w2 * __ldg(drow + p2);
+      e0 += dv;
+      e2 = fmaf((p2 - sc[2]) * tab->inv_hM[2], dv, e2);
+    }
+    q0 = fmaf(a, e0, q0);
+    qs0 = fmaf(a * u0, e0, qs0);
+    qs1 = fmaf(a * u1, e0, qs1);
+    qs2 = fmaf(a, e2, qs2);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+    qs0 += __shfl_xor_sync(0xffffffffu, qs0, o);
+    qs1 += __shfl_xor_sync(0xffffffffu, qs1, o);
+    qs2 += __shfl_xor_sync(0xffffffffu, qs2, o);
+  }
+  Q0 = q0;
+  Qs[0] = qs0;
+  Qs[1] = qs1;
+  Qs[2] = qs2;
+}
+
 __device__ __forceinline__ void f3_tile_origin_S(const Geo3& g, int S, int o[3]) {
   const int b2 = S % g.nb[2], b1 = (S / g.nb[2]) % g.nb[1], b0 = S / (g.nb[2] * g.nb[1]);
   o[0] = 4 * b0;
@@ -1172,8 +1217,10 @@ __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __
     }
     for (int p = 0; p < 7; ++p)
       for (int o = 16; o > 0; o >>= 1) Pv[p] += __shfl_xor_sync(0xffffffffu, Pv[p], o);
+    const int sc[3] = {c0, c1, c2};
+    float Q0, Qs[3];
+    f3_tdiag_warp(g, tab, Dp, sc, sc, lane, Q0, Qs);
     if (lane == 0) {
-      const int sc[3] = {c0, c1, c2};
       const PtGeo sg = f3_geo(tab, c0, c1, c2);
       float beta[7];
       const float inv = f3_beta(sg, sg, Pv, beta);
@@ -1183,8 +1230,6 @@ __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __
         r10[j] = tab->rho[j][sc[j]][2 * F3_TMAX][1];
         r20[j] = tab->rho[j][sc[j]][2 * F3_TMAX][3];
       }
-      float Q0, Qs[3];
-      f3_tdiag_direct(g, tab, Dp, sc, sc, Q0, Qs);
       const int dx[3] = {0, 0, 0};
       int bad = 0;
       const float corr = f3_corr(sg, sg, r00, r10, r20, Q0, Qs, dx, tab->inv_hM, beta, inv, bad);
@@ -1193,7 +1238,15 @@ __global__ void k_f3_trace(Geo3 g, const Tab3* __restrict__ tab, const float* __
       if (diag) diag[x] = contrib;
     }
   }
-  if (trace && lane == 0 && x < g.P) atomicAdd(trace, contrib);
+  // the block's warps summed in shared memory, one atomic per block
+  __shared__ double wsum[32];
+  if (lane == 0) wsum[threadIdx.x >> 5] = contrib;
+  __syncthreads();
+  if (trace && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    atomicAdd(trace, t);
+  }
 }
 
 // ---------------------------------------------------------------------------

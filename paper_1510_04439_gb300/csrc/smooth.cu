@@ -259,20 +259,26 @@ __global__ void k_mean_prep(int P, const int32_t* __restrict__ cnt, const double
   out[2 * P + p] = cnt[p] > 0 ? 1.0 : 0.0;
 }
 
+// One thread per (node, job): the jobs of a pass run side by side and each tap
+// sum is split into two interleaved FP64 chains (even and odd offsets), since
+// dependent FP64 operations have a long latency on this GPU.
 __global__ void k_mean_pass(int P, int M, MeanPass mp, const double* __restrict__ tab,
                             const double* __restrict__ in, double* __restrict__ out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)P * mp.njobs) return;
+  const int j = (int)(e / P), p = (int)(e - (long long)j * P);
   const int c = (p / mp.stride) % M;
   const int lo = max(-mp.T, -c), hi = min(mp.T, M - 1 - c);
-  const double* wt = tab + (size_t)mp.axis * TROWS * TW + TMAX;
-  for (int j = 0; j < mp.njobs; ++j) {
-    const double* src = in + (size_t)mp.src[j] * P;
-    const double* w = wt + mp.row[j] * TW;
-    double s = 0.0;
-    for (int r = lo; r <= hi; ++r) s = fma(w[r], src[p + r * mp.stride], s);
-    out[(size_t)j * P + p] = s;
+  const double* w = tab + (size_t)mp.axis * TROWS * TW + TMAX + mp.row[j] * TW;
+  const double* src = in + (size_t)mp.src[j] * P;
+  double s0 = 0.0, s1 = 0.0;
+  int r = lo;
+  for (; r + 1 <= hi; r += 2) {
+    s0 = fma(w[r], src[p + r * mp.stride], s0);
+    s1 = fma(w[r + 1], src[p + (r + 1) * mp.stride], s1);
   }
+  if (r <= hi) s0 = fma(w[r], src[p + r * mp.stride], s0);
+  out[(size_t)j * P + p] = s0 + s1;
 }
 
 struct MeanIdx {
@@ -1909,7 +1915,8 @@ fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t*
   double* in = bufA;
   double* out = bufB;
   for (const MeanPass& mp : passes) {
-    k_mean_pass<<<nb, 256, 0, ctx->stream>>>(P, g->m[mp.axis], mp, tabw, in, out);
+    k_mean_pass<<<(int)(((long long)P * mp.njobs + 255) / 256), 256, 0, ctx->stream>>>(
+        P, g->m[mp.axis], mp, tabw, in, out);
     FPCA_LAUNCHED(ctx, "mean_pass");
     std::swap(in, out);
   }
