@@ -131,23 +131,37 @@ __global__ void k_f3_residuals(Geo3 g, const TY* __restrict__ y, const double* _
                                float scale, float* __restrict__ Rt32, __nv_bfloat16* __restrict__ Rbt,
                                __nv_bfloat16* __restrict__ Rb) {
   __shared__ float tile[32][33];
+  __shared__ float muf[32];
+  __shared__ int qs[32];
   const int p0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  // the mean and the tile-order index of the block's 32 nodes, once per block
+  if (threadIdx.y == 0) {
+    const int p = p0 + threadIdx.x;
+    muf[threadIdx.x] = p < g.P ? (float)mu[p] : 0.f;
+    int q = -1;
+    if (p < g.P) {
+      const int a2 = p % g.m[2], a1 = (p / g.m[2]) % g.m[1], a0 = p / (g.m[2] * g.m[1]);
+      q = (int)f3_perm(g, a0, a1, a2);
+    }
+    qs[threadIdx.x] = q;
+  }
+  __syncthreads();
+  // residuals in FP32 (the factor is FP32 and BF16; FP64 is slow on this GPU)
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int i = i0 + r, p = p0 + threadIdx.x;
     float v = 0.f;
-    if (i < g.n && p < g.P) v = (float)(((double)y[(size_t)i * g.P + p] - mu[p]) * (double)scale);
+    if (i < g.n && p < g.P) v = ((float)y[(size_t)i * g.P + p] - muf[threadIdx.x]) * scale;
     tile[r][threadIdx.x] = v;
+    // R~ (n_pad x p_pad, tile order): consecutive nodes are runs of consecutive q
+    if (i < g.n_pad && p < g.P) Rb[(size_t)i * g.p_pad + qs[threadIdx.x]] = __float2bfloat16_rn(v);
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int p = p0 + r, i = i0 + threadIdx.x;
     if (p >= g.P || i >= g.n_pad) continue;
     const float v = tile[threadIdx.x][r];
-    const int a2 = p % g.m[2], a1 = (p / g.m[2]) % g.m[1], a0 = p / (g.m[2] * g.m[1]);
-    const int q = f3_perm(g, a0, a1, a2);
     Rt32[(size_t)p * g.n_pad + i] = v;
-    Rbt[(size_t)q * g.n_pad + i] = __float2bfloat16_rn(v);
-    Rb[(size_t)i * g.p_pad + q] = __float2bfloat16_rn(v);
+    Rbt[(size_t)qs[r] * g.n_pad + i] = __float2bfloat16_rn(v);
   }
 }
 
