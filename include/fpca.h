@@ -209,7 +209,10 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
  *  full = 0: random projection (Section 3.4) with the caller's Gaussian
  *   test matrix omega (P x l float, k < l <= 64): Y = Sigma Omega, power_iters
  *   rounds of Q = orth(Y), Y = Sigma Q, then Q = orth(Y), B = Q' Sigma Q and
- *   the FP64 Jacobi eigenpairs of B (Rayleigh-Ritz).
+ *   the eigenpairs of B (Rayleigh-Ritz): FP32 Jacobi refined by two FP64
+ *   Ogita-Aishima steps.  orth is Cholesky QR (one pass between power
+ *   iterations, two at the end) on a compensated FP32 Gram matrix with the
+ *   Cholesky factor and its inverse in float-float (about 48 bits).
  * Outputs (device, FP64): evals k, evecs P x k (column-major: vector j at
  * evecs + j*P), fve k (may be NULL). */
 fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gamma,

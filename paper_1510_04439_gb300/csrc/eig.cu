@@ -3,7 +3,7 @@
 //
 //  Sigma    = (G + G')/2, NaN -> 0, rows/columns outside the domain -> 0
 //  Y        = Sigma Omega;  repeat q times { Q = orth(Y); Y = Sigma Q }
-//  Q        = orth(Y) by CholeskyQR2 (FP64 Gram and Cholesky)
+//  Q        = orth(Y) by CholeskyQR2 (compensated FP32 Gram, float-float Cholesky)
 //  B        = Q' Sigma Q (FP64), eigenpairs of B by cyclic Jacobi (FP64)
 //  Psi      = Q U;  lambda = theta dV;  phi = psi / sqrt(dV);  dV = 1/P
 // The dense path (full = 1) runs the same Jacobi solver on Sigma itself.
