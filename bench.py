@@ -220,6 +220,24 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x, device=None):
+    """The largest x over the ranks of the initialised process group (x itself
+    without one): the replicas' step times are combined by their maximum."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest rank (ms per step)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------
 # oracle timing (CPU): Gamma_hat at sampled output pairs by window sums
 # ----------------------------------------------------------------------------
@@ -434,12 +452,7 @@ def main():
             dist.barrier()
 
     def maxreduce(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dev)
 
     for _ in range(max(args.warmup, 3)):
         step(y, mask)
@@ -472,7 +485,7 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     ms = maxreduce(ms)
     units = float(P) * P
-    value = world * units / (ms * 1e-3)
+    value = job_value(units, world, ms)
 
     # ---- end to end: pinned host inputs in, eigenpairs out, every step ----
     ev_h = torch.empty(K_EIG, dtype=torch.float64).pin_memory()
@@ -550,7 +563,7 @@ def main():
         if hu:
             ach_u = flops_pt * evaluated / (hu[0] / hu[1] * 1e-3) / 1e12
             variant = {"precision": "FP32 moments without compensation",
-                       "ms_per_step": ms_u, "value": world * units / (ms_u * 1e-3),
+                       "ms_per_step": ms_u, "value": job_value(units, world, ms_u),
                        "roofline": {"kernel": "cov_hpass_solve", "bound": "alu",
                                     "achieved": ach_u, "peak": peak, "unit": "TFLOP/s",
                                     "frac": ach_u / peak, "ms_per_launch": hu[0] / hu[1]}}
@@ -646,7 +659,7 @@ def main():
                                    "symmetry of the estimator)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": world * units / (ms_e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_value(units, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": ms_e2e},
             "gpu_launches": launches,
