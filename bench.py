@@ -488,30 +488,50 @@ def main():
     value = job_value(units, world, ms)
 
     # ---- end to end: pinned host inputs in, eigenpairs out, every step ----
+    # One timed interval over all steps.  Each step's inputs are copied from pinned
+    # host memory on a second stream into one of two device buffers while the
+    # previous step computes; each step waits for its copy, and its eigenpairs are
+    # read back at its end.  The L2 flush before each step stays inside the interval.
     ev_h = torch.empty(K_EIG, dtype=torch.float64).pin_memory()
     vec_h = torch.empty(K_EIG, P, dtype=torch.float64).pin_memory()
     fve_h = torch.empty(K_EIG, dtype=torch.float64).pin_memory()
-    y_in = torch.empty_like(y)
-    m_in = torch.empty_like(mask)
+    y_in = [torch.empty_like(y) for _ in range(2)]
+    m_in = [torch.empty_like(mask) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
     barrier()
     torch.cuda.synchronize()
-    evs = []
-    for _ in range(args.steps):
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    copy_stream.wait_event(t_start)
+
+    def issue_copy(i):
+        b = i % 2
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(free[b])
+            y_in[b].copy_(y_host, non_blocking=True)
+            m_in[b].copy_(m_host, non_blocking=True)
+            ready[b].record(copy_stream)
+
+    issue_copy(0)
+    for i in range(args.steps):
+        if i + 1 < args.steps:
+            issue_copy(i + 1)
+        b = i % 2
         flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        y_in.copy_(y_host, non_blocking=True)
-        m_in.copy_(m_host, non_blocking=True)
-        step(y_in, m_in)
+        stream.wait_event(ready[b])
+        step(y_in[b], m_in[b])
+        free[b].record(stream)
         ev_h.copy_(bufs.evals, non_blocking=True)
         vec_h.copy_(bufs.evecs, non_blocking=True)
         fve_h.copy_(bufs.fve, non_blocking=True)
-        b.record(stream)
-        evs.append((a, b))
+    t_end.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = maxreduce(sum(a.elapsed_time(b) for a, b in evs) / args.steps)
+    ms_e2e = maxreduce(t_start.elapsed_time(t_end) / args.steps)
     h2d = y_host.numel() * y_host.element_size() + m_host.numel() * m_host.element_size()
     d2h = (ev_h.numel() + vec_h.numel() + fve_h.numel()) * 8
 
@@ -661,7 +681,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": job_value(units, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e},
+                    "ms_per_step": ms_e2e,
+                    "timing": "one interval over all steps; each step's H2D copy overlaps the "
+                              "previous step (double-buffered), L2 flush inside the interval"},
             "gpu_launches": launches,
             "roofline": roof,
             "variant_uncompensated": variant,
