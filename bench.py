@@ -674,7 +674,8 @@ def main():
                        "h": list(H), "k": K_EIG, "l": L_RP, "power_iters": Q_POWER,
                        "precision": "BF16 tcgen05 binning (FP32 accumulate, exact counts); "
                                     "FP32 compensated moments; FP32 solve, float-float "
-                                    "re-solve of ill-conditioned points; FP64 Rayleigh-Ritz",
+                                    "re-solve of ill-conditioned points; Rayleigh-Ritz by FP32 "
+                                    "Jacobi and two float-float refinement steps",
                        "symmetry": "Gamma_hat fitted at t >= s, mirrored to t < s (exact "
                                    "symmetry of the estimator)",
                        "l2": "flushed between timed steps (256 MiB write)",

@@ -56,11 +56,12 @@ __global__ void k_subject_counts(int n, int P, const uint8_t* __restrict__ mask,
 // every MB_SLICES-th subject, and the partial sums are added by a fixed
 // pairwise tree (deterministic).  Weights 1/N_i.
 constexpr int MB_SLICES = 32;  // subject slices per block: short FP64 add chains
+constexpr int MB_BATCH = 8;    // subjects whose loads are issued together (4 for FP64 y)
+template <typename TY>
 __global__ void __launch_bounds__(32 * MB_SLICES)
-    k_bin_mean_dense(int n, int P, const void* __restrict__ y, int y_prec,
-                     const uint8_t* __restrict__ mask, const int32_t* __restrict__ Ni,
-                     int32_t* __restrict__ cnt, double* __restrict__ w, double* __restrict__ v,
-                     double* __restrict__ v2) {
+    k_bin_mean_dense(int n, int P, const TY* __restrict__ y, const uint8_t* __restrict__ mask,
+                     const int32_t* __restrict__ Ni, int32_t* __restrict__ cnt,
+                     double* __restrict__ w, double* __restrict__ v, double* __restrict__ v2) {
   __shared__ double ps[3][MB_SLICES][32];
   __shared__ int pc[MB_SLICES][32];
   __shared__ float winvh[32 * MB_SLICES], winvl[32 * MB_SLICES];
@@ -84,26 +85,41 @@ __global__ void __launch_bounds__(32 * MB_SLICES)
     __syncthreads();
     if (p < P) {
       const int iend = min(n, i0 + 32 * MB_SLICES);
-      for (int i = i0 + threadIdx.y; i < iend; i += MB_SLICES) {
-        const size_t idx = (size_t)i * P + p;
-        if (mask && !mask[idx]) continue;
-        const ff::F2 wi = {winvh[i - i0], winvl[i - i0]};
-        if (wi.hi == 0.f) continue;
-        ff::F2 yy, y2;
-        if (y_prec == FPCA_F64) {
-          const double yd = static_cast<const double*>(y)[idx];
-          const float hi = (float)yd;
-          yy = {hi, (float)(yd - (double)hi)};
-          y2 = ff::mul(yy, yy);
-        } else {
-          const float yf = static_cast<const float*>(y)[idx];
-          yy = ff::make(yf);
-          y2 = ff::two_prod(yf, yf);  // exact
+      constexpr int NB = sizeof(TY) == 8 ? MB_BATCH / 2 : MB_BATCH;
+      for (int ib = i0 + threadIdx.y; ib < iend; ib += NB * MB_SLICES) {
+        // the batch's loads first (independent of the sums), then the sums in
+        // subject order
+        TY yb[NB];
+        bool ok[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int i = ib + u * MB_SLICES;
+          const size_t idx = (size_t)i * P + p;
+          ok[u] = i < iend && (!mask || mask[idx]);
+          yb[u] = i < iend ? y[idx] : TY(0);
         }
-        c += 1;
-        fw = ff::add(fw, wi);
-        fv = ff::add(fv, ff::mul(wi, yy));
-        fv2 = ff::add(fv2, ff::mul(wi, y2));
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int i = ib + u * MB_SLICES;
+          if (!ok[u]) continue;
+          const ff::F2 wi = {winvh[i - i0], winvl[i - i0]};
+          if (wi.hi == 0.f) continue;
+          ff::F2 yy, y2;
+          if constexpr (sizeof(TY) == 8) {
+            const double yd = yb[u];
+            const float hi = (float)yd;
+            yy = {hi, (float)(yd - (double)hi)};
+            y2 = ff::mul(yy, yy);
+          } else {
+            const float yf = yb[u];
+            yy = ff::make(yf);
+            y2 = ff::two_prod(yf, yf);  // exact
+          }
+          c += 1;
+          fw = ff::add(fw, wi);
+          fv = ff::add(fv, ff::mul(wi, yy));
+          fv2 = ff::add(fv2, ff::mul(wi, y2));
+        }
       }
     }
   }
@@ -350,8 +366,12 @@ fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8
 fpca_status launch_bin_mean_dense(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
                                   const uint8_t* mask, const int32_t* Ni, int32_t* cnt,
                                   double* w, double* v, double* v2) {
-  k_bin_mean_dense<<<(P + 31) / 32, dim3(32, MB_SLICES), 0, ctx->stream>>>(n, P, y, y_prec, mask,
-                                                                          Ni, cnt, w, v, v2);
+  if (y_prec == FPCA_F64)
+    k_bin_mean_dense<double><<<(P + 31) / 32, dim3(32, MB_SLICES), 0, ctx->stream>>>(
+        n, P, static_cast<const double*>(y), mask, Ni, cnt, w, v, v2);
+  else
+    k_bin_mean_dense<float><<<(P + 31) / 32, dim3(32, MB_SLICES), 0, ctx->stream>>>(
+        n, P, static_cast<const float*>(y), mask, Ni, cnt, w, v, v2);
   FPCA_LAUNCHED(ctx, "bin_mean_dense");
   return FPCA_OK;
 }

@@ -22,16 +22,22 @@ __device__ __forceinline__ double gval(const TG* G, long long idx) {
 
 // Sigma = sym(G) with NaN and out-of-domain entries zeroed; trace accumulated.
 // The arithmetic is done in the type of Sigma (FP32 for the projected path).
+// A block takes the pair of 32 x 32 tiles (I, J) and (J, I), I <= J (blocks
+// below the diagonal return at once), so G is read once and Sigma written once:
+// s = (g_pq + g_qp) / 2 is formed for (p, q) in (I, J) and written there and,
+// through the shared tile, to (q, p).  Since the sum is commutative, Sigma is
+// exactly symmetric.
 template <typename TG, typename TS>
 __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __restrict__ dom,
                             TS* __restrict__ S, double* __restrict__ trace) {
   __shared__ TS tile[32][33];
   __shared__ double dsum;  // this block's part of the trace (diagonal blocks only)
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  if (blockIdx.y > blockIdx.x) return;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   if (threadIdx.x == 0 && threadIdx.y == 0) dsum = 0.0;
-  // transposed tile: rows q in [bx, bx+32), columns p in [by, by+32)
+  // tile[r][c] = g(j0 + r, i0 + c)
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int q = bx + r, p = by + threadIdx.x;
+    const int q = j0 + r, p = i0 + threadIdx.x;
     TS v = TS(0);
     if (q < P && p < P) {
       v = (TS)G[(long long)q * P + p];
@@ -40,90 +46,163 @@ __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __re
     tile[r][threadIdx.x] = v;
   }
   __syncthreads();
+  // (p, q) = (i0 + r, j0 + c): s = (g_pq + tile[c][r]) / 2, kept in tile[c][r]
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int p = by + r, q = bx + threadIdx.x;
+    const int p = i0 + r, q = j0 + threadIdx.x;
+    TS sv = TS(0);
     if (p < P && q < P) {
       TS g = (TS)G[(long long)p * P + q];
       if (isnan(g)) g = TS(0);
-      TS sv = TS(0.5) * (g + tile[threadIdx.x][r]);
+      sv = TS(0.5) * (g + tile[threadIdx.x][r]);
       if (dom && (dom[p] <= 0 || dom[q] <= 0)) sv = TS(0);
       S[(long long)p * P + q] = sv;
       if (p == q) atomicAdd(&dsum, (double)sv);
     }
+    tile[threadIdx.x][r] = sv;
   }
-  // one global atomic per diagonal block instead of one per diagonal entry
   __syncthreads();
-  if (bx == by && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(trace, dsum);
+  if (i0 == j0) {
+    // one global atomic per diagonal block instead of one per diagonal entry
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(trace, dsum);
+    return;
+  }
+  // (q, p) = (j0 + r, i0 + c) takes s(p, q) = tile[r][c]
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int q = j0 + r, p = i0 + threadIdx.x;
+    if (q < P && p < P) S[(long long)q * P + p] = tile[r][threadIdx.x];
+  }
 }
 
-// Y (P x l) = S (P x P) X (P x l): a warp per RPW rows, lanes stride over the
-// columns of S, X staged in shared memory in chunks of QCH rows.
-// The column range is split over gridDim.y blocks (split-K); partial sums
-// are added to Y (zeroed beforehand) with atomics.
-template <typename TS, typename TX, int LM, int RPW>
-__global__ void __launch_bounds__(256)
-    k_proj(int P, int l, const TS* __restrict__ S, const TX* __restrict__ X,
-           TX* __restrict__ Y) {
-  constexpr int QCH = LM > 32 ? 128 : 256;
-  constexpr int LP = LM + 1;
-  __shared__ TX xs[QCH * LP];
+// Y (P x l) = S X for the symmetric S that k_matrixize writes (P x P, FP32).
+// Since S[k][p] == S[p][k] exactly, S is read by its rows k: the lanes of a warp
+// hold 32 consecutive output rows p (coalesced loads of S), and X[k][.] is the
+// same for the whole warp (shared-memory broadcasts).  A thread owns RPT rows
+// 32 apart, a block PJ_WARPS warps side by side (a tile of PJ_WARPS * 32 * RPT
+// rows) over one range of kb values of k, X staged in shared memory in chunks of
+// kc rows (a multiple of 2 PJ_U; the last chunk's missing rows are zero).
+// Every k range writes its partial product to part[range][c][p]; k_proj_sum adds
+// the ranges in order (no atomics: the result does not depend on scheduling).
+constexpr int PJ_WARPS = 8;
+constexpr int PJ_U = 8;    // k values per batch of loads of S
+
+template <int LM, int RPT>
+__global__ void __launch_bounds__(PJ_WARPS * 32, 2)
+    k_proj(int P, int l, int kb, int kc, const float* __restrict__ S,
+           const float* __restrict__ X, float* __restrict__ part) {
+  extern __shared__ float4 xs4[];   // [kc][LM / 4]: one chunk of X, rows past the range zero
+  constexpr int L4 = LM / 4;
+  float* xs = reinterpret_cast<float*>(xs4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = (blockIdx.x * 8 + warp) * RPW;
-  TX acc[RPW][LM];
+  const int pbase = (blockIdx.x * PJ_WARPS + warp) * 32 * RPT + lane;
+  const int kend = min(P, (blockIdx.y + 1) * kb);
+  float acc[RPT][LM];
 #pragma unroll
-  for (int r = 0; r < RPW; ++r)
+  for (int r = 0; r < RPT; ++r)
 #pragma unroll
-    for (int c = 0; c < LM; ++c) acc[r][c] = TX(0);
-  const int span = (P + gridDim.y - 1) / gridDim.y;
-  const int qbeg = blockIdx.y * span, qend = min(P, qbeg + span);
-  for (int q0 = qbeg; q0 < qend; q0 += QCH) {
+    for (int c = 0; c < LM; ++c) acc[r][c] = 0.f;
+  for (int k0 = blockIdx.y * kb; k0 < kend; k0 += kc) {
+    const int nk = min(kend - k0, kc);
     __syncthreads();
-    for (int e = threadIdx.x; e < QCH * LM; e += 256) {
-      const int qq = e / LM, c = e - qq * LM;
-      xs[qq * LP + c] = (q0 + qq < qend && c < l) ? X[(long long)(q0 + qq) * l + c] : TX(0);
+    for (int e = threadIdx.x; e < kc * LM; e += blockDim.x) {
+      const int kk = e / LM, c = e - kk * LM;
+      xs[e] = (kk < nk && c < l) ? X[(long long)(k0 + kk) * l + c] : 0.f;
     }
     __syncthreads();
-    // all of this chunk's Sigma loads are issued before the FMAs
-    constexpr int NQ = QCH / 32;
-    TX sv[NQ][RPW];
+    // two batches of S in registers: the loads of one are in flight while the
+    // other is multiplied (X holds zero rows up to a multiple of 2 PJ_U)
+    float sa[PJ_U][RPT], sb[PJ_U][RPT];
+    auto load = [&](float (&sv)[PJ_U][RPT], int k) {
 #pragma unroll
-    for (int u = 0; u < NQ; ++u) {
-      const int q = q0 + lane + 32 * u;
+      for (int u = 0; u < PJ_U; ++u)
 #pragma unroll
-      for (int r = 0; r < RPW; ++r)
-        sv[u][r] = (q < qend && row0 + r < P) ? (TX)S[(long long)(row0 + r) * P + q] : TX(0);
-    }
+        for (int r = 0; r < RPT; ++r) {
+          const int p = pbase + 32 * r;
+          sv[u][r] = (k + u < nk && p < P) ? __ldg(S + (long long)(k0 + k + u) * P + p) : 0.f;
+        }
+    };
+    auto fmas = [&](const float (&sv)[PJ_U][RPT], int k) {
 #pragma unroll
-    for (int u = 0; u < NQ; ++u) {
-      const int t = lane + 32 * u;
+      for (int u = 0; u < PJ_U; ++u)
 #pragma unroll
-      for (int c = 0; c < LM; ++c) {
-        const TX xv = xs[t * LP + c];
+        for (int c4 = 0; c4 < L4; ++c4) {
+          const float4 x = xs4[(k + u) * L4 + c4];
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) acc[r][c] = fma(sv[u][r], xv, acc[r][c]);
-      }
+          for (int r = 0; r < RPT; ++r) {
+            acc[r][4 * c4 + 0] = fmaf(sv[u][r], x.x, acc[r][4 * c4 + 0]);
+            acc[r][4 * c4 + 1] = fmaf(sv[u][r], x.y, acc[r][4 * c4 + 1]);
+            acc[r][4 * c4 + 2] = fmaf(sv[u][r], x.z, acc[r][4 * c4 + 2]);
+            acc[r][4 * c4 + 3] = fmaf(sv[u][r], x.w, acc[r][4 * c4 + 3]);
+          }
+        }
+    };
+    load(sa, 0);
+    for (int k = 0; k < nk; k += 2 * PJ_U) {
+      load(sb, k + PJ_U);
+      fmas(sa, k);
+      load(sa, k + 2 * PJ_U);
+      fmas(sb, k + PJ_U);
     }
   }
+  float* out = part + (long long)blockIdx.y * l * P;
 #pragma unroll
-  for (int r = 0; r < RPW; ++r)
+  for (int r = 0; r < RPT; ++r) {
+    const int p = pbase + 32 * r;
+    if (p < P) {
 #pragma unroll
-    for (int c = 0; c < LM; ++c) {
-      TX v = acc[r][c];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[r][c] = v;
+      for (int c = 0; c < LM; ++c)
+        if (c < l) out[(long long)c * P + p] = acc[r][c];
     }
-  if (lane == 0) {
-#pragma unroll
-    for (int r = 0; r < RPW; ++r)
-      if (row0 + r < P) {
-#pragma unroll
-        for (int c = 0; c < LM; ++c)
-          if (c < l) atomicAdd(Y + (long long)(row0 + r) * l + c, acc[r][c]);
-      }
   }
 }
 
-// Partial Gram products A'B (l x l) over blocks of GR_ROWS rows (A, B: P x l),
+// Y[p][c] = sum over the k ranges, in range order, of part[range][c][p].
+__global__ void k_proj_sum(int P, int l, int ranges, const float* __restrict__ part,
+                           float* __restrict__ Y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // c * P + p
+  const long long n = (long long)P * l;
+  if (i >= n) return;
+  // loads in groups of eight (independent of the sum), added in range order
+  float s = 0.f;
+  int j = 0;
+  for (; j + 8 <= ranges; j += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = part[(j + u) * n + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; j < ranges; ++j) s += part[j * n + i];
+  const int c = (int)(i / P), p = (int)(i - (long long)c * P);
+  Y[(long long)p * l + c] = s;
+}
+
+// Launch shape of k_proj: rows per thread and the k ranges, chosen so that the
+// grid is about two blocks per SM (the kernel's residency).
+struct ProjShape {
+  int rpt, lm, tiles, kb, kc, ranges;
+};
+
+inline ProjShape proj_shape(int P, int l, int num_sms) {
+  ProjShape s;
+  s.lm = l <= 8 ? 8 : l <= 20 ? 20 : l <= 24 ? 24 : 64;
+  s.rpt = l <= 8 ? 4 : l <= 24 ? 2 : 1;
+  const int rows = PJ_WARPS * 32 * s.rpt;
+  s.tiles = (P + rows - 1) / rows;
+  const int want = max(1, (2 * max(num_sms, 1) + s.tiles / 2) / s.tiles);
+  constexpr int q = 2 * PJ_U;
+  s.kb = ((P + want - 1) / want + q - 1) / q * q;
+  s.ranges = (P + s.kb - 1) / s.kb;
+  s.kc = min(s.kb, (32768 / (int)sizeof(float) / s.lm) / q * q);   // <= 32 KB of X
+  return s;
+}
+
+inline size_t proj_part_floats(int P, int l, int num_sms) {
+  if (l > 64) return 0;
+  const ProjShape sh = proj_shape(P, l, num_sms);
+  return (size_t)sh.ranges * l * P;
+}
+
+// Partial Gram products A'B (l x l) over blocks of gram_rows() rows (A, B: P x l),
 // written per block and summed in block order by k_gram_sum (no atomics, so the
 // result does not depend on scheduling).
 //
@@ -134,8 +213,18 @@ __global__ void __launch_bounds__(256)
 // rounding errors are summed separately (the compensated dot product of Ogita,
 // Rump and Oishi, "Accurate sum and dot product", 2005).  FP64 inputs use
 // plain FP64 sums.
-constexpr int GR_ROWS = 64;  // short per-entry chains, a wide grid
 constexpr int GR_SUB = 32;
+
+// Rows per block of the partial Gram products: about two blocks per SM (short
+// per-entry chains, a wide grid), at least 16 rows.
+inline int gram_rows(int P, int num_sms) {
+  const int want = 2 * max(num_sms, 1);
+  return max(16, ((P + want - 1) / want + 15) / 16 * 16);
+}
+inline size_t gram_part_doubles(int P, int l, int num_sms) {
+  const int rows = gram_rows(P, num_sms);
+  return (size_t)((P + rows - 1) / rows) * l * l;
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -145,10 +234,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 template <typename TX>
 __global__ void __launch_bounds__(256)
-    k_cross_gram(int P, int l, const TX* __restrict__ A, const TX* __restrict__ B,
+    k_cross_gram(int P, int l, int rows, const TX* __restrict__ A, const TX* __restrict__ B,
                  double* __restrict__ part) {
   __shared__ TX As[GR_SUB * 64], Bs[GR_SUB * 64];
-  const int r0 = blockIdx.x * GR_ROWS, r1 = min(P, r0 + GR_ROWS);
+  const int r0 = blockIdx.x * rows, r1 = min(P, r0 + rows);
   const int ne = l * l;
   // up to 16 entries per thread (l <= 64, 256 threads)
   float hs[16], hc[16];
@@ -223,8 +312,9 @@ __global__ void k_gram_sum(int nb, int ne, const double* __restrict__ part, doub
 template <typename TX>
 fpca_status launch_cross_gram(fpca_ctx* ctx, int P, int l, const TX* A, const TX* B, double* part,
                               double* G, const char* name) {
-  const int nb = (P + GR_ROWS - 1) / GR_ROWS;
-  k_cross_gram<TX><<<nb, 256, 0, ctx->stream>>>(P, l, A, B, part);
+  const int rows = gram_rows(P, ctx->num_sms);
+  const int nb = (P + rows - 1) / rows;
+  k_cross_gram<TX><<<nb, 256, 0, ctx->stream>>>(P, l, rows, A, B, part);
   FPCA_LAUNCHED(ctx, name);
   k_gram_sum<<<(l * l + 7) / 8, 256, 0, ctx->stream>>>(nb, l * l, part, G);
   FPCA_LAUNCHED(ctx, "gram_sum");
@@ -246,26 +336,32 @@ __device__ __forceinline__ ff::F2 ff_of(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 
-// Upper Cholesky G = R'R and R^-1 in float-float (l <= 64), one block of
-// CH_THREADS threads, everything in shared memory.  Float-float rather than
+// Upper Cholesky G = R'R and R^-1 in float-float (l <= 64), one block,
+// everything in shared memory.  Float-float rather than
 // FP64: FP64 operations have long latency on this GPU and both factorisations
 // are serial chains of l steps (the Gram matrix factored here is itself
-// accurate to about 1e-14, from the compensated Gram kernel).  Each step's
-// updates are spread over all threads, so a step costs a few dependent
-// float-float operations and two barriers.
-//   Cholesky, right-looking: step j forms 1/sqrt(G_jj) and row j of R, then
-//   G_ik -= R_ji R_jk over the trailing upper triangle i <= k.
-//   Inverse, by rows from the bottom: x_ic = (delta_ic - a_ic) / R_ii for every
-//   column c >= i, then a_kc += R_ki x_ic for k < i (a starts at 0).
+// accurate to about 1e-14, from the compensated Gram kernel).  Every thread
+// owns fixed entries of the l x l arrays and each step costs one barrier:
+//   Cholesky, right-looking: at step j the owner of (i, k), j < i <= k,
+//   subtracts R_ji R_jk = (G_ji y)(G_jk y), y = 1/sqrt(G_jj), each thread forming
+//   y from the pivot itself.  Row j is final after step j - 1 and read unscaled;
+//   the rows are scaled into R after the last step.
+//   Inverse, by rows from the bottom: at step i the owner of (k, c), k < i <= c,
+//   adds R_ki x_ic, x_ic = (delta_ic - a_ic) / R_ii formed from row i of the sums
+//   (final after step i + 1); row i of R^-1 is x_i. (a starts at 0.)
 // Output: R^-1 (l x l row-major, upper triangular) as hi parts Ih and lo parts
 // Il.  Rank-deficient directions (pivot <= 1e-13 of the largest diagonal) get a
 // zero row and column.
-constexpr int CH_THREADS = 256;
+// OWN entries per thread: 1 (l <= 32, l^2 threads rounded up to a warp) or 4
+// (l <= 64, 1024 threads); a fixed count keeps the owned entries in registers
+// without predicated copies of the update for entries that do not exist.
 inline size_t chol_ff_smem(int l) { return sizeof(float) * (4 * (size_t)l * (l + 1) + 2 * l + 1); }
+inline int chol_ff_threads(int l) { return l <= 32 ? (l * l + 31) / 32 * 32 : 1024; }
 
-__global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __restrict__ G,
-                                                        float* __restrict__ Ih,
-                                                        float* __restrict__ Il) {
+template <int OWN>
+__global__ void __launch_bounds__(1024) k_chol_ff(int l, const double* __restrict__ G,
+                                                  float* __restrict__ Ih,
+                                                  float* __restrict__ Il) {
   extern __shared__ float chs[];
   const int ld = l + 1;
   float* Gh = chs;              // [l][ld] trailing matrix, then R by rows
@@ -275,14 +371,22 @@ __global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __r
   float* yh = Al + l * ld;      // [l] 1 / R_jj
   float* yl = yh + l;
   float* dmax_s = yl + l;
-  const int t = threadIdx.x;
-  for (int e = t; e < l * l; e += CH_THREADS) {
-    const int i = e / l, k = e - i * l;
-    const ff::F2 g = ff_of(G[e]);
-    Gh[i * ld + k] = g.hi;
-    Gl[i * ld + k] = g.lo;
-    Ah[i * ld + k] = 0.f;
-    Al[i * ld + k] = 0.f;
+  const int t = threadIdx.x, nt = blockDim.x;
+  int oi[OWN], ok[OWN];   // owned entries (row, column); -1: none
+#pragma unroll
+  for (int r = 0; r < OWN; ++r) {
+    const int e = t + r * nt;
+    oi[r] = -1;
+    ok[r] = 0;
+    if (e < l * l) {
+      oi[r] = e / l;
+      ok[r] = e - oi[r] * l;
+      const ff::F2 g = ff_of(G[e]);
+      Gh[oi[r] * ld + ok[r]] = g.hi;
+      Gl[oi[r] * ld + ok[r]] = g.lo;
+      Ah[oi[r] * ld + ok[r]] = 0.f;
+      Al[oi[r] * ld + ok[r]] = 0.f;
+    }
   }
   __syncthreads();
   if (t < 32) {
@@ -292,62 +396,71 @@ __global__ void __launch_bounds__(CH_THREADS) k_chol_ff(int l, const double* __r
     if (t == 0) *dmax_s = dm;
   }
   __syncthreads();
-  const float dmax = *dmax_s;
+  const float thr = 1e-13f * *dmax_s;
 #pragma unroll 1
   for (int j = 0; j < l; ++j) {
-    // row j of R (entries k >= j), every thread computing the same 1/sqrt(pivot)
     const ff::F2 piv = {Gh[j * ld + j], Gl[j * ld + j]};
-    ff::F2 y = ff::make(0.f);
-    if (piv.hi > 1e-13f * dmax) y = rsqrt_ff(piv);
-    __syncthreads();  // every thread has read the pivot
-    for (int k = j + t; k < l; k += CH_THREADS) {
-      const ff::F2 r = ff::mul(k == j ? piv : ff::F2{Gh[j * ld + k], Gl[j * ld + k]}, y);
-      Gh[j * ld + k] = r.hi;
-      Gl[j * ld + k] = r.lo;
-    }
-    if (t == 0) {
-      yh[j] = y.hi;
-      yl[j] = y.lo;
-    }
-    __syncthreads();
-    // trailing upper triangle j < i <= k < l
-    const int m = l - j - 1;
-    for (int e = t; e < m * m; e += CH_THREADS) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k < i) continue;
-      const ff::F2 g = ff::sub_mul(ff::F2{Gh[i * ld + k], Gl[i * ld + k]},
-                                   ff::F2{Gh[j * ld + i], Gl[j * ld + i]},
-                                   ff::F2{Gh[j * ld + k], Gl[j * ld + k]});
-      Gh[i * ld + k] = g.hi;
-      Gl[i * ld + k] = g.lo;
+    const ff::F2 y = piv.hi > thr ? rsqrt_ff(piv) : ff::make(0.f);
+#pragma unroll
+    for (int r = 0; r < OWN; ++r) {
+      const int i = oi[r], k = ok[r];
+      if (i > j && k >= i) {
+        const ff::F2 rji = ff::mul(ff::F2{Gh[j * ld + i], Gl[j * ld + i]}, y);
+        const ff::F2 rjk = ff::mul(ff::F2{Gh[j * ld + k], Gl[j * ld + k]}, y);
+        const ff::F2 g = ff::sub_mul(ff::F2{Gh[i * ld + k], Gl[i * ld + k]}, rji, rjk);
+        Gh[i * ld + k] = g.hi;
+        Gl[i * ld + k] = g.lo;
+      }
     }
     __syncthreads();
   }
-  // R^-1 by rows from the bottom; row i of R^-1 goes straight to Ih/Il
+  // 1 / R_jj from the final pivots, then the rows of R
+  for (int jj = t; jj < l; jj += nt) {
+    const ff::F2 piv = {Gh[jj * ld + jj], Gl[jj * ld + jj]};
+    const ff::F2 y = piv.hi > thr ? rsqrt_ff(piv) : ff::make(0.f);
+    yh[jj] = y.hi;
+    yl[jj] = y.lo;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < OWN; ++r) {
+    const int i = oi[r], k = ok[r];
+    if (i >= 0 && k >= i) {
+      const ff::F2 rr = ff::mul(ff::F2{Gh[i * ld + k], Gl[i * ld + k]}, ff::F2{yh[i], yl[i]});
+      Gh[i * ld + k] = rr.hi;
+      Gl[i * ld + k] = rr.lo;
+    }
+  }
+  __syncthreads();
+  // R^-1 by rows from the bottom
 #pragma unroll 1
-  for (int i = l - 1; i >= 0; --i) {
+  for (int i = l - 1; i > 0; --i) {
     const ff::F2 d = {yh[i], yl[i]};
-    for (int c = t; c < l; c += CH_THREADS) {
+#pragma unroll
+    for (int r = 0; r < OWN; ++r) {
+      const int k = oi[r], c = ok[r];
+      if (k >= 0 && k < i && c >= i) {
+        const ff::F2 x = ff::mul(
+            ff::add(ff::make(c == i ? 1.f : 0.f), ff::neg(ff::F2{Ah[i * ld + c], Al[i * ld + c]})), d);
+        const ff::F2 a = ff::add(ff::F2{Ah[k * ld + c], Al[k * ld + c]},
+                                 ff::mul(ff::F2{Gh[k * ld + i], Gl[k * ld + i]}, x));
+        Ah[k * ld + c] = a.hi;
+        Al[k * ld + c] = a.lo;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < OWN; ++r) {
+    const int i = oi[r], c = ok[r];
+    if (i >= 0) {
       ff::F2 x = ff::make(0.f);
       if (c >= i)
         x = ff::mul(ff::add(ff::make(c == i ? 1.f : 0.f), ff::neg(ff::F2{Ah[i * ld + c], Al[i * ld + c]})),
-                    d);
+                    ff::F2{yh[i], yl[i]});
       Ih[i * l + c] = x.hi;
       Il[i * l + c] = x.lo;
-      Ah[i * ld + c] = x.hi;  // row i of the sums is dead: keep x there for the update
-      Al[i * ld + c] = x.lo;
     }
-    __syncthreads();
-    for (int e = t; e < i * l; e += CH_THREADS) {
-      const int k = e / l, c = e % l;
-      if (c < i) continue;
-      const ff::F2 a = ff::add(ff::F2{Ah[k * ld + c], Al[k * ld + c]},
-                               ff::mul(ff::F2{Gh[k * ld + i], Gl[k * ld + i]},
-                                       ff::F2{Ah[i * ld + c], Al[i * ld + c]}));
-      Ah[k * ld + c] = a.hi;
-      Al[k * ld + c] = a.lo;
-    }
-    __syncthreads();
   }
 }
 
@@ -490,22 +603,80 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Cyclic parallel Jacobi sweeps (the pair schedule of k_jacobi) on A and V
-// in shared memory, in the arithmetic of T, until off(A)^2 <= tol * diag(A)^2
-// or max_sweeps; every thread of the block takes part.
-template <typename T>
-__device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double tol, T* cs,
-                              int* pr, double* red, int* done) {
+// Pair (p, q), p < q, of position i (0 <= i < ne / 2) at step `step` of a sweep:
+// the round-robin schedule of k_jacobi (ne even; q == n marks the dummy of odd n).
+__device__ __forceinline__ void rr_pair(int ne, int step, int i, int& p, int& q) {
+  const int m = ne - 1;
+  if (i == 0) {
+    p = m;
+    q = step;
+  } else {
+    p = step + i;
+    if (p >= m) p -= m;
+    q = step - i;
+    if (q < 0) q += m;
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// The rotation (c, s) that annihilates a_pq: tau = (a_qq - a_pp) / (2 a_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c.
+__device__ __forceinline__ void rr_rot(const float* A, int ld, int n, int p, int q, float& c,
+                                       float& sn) {
+  c = 1.f;
+  sn = 0.f;
+  if (q >= n) return;
+  const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+  if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-18f * sqrtf(fabsf(app) * fabsf(aqq))) {
+    const float tau = (aqq - app) / (2.f * apq);
+    const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    c = 1.f / sqrtf(1.f + t * t);
+    sn = t * c;
+  }
+}
+
+// Cyclic parallel Jacobi in FP32 on the n x n matrix in Acur (ld = n + 1), V
+// accumulating the rotations, until off(A)^2 <= tol diag(A)^2 or max_sweeps.
+// Every step applies ne / 2 disjoint rotations as one two-sided update:
+// each work item owns either a 2 x 2 block (rows of pair bi, columns of pair
+// bj) of A, read from Acur and written to Anext after both rotations, or the
+// two entries of one row k of V in the columns of pair bj (updated in place).
+// Each item forms the rotations it needs from Acur itself, so a step costs one
+// barrier.  Returns the buffer that holds the final A.
+// ITEMS work items per thread: (np^2 + n np) <= ITEMS * blockDim.x; 1 up to 1024
+// items (n <= 36), else 3 (n <= 64).
+template <int ITEMS>
+__device__ float* rr_jacobi_f32(int n, float* Acur, float* Anext, float* V, int max_sweeps,
+                                float tol, float* red, int* done) {
+  const int ld = n + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int ne = (n + 1) & ~1;
-  const int np = ne / 2;
+  const int ne = (n + 1) & ~1, np = ne / 2;
+  const int nblk = np * np, nitems = nblk + n * np;
+  int ia[ITEMS], ib[ITEMS];   // block (bi, bj), or V row k (ia = -1 - k) and pair bj
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const int w = tid + r * nt;
+    ia[r] = -(1 << 30);
+    ib[r] = 0;
+    if (w < nblk) {
+      ia[r] = w / np;
+      ib[r] = w - ia[r] * np;
+    } else if (w < nitems) {
+      const int v = w - nblk;
+      const int k = v / np;
+      ia[r] = -1 - k;
+      ib[r] = v - k * np;
+    }
+  }
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // the stopping test in the working type T: an FP32 Jacobi needs no FP64
-    // sums here (serial FP64 adds are slow on this GPU)
-    T off = T(0), dia = T(0);
+    float off = 0.f, dia = 0.f;
     for (int e = tid; e < n * n; e += nt) {
       const int r = e / n, c = e - r * n;
-      const T a = A[r * ld + c];
+      const float a = Acur[r * ld + c];
       if (r == c) dia += a * a;
       else off += a * a;
     }
@@ -514,111 +685,100 @@ __device__ void jacobi_sweeps(int n, int ld, T* A, T* V, int max_sweeps, double 
       dia += __shfl_xor_sync(0xffffffffu, dia, o);
     }
     if ((tid & 31) == 0) {
-      red[2 * (tid >> 5)] = (double)off;
-      red[2 * (tid >> 5) + 1] = (double)dia;
+      red[2 * (tid >> 5)] = off;
+      red[2 * (tid >> 5) + 1] = dia;
     }
     __syncthreads();
     if (tid == 0) {
-      T ot = T(0), dt = T(0);
-      for (int w = 0; w < nt / 32; ++w) {
-        ot += (T)red[2 * w];
-        dt += (T)red[2 * w + 1];
+      float ot = 0.f, dt = 0.f;
+      for (int w = 0; w < (nt + 31) / 32; ++w) {
+        ot += red[2 * w];
+        dt += red[2 * w + 1];
       }
-      *done = ((double)ot <= tol * (double)dt) || ot == T(0);
+      *done = (ot <= tol * dt) || ot == 0.f;
     }
     __syncthreads();
     if (*done) break;
     for (int step = 0; step < ne - 1; ++step) {
-      if (tid < np) {
-        const int i = tid;
-        int p, q;
-        if (i == 0) {
-          p = ne - 1;
-          q = step;
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        if (ia[r] == -(1 << 30)) continue;
+        int pj, qj;
+        float cj, sj;
+        rr_pair(ne, step, ib[r], pj, qj);
+        rr_rot(Acur, ld, n, pj, qj, cj, sj);
+        if (ia[r] >= 0) {
+          int pi, qi;
+          float ci, si;
+          rr_pair(ne, step, ia[r], pi, qi);
+          rr_rot(Acur, ld, n, pi, qi, ci, si);
+          // columns (pj, qj) first, then rows (pi, qi); index n is the dummy
+          const bool qiv = qi < n, qjv = qj < n;
+          const float m00 = Acur[pi * ld + pj];
+          const float m01 = qjv ? Acur[pi * ld + qj] : 0.f;
+          const float m10 = qiv ? Acur[qi * ld + pj] : 0.f;
+          const float m11 = (qiv && qjv) ? Acur[qi * ld + qj] : 0.f;
+          const float c00 = cj * m00 - sj * m01, c01 = sj * m00 + cj * m01;
+          const float c10 = cj * m10 - sj * m11, c11 = sj * m10 + cj * m11;
+          Anext[pi * ld + pj] = ci * c00 - si * c10;
+          if (qjv) Anext[pi * ld + qj] = ci * c01 - si * c11;
+          if (qiv) Anext[qi * ld + pj] = si * c00 + ci * c10;
+          if (qiv && qjv) Anext[qi * ld + qj] = si * c01 + ci * c11;
         } else {
-          p = (step + i) % (ne - 1);
-          q = (step - i + (ne - 1)) % (ne - 1);
-        }
-        if (p > q) {
-          const int tt = p;
-          p = q;
-          q = tt;
-        }
-        T c = T(1), sn = T(0);
-        if (q < n) {
-          const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-          if (fabs(apq) > T(1e-30) && fabs(apq) > T(1e-18) * sqrt(fabs(app) * fabs(aqq))) {
-            const T tau = (aqq - app) / (T(2) * apq);
-            const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-            c = T(1) / sqrt(T(1) + tt * tt);
-            sn = tt * c;
+          const int k = -1 - ia[r];
+          if (qj < n) {
+            const float vp = V[k * ld + pj], vq = V[k * ld + qj];
+            V[k * ld + pj] = cj * vp - sj * vq;
+            V[k * ld + qj] = sj * vp + cj * vq;
           }
         }
-        pr[2 * i] = p;
-        pr[2 * i + 1] = q;
-        cs[2 * i] = c;
-        cs[2 * i + 1] = sn;
       }
       __syncthreads();
-      for (int e = tid; e < np * n; e += nt) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pr[2 * i], q = pr[2 * i + 1];
-        if (q >= n) continue;
-        const T c = cs[2 * i], sn = cs[2 * i + 1];
-        const T akp = A[k * ld + p], akq = A[k * ld + q];
-        A[k * ld + p] = c * akp - sn * akq;
-        A[k * ld + q] = sn * akp + c * akq;
-        const T vkp = V[k * ld + p], vkq = V[k * ld + q];
-        V[k * ld + p] = c * vkp - sn * vkq;
-        V[k * ld + q] = sn * vkp + c * vkq;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * n; e += nt) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pr[2 * i], q = pr[2 * i + 1];
-        if (q >= n) continue;
-        const T c = cs[2 * i], sn = cs[2 * i + 1];
-        const T apk = A[p * ld + k], aqk = A[q * ld + k];
-        A[p * ld + k] = c * apk - sn * aqk;
-        A[q * ld + k] = sn * apk + c * aqk;
-      }
-      __syncthreads();
+      float* t = Acur;
+      Acur = Anext;
+      Anext = t;
     }
   }
+  return Acur;
 }
 
 // Symmetric eigendecomposition of the n x n (n <= 64) Rayleigh-Ritz matrix with an
-// FP64 result at a fraction of the FP64 work (FP64 is slow on this GPU):
+// accurate result at a fraction of the FP64 work (FP64 is slow on this GPU):
 //  1. cyclic Jacobi in FP32 on (A + A')/2 (off-diagonal to 3e-5 of the diagonal, at
 //     most 10 sweeps: FP32 rounding stalls it near 1e-7), one block;
 //  2. two steps of the iterative refinement of Ogita and Aishima ("Iterative
-//     refinement for symmetric eigenvalue decomposition", 2018) in FP64 on the FP32
+//     refinement for symmetric eigenvalue decomposition", 2018) on the FP32
 //     eigenvectors X:  R = I - X'X,  S = X'AX,  lambda_i = s_ii / (1 - r_ii),
 //     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs and
 //     r_ij / 2 inside clusters (gap <= delta = 2(|S - diag S| + |A| |R|), Frobenius
-//     norms), X <- X + X E.  Each step squares the error, so two steps reach FP64.
-//     Both steps run in one block (k_rr_refine) for n <= 32, as separate launches
-//     spread over n blocks beyond.
+//     norms), X <- X + X E.  Each step squares the error.  For n <= 32 both steps
+//     run in one block in float-float (k_rr_refine); beyond, in FP64 as separate
+//     launches spread over n blocks.
 // Outputs: A <- diag(lambda), V <- eigenvectors (columns, FP64).
+inline size_t rr_jacobi32_smem(int n) { return sizeof(float) * 3 * (size_t)n * (n + 1); }
+
+template <int ITEMS>
 __global__ void __launch_bounds__(1024)
     k_rr_jacobi32(int n, double* __restrict__ Ag, double* __restrict__ Asym,
                   double* __restrict__ X) {
-  __shared__ float A32[64 * 65], V32[64 * 65];
-  __shared__ float cs32[64];
-  __shared__ int pr[64];
-  __shared__ double red[64];
+  extern __shared__ float rjs[];
+  __shared__ float red[64];
   __shared__ int done;
+  const int ld = n + 1;
+  float* A0 = rjs;
+  float* A1 = A0 + n * ld;
+  float* V32 = A1 + n * ld;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e - (e / n) * n;
     const double a = 0.5 * (Ag[e] + Ag[j * n + i]);
     Asym[e] = a;
-    A32[i * (n + 1) + j] = (float)a;
-    V32[i * (n + 1) + j] = (i == j) ? 1.f : 0.f;
+    A0[i * ld + j] = (float)a;
+    V32[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_sweeps<float>(n, n + 1, A32, V32, 10, 1e-9, cs32, pr, red, &done);
-  for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * (n + 1) + e % n];
+  rr_jacobi_f32<ITEMS>(n, A0, A1, V32, 10, 1e-9f, red, &done);
+  for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * ld + e % n];
 }
 
 // The refinement for l > 32 (one SM's FP64 throughput is too low for the fused
@@ -712,19 +872,27 @@ __global__ void k_eig_order(int n, const double* __restrict__ A, int* __restrict
   }
 }
 
-// psi_j = Q u_{order[j]} (Q: P x l of type TX, U: l x l FP64), j < k.
+// psi_j = Q u_{order[j]} (Q: P x l of type TX, U: l x l FP64), j < k: one
+// thread per entry (j, r), its l-term FP64 sum in three interleaved chains
+// (dependent FP64 operations have long latency on this GPU).
 template <typename TX>
 __global__ void k_ritz_vectors(int P, int l, int k, const TX* __restrict__ Q,
                                const double* __restrict__ U, const int* __restrict__ order,
                                double* __restrict__ psi) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= P) return;
-  for (int j = 0; j < k; ++j) {
-    const int col = order[j];
-    double s = 0.0;
-    for (int i = 0; i < l; ++i) s += (double)Q[(long long)r * l + i] * U[(long long)i * l + col];
-    psi[(long long)j * P + r] = s;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // j * P + r
+  if (e >= (long long)P * k) return;
+  const int j = (int)(e / P), r = (int)(e - (long long)j * P);
+  const int col = order[j];
+  const TX* q = Q + (long long)r * l;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  int i = 0;
+  for (; i + 3 <= l; i += 3) {
+    s0 = fma((double)q[i], U[(long long)i * l + col], s0);
+    s1 = fma((double)q[i + 1], U[(long long)(i + 1) * l + col], s1);
+    s2 = fma((double)q[i + 2], U[(long long)(i + 2) * l + col], s2);
   }
+  for (; i < l; ++i) s0 = fma((double)q[i], U[(long long)i * l + col], s0);
+  psi[e] = (s0 + s1) + s2;
 }
 
 // Dense path: psi_j = V[:, order[j]].
@@ -737,156 +905,204 @@ __global__ void k_dense_vectors(int P, int k, const double* __restrict__ V,
 }
 
 // Sign (largest-magnitude entry positive, first occurrence on ties), rescale
-// phi = psi / sqrt(dV), lambda = theta dV, FVE.  One block per eigenvector.
-__global__ void k_finish(int P, int n, int k, double dv, const double* __restrict__ Aeig,
-                         const int* __restrict__ order, const double* __restrict__ trace,
-                         double* __restrict__ evals, double* __restrict__ evecs,
-                         double* __restrict__ fve) {
+// phi = psi / sqrt(dV) (inv_sqrt_dv = 1 / sqrt(dV) from the host), lambda = theta
+// dV, FVE = cumulative theta / trace.  One block per eigenvector.  The magnitudes
+// are compared through their bit patterns (non-negative doubles order as their
+// 64-bit integers), keyed with the index so that ties take the first entry.
+__device__ __forceinline__ unsigned long long fin_better(unsigned long long a, int ia,
+                                                         unsigned long long b, int ib) {
+  return (b > a || (b == a && ib < ia)) ? 1ull : 0ull;
+}
+
+__global__ void __launch_bounds__(1024)
+    k_finish(int P, int n, int k, double dv, double inv_sqrt_dv, const double* __restrict__ Aeig,
+             const int* __restrict__ order, const double* __restrict__ trace,
+             double* __restrict__ evals, double* __restrict__ evecs, double* __restrict__ fve) {
   const int j = blockIdx.x;
   double* v = evecs + (long long)j * P;
-  __shared__ double bv[1024];
-  __shared__ int bi[1024];
-  double best = -1.0;
+  __shared__ unsigned long long wb[32];
+  __shared__ int wi[32];
+  __shared__ double sgn;
+  unsigned long long best = 0;
   int bidx = 0x7fffffff;
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
-    const double a = fabs(v[r]);
-    if (a > best || (a == best && r < bidx)) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v[r]) & 0x7fffffffffffffffull;
+    if (bidx == 0x7fffffff || fin_better(best, bidx, a, r)) {
       best = a;
       bidx = r;
     }
   }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (oi != 0x7fffffff && (bidx == 0x7fffffff || fin_better(best, bidx, ob, oi))) {
+      best = ob;
+      bidx = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    wb[w] = best;
+    wi[w] = bidx;
+  }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      const double ob = bv[threadIdx.x + s];
-      const int oi = bi[threadIdx.x + s];
-      if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-        bv[threadIdx.x] = ob;
-        bi[threadIdx.x] = oi;
+  if (w == 0) {
+    best = lane < nw ? wb[lane] : 0ull;
+    bidx = lane < nw ? wi[lane] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (oi != 0x7fffffff && (bidx == 0x7fffffff || fin_better(best, bidx, ob, oi))) {
+        best = ob;
+        bidx = oi;
       }
     }
-    __syncthreads();
+    if (lane == 0) sgn = (bidx != 0x7fffffff && v[bidx] < 0.0) ? -inv_sqrt_dv : inv_sqrt_dv;
   }
-  const double sign = v[bi[0]] < 0.0 ? -1.0 : 1.0;
-  const double scale = sign / sqrt(dv);
   __syncthreads();
+  const double scale = sgn;
   for (int r = threadIdx.x; r < P; r += blockDim.x) v[r] *= scale;
   if (threadIdx.x == 0) {
     const double th = Aeig[(long long)order[j] * n + order[j]];
     evals[j] = th * dv;
     if (fve) {
       double cum = 0.0;
-      for (int i = 0; i <= j; ++i) cum += Aeig[(long long)order[i] * n + order[i]] * dv;
-      fve[j] = cum / (trace[0] * dv);
+      for (int i = 0; i <= j; ++i) cum += Aeig[(long long)order[i] * n + order[i]];
+      fve[j] = cum / trace[0];
     }
   }
 }
 
 // Both Ogita-Aishima refinement steps of k_rr_jacobi32's eigenvectors in one block
-// (l <= 32), with the l x l matrices in shared memory: per step
+// (n <= 32), in float-float with every n x n matrix in shared memory: per step
 // R = I - X'X, U = A X, S = X'U, lambda_i = s_ii / (1 - r_ii),
 // delta = 2 (|S - diag S| + |A| |R|), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
 // or r_ij / 2 inside clusters, X <- X + X E; then A <- diag(lambda), V <- X.
+// Float-float (about 2^-48) rather than FP64: the products are short serial
+// chains, and dependent FP64 operations have long latency on this GPU; the
+// result is accurate to about 1e-14, well below what the FP32 Sigma of the
+// projection resolves.  The cluster threshold delta only needs FP32.
 // Each product entry is split into two half-length dot products (neighbouring
-// threads), so the serial FP64 chains (long-latency on this GPU) stay about l/2
-// long.
+// threads) joined by a shuffle.
 constexpr int RF_THREADS = 1024;
-__device__ __forceinline__ void rf_product(int n, const double* L, bool tl, const double* M,
-                                           double* C, double diag, double sign) {
-  // C = diag I + sign op(L) M, op(L) = L' when tl; entry o by threads 2o and
-  // 2o + 1 (neighbouring lanes), each summing half of k, joined by a shuffle
-  const int h = (n + 1) / 2;
+
+struct FFMat {
+  float* h;
+  float* l;
+  __device__ ff::F2 at(int e) const { return {h[e], l[e]}; }
+  __device__ void put(int e, ff::F2 v) const {
+    h[e] = v.hi;
+    l[e] = v.lo;
+  }
+};
+
+// C = diag I + sign op(L) M, op(L) = L' when tl
+__device__ __forceinline__ void rf_product(int n, FFMat L, bool tl, FFMat M, FFMat C, float diag,
+                                           float sign) {
+  const int hn = (n + 1) / 2;
   const int ne2 = 2 * n * n;
   for (int base = 0; base < ne2; base += RF_THREADS) {
     const int e = base + threadIdx.x;
     const int o = e >> 1, part = e & 1;
-    double acc = 0.0;
+    ff::F2 acc = ff::make(0.f);
+    int i = 0, j = 0;
     if (e < ne2) {
-      const int i = o / n, j = o - i * n;
-      const int k0 = part * h, k1 = min(n, k0 + h);
-      for (int k = k0; k < k1; ++k) acc = fma(tl ? L[k * n + i] : L[i * n + k], M[k * n + j], acc);
+      i = o / n;
+      j = o - i * n;
+      const int k0 = part * hn, k1 = min(n, k0 + hn);
+      for (int k = k0; k < k1; ++k)
+        acc = ff::add(acc, ff::mul(L.at(tl ? k * n + i : i * n + k), M.at(k * n + j)));
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    const float oh = __shfl_xor_sync(0xffffffffu, acc.hi, 1);
+    const float ol = __shfl_xor_sync(0xffffffffu, acc.lo, 1);
     if (e < ne2 && part == 0) {
-      const int i = o / n, j = o - i * n;
-      C[o] = ((i == j) ? diag : 0.0) + sign * acc;
+      ff::F2 v = ff::add(acc, ff::F2{oh, ol});
+      if (sign < 0.f) v = ff::neg(v);
+      if (i == j) v = ff::add(v, ff::make(diag));
+      C.put(o, v);
     }
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ double rf_block_sum(double v, double* red) {
+__device__ __forceinline__ float rf_block_sum(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
-    double x = red[lane];  // RF_THREADS / 32 == 32 partials
+    float x = red[lane];  // RF_THREADS / 32 == 32 partials
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) red[32] = x;
   }
   __syncthreads();
-  const double r = red[32];
+  const float r = red[32];
   __syncthreads();
   return r;
 }
 
-inline size_t rr_refine_smem(int n) { return sizeof(double) * (5 * (size_t)n * n + n + 33); }
+inline size_t rr_refine_smem(int n) { return sizeof(float) * (10 * (size_t)n * n + 2 * n + 33); }
 
 __global__ void __launch_bounds__(RF_THREADS)
     k_rr_refine(int n, const double* __restrict__ Asym, const double* __restrict__ X0,
                 double* __restrict__ Ag, double* __restrict__ Vg) {
-  extern __shared__ double rfs[];
-  double* A = rfs;
-  double* X = A + n * n;
-  double* R = X + n * n;
-  double* U = R + n * n;
-  double* S = U + n * n;
-  double* lam = S + n * n;
-  double* red = lam + n;  // [33]
-  const int t = threadIdx.x, nn = n * n;
+  extern __shared__ float rfs[];
+  const int nn = n * n;
+  const FFMat A{rfs, rfs + nn}, X{rfs + 2 * nn, rfs + 3 * nn}, R{rfs + 4 * nn, rfs + 5 * nn},
+      U{rfs + 6 * nn, rfs + 7 * nn}, S{rfs + 8 * nn, rfs + 9 * nn};
+  const FFMat lam{rfs + 10 * nn, rfs + 10 * nn + n};
+  float* red = rfs + 10 * nn + 2 * n;  // [33]
+  const int t = threadIdx.x;
+  float an = 0.f;
   for (int e = t; e < nn; e += RF_THREADS) {
-    A[e] = Asym[e];
-    X[e] = X0[e];
+    const double a = Asym[e], x = X0[e];
+    const float ah = (float)a, xh = (float)x;
+    A.put(e, {ah, (float)(a - (double)ah)});
+    X.put(e, {xh, (float)(x - (double)xh)});
+    an += ah * ah;
   }
-  __syncthreads();
-  double an = 0.0;
-  for (int e = t; e < nn; e += RF_THREADS) an += A[e] * A[e];
-  an = rf_block_sum(an, red);
+  an = rf_block_sum(an, red);  // (its barriers also publish A and X)
   for (int step = 0; step < 2; ++step) {
-    rf_product(n, X, true, X, R, 1.0, -1.0);  // R = I - X'X
-    rf_product(n, A, false, X, U, 0.0, 1.0);  // U = A X
-    rf_product(n, X, true, U, S, 0.0, 1.0);   // S = X'AX
-    for (int i = t; i < n; i += RF_THREADS) lam[i] = S[i * n + i] / (1.0 - R[i * n + i]);
-    double so = 0.0, rn = 0.0;
+    rf_product(n, X, true, X, R, 1.f, -1.f);  // R = I - X'X
+    rf_product(n, A, false, X, U, 0.f, 1.f);  // U = A X
+    rf_product(n, X, true, U, S, 0.f, 1.f);   // S = X'AX
+    for (int i = t; i < n; i += RF_THREADS)
+      lam.put(i, ff::mul(S.at(i * n + i), ff::recip(ff::add(ff::make(1.f), ff::neg(R.at(i * n + i))))));
+    float so = 0.f, rn = 0.f;
     for (int e = t; e < nn; e += RF_THREADS) {
-      if (e / n != e % n) so += S[e] * S[e];
-      rn += R[e] * R[e];
+      if (e / n != e % n) so += S.h[e] * S.h[e];
+      rn += R.h[e] * R.h[e];
     }
     so = rf_block_sum(so, red);  // (the barriers inside also publish lam)
     rn = rf_block_sum(rn, red);
-    const double delta = 2.0 * (sqrt(so) + sqrt(an) * sqrt(rn));
+    const float delta = 2.f * (sqrtf(so) + sqrtf(an) * sqrtf(rn));
     for (int e = t; e < nn; e += RF_THREADS) {  // E into U (dead once S is formed)
       const int i = e / n, j = e - i * n;
-      const double gap = lam[j] - lam[i];
-      U[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lam[j] * R[e]) / gap;
+      const ff::F2 gap = ff::add(lam.at(j), ff::neg(lam.at(i)));
+      ff::F2 E;
+      if (i == j || fabsf(gap.hi) <= delta) {
+        E = R.at(e);
+        E.hi *= 0.5f;
+        E.lo *= 0.5f;
+      } else {
+        E = ff::mul(ff::add(S.at(e), ff::mul(lam.at(j), R.at(e))), ff::recip(gap));
+      }
+      U.put(e, E);
     }
     __syncthreads();
-    rf_product(n, X, false, U, S, 0.0, 1.0);  // S = X E
-    for (int e = t; e < nn; e += RF_THREADS) X[e] += S[e];
+    rf_product(n, X, false, U, S, 0.f, 1.f);  // S = X E
+    for (int e = t; e < nn; e += RF_THREADS) X.put(e, ff::add(X.at(e), S.at(e)));
     __syncthreads();
   }
   for (int e = t; e < nn; e += RF_THREADS) {
     const int i = e / n, j = e - i * n;
-    Ag[e] = (i == j) ? lam[i] : 0.0;
-    Vg[e] = X[e];
+    Ag[e] = (i == j) ? ff::to_double(lam.at(i)) : 0.0;
+    Vg[e] = ff::to_double(X.at(e));
   }
 }
 
-// Rayleigh-Ritz eigensolver (FP32 Jacobi + two FP64 refinement steps); scratch
-// holds 5 l^2 + l doubles.
+// Rayleigh-Ritz eigensolver (FP32 Jacobi + two refinement steps: float-float for
+// l <= 32, FP64 beyond); scratch holds 5 l^2 + l doubles.
 fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double* scratch) {
   const size_t nn = (size_t)l * l;
   double* As = scratch;   // symmetrised input
@@ -896,14 +1112,22 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
   double* S = U + nn;
   double* lam = S + nn;
   double* E = U;  // U is dead once S is formed
-  // one thread per element of a step's rotations (np pairs x l): wider blocks only
-  // make the three barriers of every step dearer
-  const int jt = min(1024, max(64, ((((l + 1) & ~1) / 2 * l + 31) / 32) * 32));
-  k_rr_jacobi32<<<1, jt, 0, ctx->stream>>>(l, A, As, X);
+  // one thread per work item of a step (np^2 blocks of A, l np pairs of V entries)
+  const int np = ((l + 1) & ~1) / 2;
+  const int items = np * np + l * np;
+  const int jt = min(1024, max(64, ((items + 31) / 32) * 32));
+  const size_t jsm = rr_jacobi32_smem(l);
+  if (items <= 1024) {
+    k_rr_jacobi32<1><<<1, jt, jsm, ctx->stream>>>(l, A, As, X);
+  } else {
+    if (jsm > 48 * 1024)
+      cudaFuncSetAttribute(k_rr_jacobi32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+    k_rr_jacobi32<3><<<1, jt, jsm, ctx->stream>>>(l, A, As, X);
+  }
   FPCA_LAUNCHED(ctx, "jacobi");
   if (l <= 32) {
     k_rr_refine<<<1, RF_THREADS, rr_refine_smem(l), ctx->stream>>>(l, As, X, A, V);
-    FPCA_LAUNCHED(ctx, "jacobi");
+    FPCA_LAUNCHED(ctx, "rr_refine");
     return FPCA_OK;
   }
   for (int step = 0; step < 2; ++step) {
@@ -923,25 +1147,32 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
   return FPCA_OK;
 }
 
+template <int LM, int RPT>
+void proj_launch(fpca_ctx* ctx, const ProjShape& sh, int P, int l, const float* S,
+                 const float* X, float* part) {
+  const size_t smem = sizeof(float) * (size_t)sh.kc * LM;
+  k_proj<LM, RPT><<<dim3(sh.tiles, sh.ranges), PJ_WARPS * 32, smem, ctx->stream>>>(
+      P, l, sh.kb, sh.kc, S, X, part);
+}
+
 template <typename TS>
-fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, TS* Y) {
-  const int nb8 = (P + 7) / 8;
-  const int ksplit = P >= 2048 ? 8 : 1;
-  const int ksplit2 = P >= 2048 ? 2 : 1;   // (measured best for 4 rows per warp)
-  cudaMemsetAsync(Y, 0, sizeof(TS) * (size_t)P * l, ctx->stream);
-  if (l <= 8) {
-    k_proj<TS, TS, 8, 4><<<dim3((nb8 + 3) / 4, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
-  } else if (l <= 20) {
-    k_proj<TS, TS, 20, 4><<<dim3((nb8 + 3) / 4, ksplit2), 256, 0, ctx->stream>>>(P, l, S, X, Y);
-  } else if (l <= 24) {
-    k_proj<TS, TS, 24, 4><<<dim3((nb8 + 3) / 4, ksplit2), 256, 0, ctx->stream>>>(P, l, S, X, Y);
-  } else if (l <= 64) {
-    k_proj<TS, TS, 64, 1><<<dim3(nb8, ksplit), 256, 0, ctx->stream>>>(P, l, S, X, Y);
+fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, TS* Y,
+                        float* part) {
+  if constexpr (sizeof(TS) != 4) {
+    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection runs on FP32 Sigma");
   } else {
-    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection built for l <= 64");
+    if (l > 64) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection built for l <= 64");
+    const ProjShape sh = proj_shape(P, l, ctx->num_sms);
+    if (sh.lm == 8) proj_launch<8, 4>(ctx, sh, P, l, S, X, part);
+    else if (sh.lm == 20) proj_launch<20, 2>(ctx, sh, P, l, S, X, part);
+    else if (sh.lm == 24) proj_launch<24, 2>(ctx, sh, P, l, S, X, part);
+    else proj_launch<64, 1>(ctx, sh, P, l, S, X, part);
+    FPCA_LAUNCHED(ctx, "proj");
+    const long long n = (long long)P * l;
+    k_proj_sum<<<(int)((n + 255) / 256), 256, 0, ctx->stream>>>(P, l, sh.ranges, part, Y);
+    FPCA_LAUNCHED(ctx, "proj_sum");
+    return FPCA_OK;
   }
-  FPCA_LAUNCHED(ctx, "proj");
-  return FPCA_OK;
 }
 
 // Orthonormal basis Q of range(Y) by Cholesky QR: passes = 2 (CholeskyQR2) for the
@@ -958,9 +1189,13 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, doub
     // Rinv holds R^-1 as hi and lo parts (l <= 64)
     float* Ih = reinterpret_cast<float*>(Rinv);
     float* Il = Ih + l * l;
-    cudaFuncSetAttribute(k_chol_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)chol_ff_smem(l));
-    k_chol_ff<<<1, CH_THREADS, chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
+    if (l <= 32)
+      k_chol_ff<1><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
+    else {
+      cudaFuncSetAttribute(k_chol_ff<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)chol_ff_smem(l));
+      k_chol_ff<4><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
+    }
     FPCA_LAUNCHED(ctx, "chol_inv");
     const long long ne = (long long)P * l;
     k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, Q);
@@ -982,8 +1217,9 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
                       3 * WsCarve::round(sizeof(double) * (size_t)l * l) +
                       2 * WsCarve::round(sizeof(double) * (size_t)n * n) +
                       WsCarve::round(sizeof(double) * 2 * n) + WsCarve::round(sizeof(int) * 3 * n) +
-                      WsCarve::round(sizeof(double) * (size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l) +
-                      WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) + 4096;
+                      WsCarve::round(sizeof(double) * gram_part_doubles(P, l, ctx->num_sms)) +
+                      WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) +
+                      WsCarve::round(sizeof(float) * proj_part_floats(P, l, ctx->num_sms)) + 4096;
   void* ws = fpca_workspace(ctx, need);
   if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
   WsCarve carve(ws);
@@ -1001,8 +1237,9 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   double* cs = carve.take<double>(2 * n);
   int* pairs = carve.take<int>(2 * n);
   int* order = carve.take<int>(n);
-  double* part = carve.take<double>((size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l);
+  double* part = carve.take<double>(gram_part_doubles(P, l, ctx->num_sms));
   double* rrs = carve.take<double>(5 * (size_t)l * l + l);
+  float* ppart = carve.take<float>(proj_part_floats(P, l, ctx->num_sms));
 
   cudaMemsetAsync(trace, 0, sizeof(double), ctx->stream);
   k_matrixize<TG, TS><<<dim3((P + 31) / 32, (P + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(
@@ -1022,7 +1259,8 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
     k_dense_vectors<<<(int)(((long long)P * k + 255) / 256), 256, 0, ctx->stream>>>(P, k, V, order,
                                                                                     evecs);
     FPCA_LAUNCHED(ctx, "dense_vectors");
-    k_finish<<<k, 1024, 0, ctx->stream>>>(P, P, k, dv, A, order, trace, evals, evecs, fve);
+    k_finish<<<k, 1024, 0, ctx->stream>>>(P, P, k, dv, 1.0 / std::sqrt(dv), A, order, trace,
+                                          evals, evecs, fve);
     FPCA_LAUNCHED(ctx, "eig_finish");
     return FPCA_OK;
   }
@@ -1032,17 +1270,17 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   } else {
     return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "random projection runs on FP32 Sigma");
   }
-  fpca_status s = launch_proj<TS>(ctx, P, l, S, Om, Y);
+  fpca_status s = launch_proj<TS>(ctx, P, l, S, Om, Y, ppart);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
     s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part, 1);
     if (s != FPCA_OK) return s;
-    s = launch_proj<TS>(ctx, P, l, S, Q, Y);
+    s = launch_proj<TS>(ctx, P, l, S, Q, Y, ppart);
     if (s != FPCA_OK) return s;
   }
   s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part);
   if (s != FPCA_OK) return s;
-  s = launch_proj<TS>(ctx, P, l, S, Q, Z);
+  s = launch_proj<TS>(ctx, P, l, S, Q, Z, ppart);
   if (s != FPCA_OK) return s;
   s = launch_cross_gram<TS>(ctx, P, l, Q, Z, part, A, "ritz_gram");
   if (s != FPCA_OK) return s;
@@ -1052,9 +1290,11 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   }
   k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, A, order);
   FPCA_LAUNCHED(ctx, "eig_order");
-  k_ritz_vectors<TS><<<(P + 127) / 128, 128, 0, ctx->stream>>>(P, l, k, Q, V, order, evecs);
+  k_ritz_vectors<TS><<<(int)(((long long)P * k + 255) / 256), 256, 0, ctx->stream>>>(
+      P, l, k, Q, V, order, evecs);
   FPCA_LAUNCHED(ctx, "ritz_vectors");
-  k_finish<<<k, 1024, 0, ctx->stream>>>(P, l, k, dv, A, order, trace, evals, evecs, fve);
+  k_finish<<<k, 1024, 0, ctx->stream>>>(P, l, k, dv, 1.0 / std::sqrt(dv), A, order, trace, evals,
+                                        evecs, fve);
   FPCA_LAUNCHED(ctx, "eig_finish");
   return FPCA_OK;
 }
@@ -1085,15 +1325,15 @@ fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, 
 // CholeskyQR2 and power iterations, Rayleigh-Ritz in FP64, rescaling and FVE
 // (trace of Sigma supplied by the caller in ws.trace[0], unscaled).
 // ---------------------------------------------------------------------------
-size_t rproj_ws_bytes(int P, int l) {
+size_t rproj_ws_bytes(const fpca_ctx* ctx, int P, int l) {
   return 3 * WsCarve::round(sizeof(float) * (size_t)P * l) +
          5 * WsCarve::round(sizeof(double) * (size_t)l * l) + WsCarve::round(sizeof(double) * 4) +
          WsCarve::round(sizeof(int) * 3 * (size_t)l) +
-         WsCarve::round(sizeof(double) * (size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l) +
+         WsCarve::round(sizeof(double) * gram_part_doubles(P, l, ctx->num_sms)) +
          WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) + 2048;
 }
 
-void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w) {
+void rproj_ws_carve(const fpca_ctx* ctx, WsCarve& c, int P, int l, RprojWs& w) {
   w.Y = c.take<float>((size_t)P * l);
   w.Q = c.take<float>((size_t)P * l);
   w.Z = c.take<float>((size_t)P * l);
@@ -1104,7 +1344,7 @@ void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w) {
   w.V = c.take<double>((size_t)l * l);
   w.trace = c.take<double>(4);
   w.order = c.take<int>(3 * (size_t)l);
-  w.part = c.take<double>((size_t)((P + GR_ROWS - 1) / GR_ROWS) * l * l);
+  w.part = c.take<double>(gram_part_doubles(P, l, ctx->num_sms));
   w.rr = c.take<double>(5 * (size_t)l * l + l);
 }
 
@@ -1129,10 +1369,11 @@ fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, 
   if (s != FPCA_OK) return s;
   k_eig_order<<<1, 1024, 0, ctx->stream>>>(l, w.A, w.order);
   FPCA_LAUNCHED(ctx, "eig_order");
-  k_ritz_vectors<float><<<(P + 127) / 128, 128, 0, ctx->stream>>>(P, l, k, w.Q, w.V, w.order,
-                                                                   evecs);
+  k_ritz_vectors<float><<<(int)(((long long)P * k + 255) / 256), 256, 0, ctx->stream>>>(
+      P, l, k, w.Q, w.V, w.order, evecs);
   FPCA_LAUNCHED(ctx, "ritz_vectors");
-  k_finish<<<k, 1024, 0, ctx->stream>>>(P, l, k, dv, w.A, w.order, w.trace, evals, evecs, fve);
+  k_finish<<<k, 1024, 0, ctx->stream>>>(P, l, k, dv, 1.0 / std::sqrt(dv), w.A, w.order, w.trace,
+                                        evals, evecs, fve);
   FPCA_LAUNCHED(ctx, "eig_finish");
   return FPCA_OK;
 }

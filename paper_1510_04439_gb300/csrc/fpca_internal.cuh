@@ -138,8 +138,8 @@ struct RprojWs {
   double* part;  // per-block partial Gram products
   double* rr;    // Rayleigh-Ritz eigensolver scratch (5 l^2 + l)
 };
-size_t rproj_ws_bytes(int P, int l);
-void rproj_ws_carve(WsCarve& c, int P, int l, RprojWs& w);
+size_t rproj_ws_bytes(const fpca_ctx* ctx, int P, int l);
+void rproj_ws_carve(const fpca_ctx* ctx, WsCarve& c, int P, int l, RprojWs& w);
 fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, double dv,
                            const float* omega, RprojOp op, const RprojWs& w, double* evals,
                            double* evecs, double* fve);

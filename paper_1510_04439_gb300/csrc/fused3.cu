@@ -1827,12 +1827,12 @@ fpca_status fpca_rproj_eig_factor(fpca_ctx* ctx, const fpca_grid* grid, const vo
   F3Work w{};
   void* ws = nullptr;
   const int P = grid ? grid->m[0] * grid->m[1] * grid->m[2] : 0;
-  fpca_status s = f3_setup(ctx, grid, factor, n, h, l, rproj_ws_bytes(P, l), w, &ws);
+  fpca_status s = f3_setup(ctx, grid, factor, n, h, l, rproj_ws_bytes(ctx, P, l), w, &ws);
   if (s != FPCA_OK) return s;
   WsCarve c(ws);
   f3_work_carve(c, w);
   RprojWs rw;
-  rproj_ws_carve(c, P, l, rw);
+  rproj_ws_carve(ctx, c, P, l, rw);
   s = f3_prepare(ctx, w, factor, h);
   if (s != FPCA_OK) return s;
   cudaMemsetAsync(rw.trace, 0, sizeof(double), ctx->stream);

@@ -351,6 +351,41 @@ def test_eig_dense_and_rproj_vs_oracle(ctx, B):
     assert np.allclose(host(fve), fve_r, rtol=1e-4)
 
 
+@pytest.mark.parametrize("m,l", [((23, 31), 6), ((23, 31), 12), ((23, 31), 18), ((17, 45), 24),
+                                 ((17, 45), 40), ((40, 41), 64)])
+def test_rproj_widths_and_ragged_grids(ctx, m, l):
+    """Random projection at every width the projection kernel is built for (l <= 8, 20,
+    24, 64), on grids whose node counts leave ragged row tiles and k ranges, with a
+    ragged domain; the same Omega on both sides."""
+    P = m[0] * m[1]
+    rng = np.random.default_rng(l + P)
+    s = (np.arange(m[0]) + 0.5) / m[0]
+    t = (np.arange(m[1]) + 0.5) / m[1]
+    S, T = np.meshgrid(s, t, indexing="ij")
+    lam0 = [8.0, 4.0, 2.0, 1.0, 0.5, 0.25]
+    phis = [np.cos(np.pi * (j + 1) * S) * np.sin(np.pi * (j % 3 + 1) * T + 0.3 * j)
+            for j in range(len(lam0))]
+    F = np.stack([f.ravel() for f in phis], axis=1)
+    G = F @ np.diag(lam0) @ F.T
+    E = rng.standard_normal((P, P)) * 1e-3
+    G = G + 0.5 * (E + E.T)
+    cnt = ((S - 0.5) ** 2 + (T - 0.5) ** 2 <= 0.23).astype(np.int32).ravel()
+    k = min(6, l - 1)   # the projection needs k < l
+    om = fs.gaussian_test_matrix(P, l, 11)
+    ev = torch.empty(k, dtype=torch.float64, device=DEV)
+    vec = torch.empty(k, P, dtype=torch.float64, device=DEV)
+    fve = torch.empty(k, dtype=torch.float64, device=DEV)
+    ctx.rproj_eig(m, dev(G, torch.float32), k, ev, vec, fve, domain=dev(cnt, torch.int32),
+                  omega=dev(om, torch.float32), power_iters=2)
+    ctx.sync()
+    lam_r, phi_r, fve_r = oe.rproj_eig(G.astype(np.float32).astype(np.float64), m, cnt > 0, om,
+                                       k, 2)
+    assert np.allclose(host(ev), lam_r, rtol=1e-4)
+    for j in range(k):
+        assert oe.subspace_angle(host(vec)[j:j + 1].T, phi_r[:, j:j + 1]) <= 1e-3
+    assert np.allclose(host(fve), fve_r, rtol=1e-4)
+
+
 # ----------------------------------------------------------------------------
 # end to end
 # ----------------------------------------------------------------------------
