@@ -176,57 +176,64 @@ __global__ void k_bin_mean_sparse(int n, long long N, int d, int m0, int m1, int
 //   plane 0: M_ip                 (pair counts  C = M'M)
 //   plane 1: w_i M_ip             (W = (wM)'M, exact 0/1 right operand)
 //   plane 2: sqrt(w_i) R_ip M_ip  (V = R~'R~)
-// A 32 x 32 tile is transposed through shared memory.
-__global__ void k_cov_operands_bf16(int n, int P, int Kpad, const void* __restrict__ y,
-                                    int y_prec, const uint8_t* __restrict__ mask,
-                                    const int32_t* __restrict__ Ni, const double* __restrict__ mu,
-                                    int mode, __nv_bfloat16* __restrict__ ops) {
-  __shared__ float tm[32][33], tw[32][33], tr[32][33];
-  __shared__ float wsub[32], swsub[32], muf[32];
-  const int i0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+// A tile of 64 subjects x 32 nodes is transposed through shared memory: the
+// reads run along the nodes (y, mask), the writes along the subjects as BF16
+// pairs (128 bytes per node and plane).
+template <typename TY>
+__global__ void __launch_bounds__(256)
+    k_cov_operands_bf16(int n, int P, int Kpad, const TY* __restrict__ y,
+                        const uint8_t* __restrict__ mask, const int32_t* __restrict__ Ni,
+                        const double* __restrict__ mu, int mode, __nv_bfloat162* __restrict__ ops) {
+  __shared__ float tw[64][33], tr[64][33];
+  __shared__ uint8_t tm[64][36];
+  __shared__ float wsub[64], swsub[64], muf[32];
+  const int i0 = blockIdx.y * 64, p0 = blockIdx.x * 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   // per-subject weights w_i = 1/(N_i (N_i - 1)) and sqrt(w_i), and the mean at the
   // block's 32 nodes, once per block and in FP32: the operands are rounded to
   // BF16, so FP32 is ample (and FP64 operations are slow on this GPU)
-  if (threadIdx.y == 0) {
-    const int i = i0 + threadIdx.x;
+  if (tid < 64) {
+    const int i = i0 + tid;
     const int N = i < n ? Ni[i] : 0;
     const float wi = N >= 2 ? 1.f / ((float)N * (float)(N - 1)) : 0.f;
-    wsub[threadIdx.x] = wi;
-    swsub[threadIdx.x] = sqrtf(wi);
-  } else if (threadIdx.y == 1) {
-    const int p = p0 + threadIdx.x;
-    muf[threadIdx.x] = (p < P && mode == FPCA_COV_RESIDUAL) ? (float)mu[p] : 0.f;
+    wsub[tid] = wi;
+    swsub[tid] = sqrtf(wi);
+  } else if (tid < 96) {
+    const int p = p0 + tid - 64;
+    muf[tid - 64] = (p < P && mode == FPCA_COV_RESIDUAL) ? (float)mu[p] : 0.f;
+  }
+  // this thread's 8 observations, loads first (mask and y together)
+  TY yv[8];
+  uint8_t ob[8];
+  const int p = p0 + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int i = i0 + threadIdx.y + 8 * u;
+    const bool in = i < n && p < P;
+    const size_t idx = (size_t)i * P + p;
+    ob[u] = in ? (mask ? mask[idx] : (uint8_t)1) : (uint8_t)0;
+    yv[u] = in ? y[idx] : TY(0);
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int i = i0 + r, p = p0 + threadIdx.x;
-    float fm = 0.f, fw = 0.f, fr = 0.f;
-    if (i < n && p < P) {
-      const size_t idx = (size_t)i * P + p;
-      const bool obs = mask ? mask[idx] != 0 : true;
-      if (obs) {
-        const float yy = y_prec == FPCA_F64 ? (float)static_cast<const double*>(y)[idx]
-                                            : static_cast<const float*>(y)[idx];
-        const float rr = yy - muf[threadIdx.x];
-        fm = 1.f;
-        fw = wsub[r];
-        fr = swsub[r] * rr;
-      }
-    }
-    tm[r][threadIdx.x] = fm;
-    tw[r][threadIdx.x] = fw;
-    tr[r][threadIdx.x] = fr;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int r = threadIdx.y + 8 * u;
+    const bool obs = ob[u] != 0;
+    tm[r][threadIdx.x] = obs ? 1 : 0;
+    tw[r][threadIdx.x] = obs ? wsub[r] : 0.f;
+    tr[r][threadIdx.x] = obs ? swsub[r] * ((float)yv[u] - muf[threadIdx.x]) : 0.f;
   }
   __syncthreads();
-  const size_t plane = (size_t)P * Kpad;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int p = p0 + r, i = i0 + threadIdx.x;
-    if (p < P && i < Kpad) {
-      const size_t o = (size_t)p * Kpad + i;
-      ops[o] = __float2bfloat16_rn(tm[threadIdx.x][r]);
-      ops[plane + o] = __float2bfloat16_rn(tw[threadIdx.x][r]);
-      ops[2 * plane + o] = __float2bfloat16_rn(tr[threadIdx.x][r]);
-    }
+  // node p0 + c, subjects i0 + 2 lane and i0 + 2 lane + 1
+  const size_t plane = (size_t)P * Kpad / 2;   // in BF16 pairs
+  for (int c = threadIdx.y; c < 32; c += 8) {
+    const int pn = p0 + c;
+    if (pn >= P) continue;
+    const int a = 2 * threadIdx.x;
+    const size_t o = ((size_t)pn * Kpad + i0) / 2 + threadIdx.x;
+    ops[o] = __floats2bfloat162_rn((float)tm[a][c], (float)tm[a + 1][c]);
+    ops[plane + o] = __floats2bfloat162_rn(tw[a][c], tw[a + 1][c]);
+    ops[2 * plane + o] = __floats2bfloat162_rn(tr[a][c], tr[a + 1][c]);
   }
 }
 
@@ -400,9 +407,15 @@ fpca_status launch_bin_mean_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, con
 fpca_status launch_cov_operands_bf16(fpca_ctx* ctx, int n, int P, int Kpad, const void* y,
                                      int y_prec, const uint8_t* mask, const int32_t* Ni,
                                      const double* mu, int mode, uint16_t* ops) {
-  dim3 grid((P + 31) / 32, Kpad / 32);
-  k_cov_operands_bf16<<<grid, dim3(32, 8), 0, ctx->stream>>>(
-      n, P, Kpad, y, y_prec, mask, Ni, mu, mode, reinterpret_cast<__nv_bfloat16*>(ops));
+  if (Kpad % 64 != 0) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "Kpad = %d", Kpad);
+  dim3 grid((P + 31) / 32, Kpad / 64);
+  __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(ops);
+  if (y_prec == FPCA_F64)
+    k_cov_operands_bf16<double><<<grid, dim3(32, 8), 0, ctx->stream>>>(
+        n, P, Kpad, static_cast<const double*>(y), mask, Ni, mu, mode, o2);
+  else
+    k_cov_operands_bf16<float><<<grid, dim3(32, 8), 0, ctx->stream>>>(
+        n, P, Kpad, static_cast<const float*>(y), mask, Ni, mu, mode, o2);
   FPCA_LAUNCHED(ctx, "cov_operands_bf16");
   return FPCA_OK;
 }

@@ -625,6 +625,10 @@ __device__ __forceinline__ void rr_pair(int ne, int step, int i, int& p, int& q)
 
 // The rotation (c, s) that annihilates a_pq: tau = (a_qq - a_pp) / (2 a_pq),
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c.
+// The quotients and 1 / sqrt(1 + t^2) (argument in [1, 2]) use the fast
+// approximate forms: c^2 + s^2 = 1 then holds to a few FP32 ulps, and the
+// refinement that follows the FP32 Jacobi restores orthogonality anyway.  The
+// square root of 1 + tau^2 stays exact so that tau^2 = inf still gives t = 0.
 __device__ __forceinline__ void rr_rot(const float* A, int ld, int n, int p, int q, float& c,
                                        float& sn) {
   c = 1.f;
@@ -632,9 +636,9 @@ __device__ __forceinline__ void rr_rot(const float* A, int ld, int n, int p, int
   if (q >= n) return;
   const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
   if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-18f * sqrtf(fabsf(app) * fabsf(aqq))) {
-    const float tau = (aqq - app) / (2.f * apq);
-    const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-    c = 1.f / sqrtf(1.f + t * t);
+    const float tau = __fdividef(aqq - app, 2.f * apq);
+    const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sqrtf(1.f + tau * tau));
+    c = rsqrtf(1.f + t * t);
     sn = t * c;
   }
 }
@@ -1010,6 +1014,7 @@ __device__ __forceinline__ void rf_product(int n, FFMat L, bool tl, FFMat M, FFM
       i = o / n;
       j = o - i * n;
       const int k0 = part * hn, k1 = min(n, k0 + hn);
+#pragma unroll 4
       for (int k = k0; k < k1; ++k)
         acc = ff::add(acc, ff::mul(L.at(tl ? k * n + i : i * n + k), M.at(k * n + j)));
     }
