@@ -649,13 +649,15 @@ __device__ __forceinline__ void rr_rot(const float* A, int ld, int n, int p, int
 // each work item owns either a 2 x 2 block (rows of pair bi, columns of pair
 // bj) of A, read from Acur and written to Anext after both rotations, or the
 // two entries of one row k of V in the columns of pair bj (updated in place).
-// Each item forms the rotations it needs from Acur itself, so a step costs one
-// barrier.  Returns the buffer that holds the final A.
+// With one item per thread each item forms the rotations it needs from Acur
+// itself, so a step costs one barrier; with several items per thread the
+// rotations are formed once into cs (np pairs) behind a second barrier.
+// Returns the buffer that holds the final A.
 // ITEMS work items per thread: (np^2 + n np) <= ITEMS * blockDim.x; 1 up to 1024
 // items (n <= 36), else 3 (n <= 64).
 template <int ITEMS>
 __device__ float* rr_jacobi_f32(int n, float* Acur, float* Anext, float* V, int max_sweeps,
-                                float tol, float* red, int* done) {
+                                float tol, float* red, float* cs, int* done) {
   const int ld = n + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = (n + 1) & ~1, np = ne / 2;
@@ -704,18 +706,37 @@ __device__ float* rr_jacobi_f32(int n, float* Acur, float* Anext, float* V, int 
     __syncthreads();
     if (*done) break;
     for (int step = 0; step < ne - 1; ++step) {
+      if constexpr (ITEMS > 1) {
+        // several items per thread: the np rotations once, then the updates
+        for (int i = tid; i < np; i += nt) {
+          int p, q;
+          rr_pair(ne, step, i, p, q);
+          rr_rot(Acur, ld, n, p, q, cs[2 * i], cs[2 * i + 1]);
+        }
+        __syncthreads();
+      }
 #pragma unroll
       for (int r = 0; r < ITEMS; ++r) {
         if (ia[r] == -(1 << 30)) continue;
         int pj, qj;
         float cj, sj;
         rr_pair(ne, step, ib[r], pj, qj);
-        rr_rot(Acur, ld, n, pj, qj, cj, sj);
+        if constexpr (ITEMS > 1) {
+          cj = cs[2 * ib[r]];
+          sj = cs[2 * ib[r] + 1];
+        } else {
+          rr_rot(Acur, ld, n, pj, qj, cj, sj);
+        }
         if (ia[r] >= 0) {
           int pi, qi;
           float ci, si;
           rr_pair(ne, step, ia[r], pi, qi);
-          rr_rot(Acur, ld, n, pi, qi, ci, si);
+          if constexpr (ITEMS > 1) {
+            ci = cs[2 * ia[r]];
+            si = cs[2 * ia[r] + 1];
+          } else {
+            rr_rot(Acur, ld, n, pi, qi, ci, si);
+          }
           // columns (pj, qj) first, then rows (pi, qi); index n is the dummy
           const bool qiv = qi < n, qjv = qj < n;
           const float m00 = Acur[pi * ld + pj];
@@ -767,6 +788,7 @@ __global__ void __launch_bounds__(1024)
                   double* __restrict__ X) {
   extern __shared__ float rjs[];
   __shared__ float red[64];
+  __shared__ float cs[64];   // (c, s) of each pair (ITEMS > 1)
   __shared__ int done;
   const int ld = n + 1;
   float* A0 = rjs;
@@ -781,7 +803,7 @@ __global__ void __launch_bounds__(1024)
     V32[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  rr_jacobi_f32<ITEMS>(n, A0, A1, V32, 10, 1e-9f, red, &done);
+  rr_jacobi_f32<ITEMS>(n, A0, A1, V32, 10, 1e-9f, red, cs, &done);
   for (int e = tid; e < n * n; e += nt) X[e] = (double)V32[(e / n) * ld + e % n];
 }
 
