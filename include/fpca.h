@@ -209,10 +209,13 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
  *  full = 0: random projection (Section 3.4) with the caller's Gaussian
  *   test matrix omega (P x l float, k < l <= 64): Y = Sigma Omega, power_iters
  *   rounds of Q = orth(Y), Y = Sigma Q, then Q = orth(Y), B = Q' Sigma Q and
- *   the eigenpairs of B (Rayleigh-Ritz): FP32 Jacobi refined by two FP64
- *   Ogita-Aishima steps.  orth is Cholesky QR (one pass between power
- *   iterations, two at the end) on a compensated FP32 Gram matrix with the
- *   Cholesky factor and its inverse in float-float (about 48 bits).
+ *   the eigenpairs of B (Rayleigh-Ritz): FP32 Jacobi refined by two
+ *   Ogita-Aishima steps (float-float, about 1e-14, for l <= 32; FP64 beyond).
+ *   The products Sigma X are FP32 with the partial sums of the k ranges
+ *   added in a fixed order (the result does not depend on scheduling).
+ *   orth is Cholesky QR (one pass between power iterations, two at the end)
+ *   on a compensated FP32 Gram matrix with the Cholesky factor and its
+ *   inverse in float-float (about 48 bits).
  * Outputs (device, FP64): evals k, evecs P x k (column-major: vector j at
  * evecs + j*P), fve k (may be NULL). */
 fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gamma,
@@ -408,8 +411,9 @@ fpca_status fpca_mise(fpca_ctx* ctx, const fpca_grid* grid, const float* xhat, c
  * Arithmetic: residuals R~ = (Y - mu_hat)/sqrt(n) in BF16 for the tensor-core
  * products (FP32 accumulation), FP32 elsewhere; per-point local solves in
  * FP32 (an ill-conditioned one makes fpca_sync() return FPCA_E_NUMERIC);
- * Rayleigh-Ritz in FP64.  For fully observed data every local system is
- * regular (status FPCA_PT_OK at every point), so no status array is produced.
+ * Rayleigh-Ritz as fpca_rproj_eig (l = 64: FP32 Jacobi, FP64 refinement).
+ * For fully observed data every local system is regular (status FPCA_PT_OK
+ * at every point), so no status array is produced.
  */
 
 /* Bytes of the factored covariance bins of n subjects on `grid` (0 if the
@@ -453,8 +457,9 @@ fpca_status fpca_smooth_cov_diag(fpca_ctx* ctx, const fpca_grid* grid, const voi
                                  const double* h, double* diag);
 
 /* Random projection of Section 3.4 on the fused operator: Y = Gamma_hat Omega,
- * power_iters re-orthonormalised power steps, Rayleigh-Ritz on l columns in
- * FP64, rescaling lambda = theta dV, phi = psi / sqrt(dV) (dV = 1/P), sign and
+ * power_iters re-orthonormalised power steps, Rayleigh-Ritz on l columns
+ * (FP32 Jacobi with two refinement steps, as fpca_rproj_eig), rescaling
+ * lambda = theta dV, phi = psi / sqrt(dV) (dV = 1/P), sign and
  * FVE (trace of Gamma_hat from its diagonal) as fpca_rproj_eig.
  *  omega  P x l floats (device), k < l <= 64.
  *  evals k, evecs P x k column-major (vector j at evecs + j*P), fve k (may
