@@ -273,6 +273,12 @@ def oracle_sample_rate(seconds, min_points=20, seed=0):
     return done / el, done, el
 
 
+def workload_config():
+    """The keys that name the timed workload; both arms report them."""
+    return {"workload": WORKLOAD, "grid": [64, 64], "n": 1000, "cov_points": 64 ** 4,
+            "h": list(H), "k": K_EIG, "l": L_RP, "power_iters": Q_POWER}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -308,7 +314,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{per_step} output pairs per step"},
+        "config": dict(workload_config(), sample=f"{per_step} output pairs per step",
+                       precision="FP64 oracle (binned local linear fits written out)"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"FP64 oracle window sums at {per_step} random in-domain "
                                    "output pairs per step; bins precomputed"},
@@ -670,8 +677,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [64, 64], "n": 1000, "cov_points": int(units),
-                       "h": list(H), "k": K_EIG, "l": L_RP, "power_iters": Q_POWER,
+            "config": {**workload_config(),
                        "precision": "BF16 tcgen05 binning (FP32 accumulate, exact counts); "
                                     "FP32 compensated moments; FP32 solve, float-float "
                                     "re-solve of ill-conditioned points; Rayleigh-Ritz by FP32 "
