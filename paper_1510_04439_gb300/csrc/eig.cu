@@ -4,9 +4,10 @@
 //  Sigma    = (G + G')/2, NaN -> 0, rows/columns outside the domain -> 0
 //  Y        = Sigma Omega;  repeat q times { Q = orth(Y); Y = Sigma Q }
 //  Q        = orth(Y) by CholeskyQR2 (compensated FP32 Gram, float-float Cholesky)
-//  B        = Q' Sigma Q (FP64), eigenpairs of B by cyclic Jacobi (FP64)
+//  B        = Q' Sigma Q (compensated FP32 sums, FP64 result); eigenpairs of B
+//             by FP32 Jacobi and two Ogita-Aishima refinement steps
 //  Psi      = Q U;  lambda = theta dV;  phi = psi / sqrt(dV);  dV = 1/P
-// The dense path (full = 1) runs the same Jacobi solver on Sigma itself.
+// The dense path (full = 1) runs a cyclic FP64 Jacobi solver on Sigma itself.
 #include <cmath>
 
 #include "fpca_internal.cuh"
