@@ -100,3 +100,15 @@ def test_cov_factor_bytes_is_a_host_function(libpath):
     for m, n in [((32, 32, 32), 2000), ((6, 5, 12), 45), ((8, 8, 8), 1)]:
         assert size(m, n) == expect(m, n)
     assert size((16, 16), 10) == 0          # not a 3-D grid
+
+
+def test_bw_param_count_is_the_oracle_layout(libpath):
+    """The network's parameter count needs no device and equals the oracle's layout:
+    for each layer of 32 -> 256 -> 256 -> 256 -> 6, fan_in x fan_out weights then fan_out
+    biases."""
+    from oracle import mlp as om
+    from paper_1510_04439_gb300 import binding
+    lib = binding.load(libpath)
+    n = int(lib.fpca_bw_param_count())
+    assert n == om.param_count()
+    assert n == sum(fi * fo + fo for fi, fo in [(32, 256), (256, 256), (256, 256), (256, 6)])
