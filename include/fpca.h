@@ -49,8 +49,9 @@ typedef enum {
 
 /* Arithmetic of a stage.
  *  F64   FP64 throughout (CUDA cores).
- *  F32   FP32 moment sums, FP32 local solve escalated to FP64 where a pivot
- *        ratio falls below 1e-2.
+ *  F32   FP32 moment sums, FP32 local solve; a point whose FP32 pivot ratio
+ *        falls below 1e-2 is solved again in float-float arithmetic (pairs of
+ *        FP32 numbers, about 48 significant bits).
  *  F32C  as F32 with Kahan-compensated moment sums.
  *  BF16  binning products on tcgen05 tensor cores, BF16 operands, FP32
  *        accumulation in tensor memory; pair counts stay exact integers. */
@@ -118,6 +119,16 @@ fpca_status fpca_sync(fpca_ctx* ctx);
 /* Number of kernels this context has launched so far (host counter). */
 uint64_t fpca_launch_count(const fpca_ctx* ctx);
 
+/* Self-check of the device-side failure detection.  Launches one thread
+ * that waits on an on-chip barrier (an mbarrier expecting one arrival) with
+ * the bounded wait every waiting kernel of this library uses.  arrive != 0:
+ * the barrier is completed first and the next fpca_sync() returns FPCA_OK.
+ * arrive == 0: nothing completes it, the wait gives up after its limit
+ * (about 2 s of GPU time) and the next fpca_sync() returns FPCA_E_TIMEOUT;
+ * the kernel exits normally, so the context and the GPU stay usable and
+ * the following fpca_sync() returns FPCA_OK again. */
+fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive);
+
 /* Kernel timing (off by default).  When enabled, a CUDA event is recorded on
  * the context stream at the start of every entry point and after every
  * kernel launch; a kernel's time is the interval between its event and the
@@ -170,6 +181,9 @@ fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* 
 
 /* Local linear covariance surface, Eq. (2.4), at every pair of bin centres,
  * for nh bandwidths h (host, nh x d), and what the eigen step needs from it.
+ * Built for d <= 2 and m[k] <= 64 (the P x P surface is materialised); d = 3
+ * grids return FPCA_E_UNSUPPORTED here and use the factored entry points
+ * (fpca_bin_cov_factor, fpca_smooth_cov_apply) instead.
  *  bins: from fpca_bin_cov; all folds are pooled for the fit.
  *  prec: FPCA_F64, FPCA_F32 or FPCA_F32C (see fpca_prec).
  *  mu_raw: for raw-mode bins, the fitted mean (Gamma_hat = b0 - mu mu);
@@ -272,9 +286,11 @@ fpca_status fpca_bw_features(fpca_ctx* ctx, const fpca_data* data, const fpca_gr
  * allocator (a framework's caching pool or a fixed arena), code running
  * where allocation is not allowed, or hosts that forbid libraries from
  * allocating behind their back.  It needs no fpca_ctx (creating one
- * allocates) and computes exactly what fpca_bin_mean computes for
- * FPCA_DENSE data, on the given stream (NULL = legacy default stream) of the
- * current device.
+ * allocates) and computes the mean bins of fpca_bin_mean for FPCA_DENSE data,
+ * on the given stream (NULL = legacy default stream) of the current device:
+ * the counts are bit-identical; w, v and v2 are the same sums added in another
+ * order (one FP64 chain per bin instead of float-float slices and an FP64
+ * tree), so they agree to about 1e-13 relative, not bit for bit.
  *
  *  y: n x P row-major, FP64 (y_prec FPCA_F64) or FP32 (FPCA_F32); mask: n x P
  *  uint8 or NULL; outputs cnt, w, v (and v2 unless NULL) of length P.  All
@@ -288,7 +304,10 @@ fpca_status fpca_bw_features(fpca_ctx* ctx, const fpca_data* data, const fpca_gr
  * GPU (other streams, other host threads) race and must be serialised by the
  * caller.  The first call on a device looks up the array's device address
  * with that device current (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Errors: FPCA_E_INVALID_ARG for bad
+ * before any stream capture.  The address is remembered with the unique id of
+ * the device's context and looked up again when that changes (after a
+ * cudaDeviceReset, the first call after it does the lookup again and should
+ * likewise come before any capture).  Errors: FPCA_E_INVALID_ARG for bad
  * arguments, FPCA_E_CUDA for a failed lookup or launch. */
 fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, const void* y, int y_prec,
                                  const uint8_t* mask, int32_t* cnt, double* w, double* v,
@@ -405,7 +424,8 @@ fpca_status fpca_mise(fpca_ctx* ctx, const fpca_grid* grid, const float* xhat, c
  *
  * Scope: d = 3, every subject observed at every grid node (dense layout,
  * mask NULL), 2 <= M_k <= 64, residual mode, the same bandwidth vector h for
- * s and t with 1..8 kernel taps per axis (taps = #{k >= 1 : k/(h_k M_k) < 1}).
+ * s and t with 1..4 kernel taps per axis (taps = #{k >= 1 : k/(h_k M_k) < 1};
+ * the shared-memory staging of the near-diagonal tile pairs holds at most 4).
  * Other inputs return FPCA_E_UNSUPPORTED.
  *
  * Arithmetic: residuals R~ = (Y - mu_hat)/sqrt(n) in BF16 for the tensor-core

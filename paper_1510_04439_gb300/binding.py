@@ -31,7 +31,7 @@ SYMBOLS = (
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
-    "fpca_mise", "fpca_bw_trust_region",
+    "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait",
 )
 
 
@@ -110,6 +110,7 @@ def load(path=LIB_PATH):
     lib.fpca_sync.argtypes = [vp]
     lib.fpca_launch_count.argtypes = [vp]
     lib.fpca_launch_count.restype = ctypes.c_uint64
+    lib.fpca_check_wait.argtypes = [vp, i32]
     lib.fpca_bin_mean.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp, vp]
     lib.fpca_smooth_mean.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp]
     lib.fpca_bin_cov.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32, i32, vp,
@@ -205,6 +206,11 @@ class Context:
 
     def sync(self):
         self._check(self.lib.fpca_sync(self.h))
+
+    def check_wait(self, arrive):
+        """Queue the bounded-wait self-check (fpca_check_wait); its outcome is
+        reported by the next sync()."""
+        self._check(self.lib.fpca_check_wait(self.h, int(bool(arrive))))
 
     @property
     def launches(self):

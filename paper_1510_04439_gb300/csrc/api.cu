@@ -5,6 +5,7 @@
 #include <new>
 
 #include "fpca_internal.cuh"
+#include "ptx.cuh"
 
 fpca_status fpca_fail(fpca_ctx* ctx, fpca_status st, const char* fmt, ...) {
   if (ctx) {
@@ -218,6 +219,31 @@ fpca_status fpca_set_stream(fpca_ctx* ctx, void* cuda_stream) {
 const char* fpca_last_error(const fpca_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 uint64_t fpca_launch_count(const fpca_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// Self-check of the failure detection: one thread waits on a shared-memory
+// mbarrier that expects one arrival, through the same bounded wait the tensor-
+// core and bulk-copy kernels use; with `arrive` set a thread arrives first.
+__global__ void k_wait_probe(int arrive, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = ptx::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(b, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) ptx::mbar_arrive(b);
+    ptx::mbar_wait(b, 0, err);  // gives up after FPCA_WAIT_LIMIT_NS, records DERR_TIMEOUT
+  }
+}
+
+fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
+  k_wait_probe<<<1, 32, 0, ctx->stream>>>(arrive ? 1 : 0, ctx->d_err);
+  FPCA_LAUNCHED(ctx, "wait_probe");
+  return FPCA_OK;
+}
 
 fpca_status fpca_profile_enable(fpca_ctx* ctx, int enable) {
   if (!ctx) return FPCA_E_INVALID_ARG;

@@ -7,6 +7,8 @@
 // its back.  fpca_bin_mean_static gives them the mean binning of dense data
 // with no allocation at all: the per-subject scratch (N_i) lives in a
 // file-scope __device__ array of fixed size.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "fpca_internal.cuh"
@@ -19,8 +21,41 @@ constexpr int kMaxSubjects = 1 << 20;
 static __device__ __align__(256) int32_t g_subject_scratch[kMaxSubjects];
 
 constexpr int kMaxDevices = 64;
+// The device address of the array, looked up per device and remembered with
+// the unique id of the context it was looked up in: after a cudaDeviceReset
+// the device gets a new primary context (and the module, with the array, may
+// load elsewhere), so a changed id triggers a new lookup.
 int32_t* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx_id[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return reinterpret_cast<Fn>(p);
+}
+
+// Unique id of the calling thread's current context (0 if there is none or the
+// driver does not report one).
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+  unsigned long long id = 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 __device__ __forceinline__ double load_y(const void* y, int prec, size_t idx) {
   return prec == FPCA_F64 ? static_cast<const double*>(y)[idx]
@@ -89,16 +124,20 @@ extern "C" fpca_status fpca_bin_mean_static(void* cuda_stream, int n, int P, con
   if (dev < 0 || dev >= kMaxDevices) return FPCA_E_UNSUPPORTED;
   int32_t* scratch = nullptr;
   {
-    // set-up, once per device with that device current: the device address
-    // of the static array (its name in host code is only a host-side stand-in)
+    // set-up, once per device (and again if the device's context was replaced)
+    // with that device current: the device address of the static array (its
+    // name in host code is only a host-side stand-in)
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_scratch_addr[dev] || id == 0 || id != g_scratch_ctx_id[dev]) {
       void* addr = nullptr;
       if (cudaGetSymbolAddress(&addr, g_subject_scratch) != cudaSuccess) {
         cudaGetLastError();
         return FPCA_E_CUDA;
       }
       g_scratch_addr[dev] = static_cast<int32_t*>(addr);
+      // the lookup makes the primary context current if nothing was yet
+      g_scratch_ctx_id[dev] = current_ctx_id();
     }
     scratch = g_scratch_addr[dev];
   }

@@ -35,7 +35,7 @@ constexpr int TROWS = 4;          // K, K u, K u^2, box (1 inside the support)
 // Thresholds of the per-point status rules.
 constexpr double PIVOT_RTOL_F64 = 1e-9;  // FP64 moments: fallback at or below
 constexpr double PIVOT_RTOL_F32 = 1e-5;  // FP32 moments: fallback at or below
-constexpr double ESCALATE_F32 = 1e-2;    // FP32 solve redone in FP64 below this
+constexpr double ESCALATE_F32 = 1e-2;    // FP32 solve redone in float-float below this
 
 struct TapParams {
   int d;

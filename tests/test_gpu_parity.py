@@ -8,8 +8,11 @@ Tolerances (stated per result):
                                    Gamma_hat rel-L2 <= 5e-3
   random projection (FP32 Sigma)   lambda rel <= 1e-4, subspace angle <= 1e-3 rad
   dense eigensolver (FP64)         lambda rel <= 1e-10, subspace angle <= 1e-8 rad
-Points whose oracle pivot ratio lies in the band where FP32 moments cannot
-decide the status ([1e-10, 1e-3]) are compared for validity only.
+Statuses: FP64 paths must equal the oracle's everywhere.  An FP32 path may
+differ only at points whose oracle pivot ratio lies in the band where FP32
+moments cannot decide the status ([1e-10, 1e-3], BAND); every mismatch is
+checked against that band (assert_status_band), and values are compared where
+both sides fitted the full local linear model.
 """
 import math
 
@@ -62,6 +65,42 @@ def oracle_ratio(p, q, m, h, C, W, V):
     except np.linalg.LinAlgError:
         return -1.0
     return float(np.min(np.diag(L) ** 2 / np.diag(A)))
+
+
+# Smallest Cholesky pivot ratios (pivot / diagonal entry, natural order) that
+# FP32 moments cannot place on the right side of the FP64 fallback threshold
+# (1e-9): the FP32 path decides its status from moments rounded to ~1e-7 and
+# falls back at 1e-5.
+BAND = (1e-10, 1e-3)
+
+
+def assert_status_band(gst, rst, pairs, m, h, C, W, V, max_mismatch=None):
+    """Every output pair whose status differs from the oracle's must lie in BAND.
+
+    ``pairs`` maps the flat positions of gst/rst to (s, t) node pairs.  The
+    FP32 sweep fits t >= s and copies (t, s) from (s, t), whose system is the
+    same one with its unknowns permuted, so a mismatch is accepted when the
+    oracle's pivot ratio of either order lies in the band.  Returns the
+    number of mismatches."""
+    gst = np.asarray(gst).ravel()
+    rst = np.asarray(rst).ravel()
+    bad = np.nonzero(gst != rst)[0]
+    if max_mismatch is not None:
+        assert bad.size <= max_mismatch, f"{bad.size} status mismatches"
+    for e in bad:
+        p, q = pairs[e]
+        assert rst[e] != sm.STATUS_EMPTY and gst[e] != sm.STATUS_EMPTY, (p, q, gst[e], rst[e])
+        r1 = oracle_ratio(p, q, m, h, C, W, V)
+        r2 = oracle_ratio(q, p, m, h, C, W, V)
+        assert any(BAND[0] <= r <= BAND[1] for r in (r1, r2)), \
+            f"status mismatch at ({p}, {q}) outside the pivot band: ratios {r1:.3g}, {r2:.3g}"
+    return int(bad.size)
+
+
+def grid_pairs(P):
+    """(P*P, 2) node pairs of a P x P surface in row-major order."""
+    s, t = np.divmod(np.arange(P * P), P)
+    return np.stack([s, t], 1)
 
 
 # ----------------------------------------------------------------------------
@@ -226,7 +265,10 @@ def test_smooth_cov_d1(ctx, B, prec):
     ctx.sync()
     rG, rst = sm.smooth_cov_grid(D.m, h, C, W, V)
     ok = (rst == sm.STATUS_OK) & (host(st) == sm.STATUS_OK)
-    assert np.mean(host(st) == rst) > 0.999
+    if prec == "f64":
+        assert np.array_equal(host(st), rst)
+    else:
+        assert_status_band(host(st), rst, grid_pairs(P), D.m, h, C, W, V, max_mismatch=P * P // 1000)
     tol = 1e-6 if prec == "f64" else 1e-5
     assert rel_l2(host(G).astype(np.float64)[ok], rG[ok]) <= tol
 
@@ -440,7 +482,7 @@ def test_pipeline_full_size_disk_64x64_n1000(ctx, B):
     ref, rst = sm.smooth_cov_points(pairs, D.m, h, C, W, V)
     g = host(bufs.gamma).astype(np.float64)[pairs[:, 0], pairs[:, 1]]
     gst = host(bufs.status)[pairs[:, 0], pairs[:, 1]]
-    assert np.array_equal(gst, rst)
+    assert_status_band(gst, rst, pairs, D.m, h, C, W, V, max_mismatch=3)
     ok = rst == sm.STATUS_OK
     assert rel_l2(g[ok], ref[ok]) <= 5e-3
     # eigen properties of the returned pairs on the GPU's own surface
@@ -512,7 +554,7 @@ def test_smooth_cov_f32_d2_ragged_tiles(ctx, B, prec, m, h):
     ctx.sync()
     rG, rst = sm.smooth_cov_grid(D.m, h, C, W, V)
     gst = host(st)
-    assert np.mean(gst == rst) > 0.999
+    assert_status_band(gst, rst, grid_pairs(P), D.m, h, C, W, V, max_mismatch=P * P // 1000)
     ok = (rst == sm.STATUS_OK) & (gst == sm.STATUS_OK)
     assert rel_l2(host(G).astype(np.float64)[ok], rG[ok]) <= 1e-5
     fb = (rst == sm.STATUS_FALLBACK) & (gst == sm.STATUS_FALLBACK)

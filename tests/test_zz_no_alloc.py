@@ -20,16 +20,22 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def _bins_allocating(ctx, y, mask, m):
+# The two entry points add the same terms in different orders (one FP64 chain
+# per bin here, float-float subject slices and an FP64 tree in fpca_bin_mean):
+# counts are bit-identical, the sums agree to about 1e-13 relative.
+RTOL = 1e-13
+
+
+def _bins_allocating(ctx, y, mask, m, with_v2=True):
     P = y.shape[1]
     cnt = torch.empty(P, dtype=torch.int32, device=DEV)
     w, v, v2 = (torch.empty(P, dtype=torch.float64, device=DEV) for _ in range(3))
-    ctx.bin_mean(ctx.dense(y, mask), m, cnt, w, v, v2)
+    ctx.bin_mean(ctx.dense(y, mask), m, cnt, w, v, v2 if with_v2 else None)
     ctx.sync()
-    return cnt, w, v, v2
+    return (cnt, w, v, v2) if with_v2 else (cnt, w, v)
 
 
-def _bins_static(lib, B, y, mask):
+def _bins_static(lib, B, y, mask, with_v2=True):
     n, P = y.shape
     cnt = torch.full((P,), -7, dtype=torch.int32, device=DEV)
     w, v, v2 = (torch.full((P,), np.nan, dtype=torch.float64, device=DEV) for _ in range(3))
@@ -39,10 +45,20 @@ def _bins_static(lib, B, y, mask):
                                   B.F64 if y.dtype == torch.float64 else B.F32,
                                   ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
                                   ctypes.c_void_p(cnt.data_ptr()), ctypes.c_void_p(w.data_ptr()),
-                                  ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(v2.data_ptr()))
+                                  ctypes.c_void_p(v.data_ptr()),
+                                  ctypes.c_void_p(v2.data_ptr()) if with_v2 else None)
     assert st == B.OK
     stream.synchronize()
+    if not with_v2:
+        assert torch.all(torch.isnan(v2)), "v2 = NULL must leave the buffer untouched"
+        return cnt, w, v
     return cnt, w, v, v2
+
+
+def _assert_same(got, ref):
+    assert torch.equal(got[0], ref[0])
+    for a, b in zip(got[1:], ref[1:]):
+        assert torch.allclose(a, b, rtol=RTOL, atol=RTOL)
 
 
 def test_static_mean_bins_match_allocating_entry_point_twice():
@@ -57,9 +73,30 @@ def test_static_mean_bins_match_allocating_entry_point_twice():
         mask = torch.from_numpy(D.mask).to(DEV)
         ref = _bins_allocating(ctx, y, mask, D.m)
         got = _bins_static(lib, B, y, mask)
-        assert torch.equal(got[0], ref[0])
-        for a, b in zip(got[1:], ref[1:]):
-            assert torch.allclose(a, b, rtol=1e-13, atol=1e-13)
+        _assert_same(got, ref)
+
+
+def test_static_mean_bins_null_mask_null_v2_and_empty_subject():
+    """mask = NULL (every node observed), v2 = NULL, and a subject whose mask row is
+    all zero (N_i = 0, skipped by both entry points), each against fpca_bin_mean."""
+    from paper_1510_04439_gb300 import binding as B
+    lib = B.load()
+    ctx = B.Context(0)
+    D = fs.make_dense(2, (12, 20), 50, [2.0, 1.0], seed=8)
+    y = torch.from_numpy(D.y).to(DEV)
+    _assert_same(_bins_static(lib, B, y, None), _bins_allocating(ctx, y, None, D.m))
+    _assert_same(_bins_static(lib, B, y, None, with_v2=False),
+                 _bins_allocating(ctx, y, None, D.m, with_v2=False))
+    D2 = fs.make_dense(2, (16, 16), 40, [2.0, 1.0], seed=9, dropout=0.2)
+    mask = D2.mask.copy()
+    mask[3, :] = 0
+    mask[17, :] = 0
+    y2 = torch.from_numpy(D2.y).to(torch.float32).to(DEV)
+    m2 = torch.from_numpy(mask).to(DEV)
+    got = _bins_static(lib, B, y2, m2)
+    _assert_same(got, _bins_allocating(ctx, y2, m2, D2.m))
+    _assert_same(_bins_static(lib, B, y2, m2, with_v2=False),
+                 _bins_allocating(ctx, y2, m2, D2.m, with_v2=False))
 
 
 def test_static_mean_bins_reject_oversize_n():
