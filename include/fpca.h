@@ -119,6 +119,18 @@ fpca_status fpca_sync(fpca_ctx* ctx);
 /* Number of kernels this context has launched so far (host counter). */
 uint64_t fpca_launch_count(const fpca_ctx* ctx);
 
+/* Choice of the t-side moment sweep of the FP32 d = 2 covariance smoother
+ * (fpca_smooth_cov_project with FPCA_F32 / FPCA_F32C):
+ *  0  automatic (default): the candidates built for the grid and windows are
+ *     timed once per (grid, windows, precision) on the context's stream and the
+ *     fastest is remembered in the context;
+ *  1  the scalar sweep (every t-plane layout and window);
+ *  2  the packed-pair sweep where it is built (t-planes 32 or 64 wide, the
+ *     same window on both t axes), else the scalar one.
+ * All choices compute the same sums in the same order per output up to the
+ * grouping of the FP32 partial sums, within the stated FP32 tolerance. */
+fpca_status fpca_set_sweep_kernel(fpca_ctx* ctx, int kernel);
+
 /* Self-check of the device-side failure detection.  Launches one thread
  * that waits on an on-chip barrier (an mbarrier expecting one arrival) with
  * the bounded wait every waiting kernel of this library uses.  arrive != 0:
@@ -247,6 +259,22 @@ fpca_status fpca_rproj_eig(fpca_ctx* ctx, const fpca_grid* grid, const void* gam
  * accumulation.  Parameter vector (device float, fpca_bw_param_count()
  * entries): for each layer W (fan_in x fan_out, row-major) then b. */
 int64_t fpca_bw_param_count(void);
+/* Initial parameters (device float, fpca_bw_param_count() entries): every
+ * weight of a layer with fan_in inputs drawn from N(0, 2 / fan_in) (He
+ * initialisation), biases zero.  The draws come from a counter-based generator
+ * (splitmix64 of (seed, parameter index), Box-Muller), so the same seed gives
+ * the same parameters on any device and any stream. */
+fpca_status fpca_bw_mlp_init(fpca_ctx* ctx, uint64_t seed, float* params);
+/* Save (save != 0) or load the trained network to or from the file `path`
+ * (host string): the parameter vector and, when the pointers are not NULL,
+ * the 32 feature means and 32 feature scales used to standardise the input
+ * (device float arrays; on save a NULL pointer writes zeros, on load a NULL
+ * pointer skips them).  The file holds an 8-byte tag, the parameter count and
+ * the values in the byte order of the host.  Loading a file of another
+ * layout returns FPCA_E_INVALID_ARG and leaves the arrays unchanged.
+ * Synchronises the context's stream. */
+fpca_status fpca_bw_mlp_io(fpca_ctx* ctx, float* params, float* feat_mu, float* feat_sd,
+                           const char* path, int save);
 /* out (B x 6) = network(feat (B x 32)); all device float. */
 fpca_status fpca_bw_predict(fpca_ctx* ctx, const float* params, const float* feat, int B,
                             float* out);

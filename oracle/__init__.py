@@ -14,9 +14,11 @@ Modules
             projection (Section 3.4)
   block     the covariance smoother at chosen output pairs (rows, tiles) from
             the data, for grids whose P x P bins are too large to hold
+  grid      the covariance smoother on whole grids of up to 64 x 64 nodes
+            (the moments as band-matrix products, a stacked solve)
   variance  the noise variance of Eq. (2.5)-(2.6)
   scores    PACE scores (Eq. 2.7), scores by integration, reconstruction
   cv        cross-validation of the covariance bandwidth (Section 3.3)
   mlp       the bandwidth-proposal network (forward, manual backward, AdamW)
 """
-from . import smoother, eigen, cv, block, variance, scores  # noqa: F401
+from . import smoother, eigen, cv, block, grid, variance, scores  # noqa: F401

@@ -167,16 +167,6 @@ def make_table(ctx, torch, seeds, log_every=0):
     return (np.stack(feats), np.stack(targets), np.stack(masks), np.array(best))
 
 
-def init_params(seed):
-    """He-style initial weights drawn on the host, zero biases."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for fi, fo in [(32, 256), (256, 256), (256, 256), (256, 6)]:
-        parts.append(rng.standard_normal(fi * fo) * math.sqrt(2.0 / fi))
-        parts.append(np.zeros(fo))
-    return np.concatenate(parts).astype(np.float32)
-
-
 def standardize(X, mu=None, sd=None):
     if mu is None:
         mu = X.mean(0)
@@ -188,7 +178,8 @@ def standardize(X, mu=None, sd=None):
 def train(ctx, torch, X, Y, M, epochs=200, batch=256, lr=1e-3, wd=1e-4, seed=0):
     """AdamW on (X, Y, M) with the GPU kernels; returns params and loss history."""
     dev = ctx.device
-    th = torch.from_numpy(init_params(seed)).to(dev)
+    th = torch.empty(ctx.bw_param_count(), dtype=torch.float32, device=dev)
+    ctx.bw_mlp_init(th, seed)
     m = torch.zeros_like(th)
     v = torch.zeros_like(th)
     loss = torch.empty(1, dtype=torch.float32, device=dev)

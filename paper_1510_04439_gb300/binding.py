@@ -31,7 +31,8 @@ SYMBOLS = (
     "fpca_bw_train_step", "fpca_bw_features", "fpca_cov_factor_bytes", "fpca_bin_cov_factor",
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
-    "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait",
+    "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait", "fpca_set_sweep_kernel",
+    "fpca_bw_mlp_init", "fpca_bw_mlp_io",
 )
 
 
@@ -111,6 +112,9 @@ def load(path=LIB_PATH):
     lib.fpca_launch_count.argtypes = [vp]
     lib.fpca_launch_count.restype = ctypes.c_uint64
     lib.fpca_check_wait.argtypes = [vp, i32]
+    lib.fpca_set_sweep_kernel.argtypes = [vp, i32]
+    lib.fpca_bw_mlp_init.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.fpca_bw_mlp_io.argtypes = [vp, vp, vp, vp, ctypes.c_char_p, i32]
     lib.fpca_bin_mean.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp, vp]
     lib.fpca_smooth_mean.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp]
     lib.fpca_bin_cov.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32, i32, vp,
@@ -206,6 +210,19 @@ class Context:
 
     def sync(self):
         self._check(self.lib.fpca_sync(self.h))
+
+    def set_sweep_kernel(self, kernel):
+        """0 automatic (timed once per grid and windows), 1 scalar, 2 packed pairs."""
+        self._check(self.lib.fpca_set_sweep_kernel(self.h, int(kernel)))
+
+    def bw_mlp_init(self, params, seed):
+        """He-normal initial network parameters from a counter-based generator."""
+        self._check(self.lib.fpca_bw_mlp_init(self.h, int(seed), _ptr(params)))
+
+    def bw_mlp_io(self, params, path, save, feat_mu=None, feat_sd=None):
+        """Save (save=True) or load the network and its feature standardisation."""
+        self._check(self.lib.fpca_bw_mlp_io(self.h, _ptr(params), _ptr(feat_mu), _ptr(feat_sd),
+                                            str(path).encode(), int(bool(save))))
 
     def check_wait(self, arrive):
         """Queue the bounded-wait self-check (fpca_check_wait); its outcome is

@@ -51,7 +51,7 @@ def build(verbose=False, extra=()):
     srcs = sources()
     objs = []
     errors = []
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         for src, obj, rc, out in ex.map(lambda s: _compile(s, list(extra)), srcs):
             if verbose and out.strip():
                 print(out, file=sys.stderr)

@@ -237,6 +237,14 @@ __global__ void k_wait_probe(int arrive, int* err) {
   }
 }
 
+fpca_status fpca_set_sweep_kernel(fpca_ctx* ctx, int kernel) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  if (kernel < 0 || kernel > 2)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "sweep kernel must be 0 (automatic), 1 or 2");
+  ctx->tside_kernel = kernel;
+  return FPCA_OK;
+}
+
 fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive) {
   if (!ctx) return FPCA_E_INVALID_ARG;
   fpca_prof_mark(ctx);

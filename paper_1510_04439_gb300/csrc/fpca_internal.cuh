@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <array>
 #include <cstdint>
 #include <cstddef>
 #include <map>
@@ -40,6 +41,12 @@ struct fpca_ctx {
   size_t f3_lists_bytes = 0;
   int f3_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int f3_ncta = 0, f3_nitems = 0, f3_npairs = 0;
+  // t-side sweep kernel of the FP32 d = 2 covariance smoother: 0 = automatic,
+  // 1 = the scalar sweep (k_hsolve2), 2 = the packed-pair sweep where built;
+  // the automatic choice per (M1, M2, T1, T2, compensated, half) once timed:
+  // 1 or 2 as above
+  int tside_kernel = 0;
+  std::map<std::array<int, 6>, int> tside_choice;
 };
 
 // Device error codes written by kernels into ctx->d_err.

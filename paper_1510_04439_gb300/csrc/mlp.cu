@@ -11,6 +11,10 @@
 // Parameter vector: for each layer, W (fan_in x fan_out, row-major) then b.
 #include <cuda_fp16.h>
 
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
 #include "fpca_internal.cuh"
 
 namespace {
@@ -198,11 +202,105 @@ fpca_status mlp_forward(fpca_ctx* ctx, const float* th, const float* X, int Bn, 
   return FPCA_OK;
 }
 
+// splitmix64 (Steele, Lea and Flood 2014): the finaliser applied to a counter.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// He-normal initial weights N(0, 2 / fan_in) and zero biases.  Parameter e draws
+// its normal value by the Box-Muller transform of two uniforms in (0, 1] taken
+// from the counter (seed, e): the result depends only on the seed.
+__global__ void k_mlp_init(uint64_t seed, float* __restrict__ params) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= kParamCount) return;
+  int l = 0;
+  while (l + 1 < NLAYER && e >= layer_off(l + 1)) ++l;
+  const long long r = e - layer_off(l);
+  const int fi = layer_in(l), fo = layer_out(l);
+  if (r >= (long long)fi * fo) {
+    params[e] = 0.f;  // bias
+    return;
+  }
+  const uint64_t a = splitmix64(seed * 0x2545F4914F6CDD1Dull + 2ull * (uint64_t)e);
+  const uint64_t b = splitmix64(seed * 0x2545F4914F6CDD1Dull + 2ull * (uint64_t)e + 1ull);
+  const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+  const double u2 = (double)(b >> 11) * 0x1.0p-53;          // [0, 1)
+  const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  params[e] = (float)(z * sqrt(2.0 / (double)fi));
+}
+
+// File layout of fpca_bw_mlp_io: magic, parameter count, the parameters, the
+// 32 feature means and the 32 feature scales, all little-endian.
+constexpr char kMlpMagic[8] = {'F', 'P', 'C', 'A', 'B', 'W', '0', '1'};
+
 }  // namespace
 
 extern "C" {
 
 int64_t fpca_bw_param_count(void) { return kParamCount; }
+
+fpca_status fpca_bw_mlp_init(fpca_ctx* ctx, uint64_t seed, float* params) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
+  if (!params) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "params is NULL");
+  k_mlp_init<<<(int)((kParamCount + 255) / 256), 256, 0, ctx->stream>>>(seed, params);
+  FPCA_LAUNCHED(ctx, "mlp_init");
+  return FPCA_OK;
+}
+
+fpca_status fpca_bw_mlp_io(fpca_ctx* ctx, float* params, float* feat_mu, float* feat_sd,
+                           const char* path, int save) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  if (!params || !path) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "params and path are required");
+  std::vector<float> buf((size_t)kParamCount + 64, 0.f);
+  const size_t nbytes = sizeof(float) * buf.size();
+  if (save) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return fpca_check_launch(ctx, "mlp_io: stream");
+    cudaError_t e = cudaMemcpy(buf.data(), params, sizeof(float) * kParamCount,
+                               cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && feat_mu)
+      e = cudaMemcpy(buf.data() + kParamCount, feat_mu, 32 * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && feat_sd)
+      e = cudaMemcpy(buf.data() + kParamCount + 32, feat_sd, 32 * sizeof(float),
+                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "mlp_io: %s", cudaGetErrorString(e));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "mlp_io: cannot write %s", path);
+    const int64_t count = kParamCount;
+    const bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(&count, 8, 1, f) == 1 &&
+                    std::fwrite(buf.data(), 1, nbytes, f) == nbytes;
+    if (std::fclose(f) != 0 || !ok)
+      return fpca_fail(ctx, FPCA_E_INVALID_ARG, "mlp_io: short write to %s", path);
+    return FPCA_OK;
+  }
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "mlp_io: cannot read %s", path);
+  char magic[8];
+  int64_t count = 0;
+  const bool head = std::fread(magic, 1, 8, f) == 8 && std::fread(&count, 8, 1, f) == 1;
+  const bool body = head && std::memcmp(magic, kMlpMagic, 8) == 0 && count == kParamCount &&
+                    std::fread(buf.data(), 1, nbytes, f) == nbytes;
+  std::fclose(f);
+  if (!body)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG,
+                     "mlp_io: %s is not a saved network of %lld parameters", path,
+                     (long long)kParamCount);
+  cudaError_t e = cudaMemcpyAsync(params, buf.data(), sizeof(float) * kParamCount,
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && feat_mu)
+    e = cudaMemcpyAsync(feat_mu, buf.data() + kParamCount, 32 * sizeof(float),
+                        cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && feat_sd)
+    e = cudaMemcpyAsync(feat_sd, buf.data() + kParamCount + 32, 32 * sizeof(float),
+                        cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // buf is a host temporary
+  if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "mlp_io: %s", cudaGetErrorString(e));
+  return FPCA_OK;
+}
 
 fpca_status fpca_bw_predict(fpca_ctx* ctx, const float* params, const float* feat, int B,
                             float* out) {

@@ -20,22 +20,17 @@
 // A box-filter pass of the indicator [count > 0] runs alongside and gives
 // the number of non-empty bin pairs in each window.
 #include <algorithm>
+#include <array>
 #include <cmath>
 
 #include "fpca_internal.cuh"
 #include "ptx.cuh"
 #include "ff.cuh"
+#include "tside.cuh"
 
 namespace {
 
-constexpr int TMAX = 63;          // largest tap offset supported (m <= 64)
-constexpr int TW = 2 * TMAX + 1;  // table width
-constexpr int TROWS = 4;          // K, K u, K u^2, box (1 inside the support)
-
-// Thresholds of the per-point status rules.
-constexpr double PIVOT_RTOL_F64 = 1e-9;  // FP64 moments: fallback at or below
-constexpr double PIVOT_RTOL_F32 = 1e-5;  // FP32 moments: fallback at or below
-constexpr double ESCALATE_F32 = 1e-2;    // FP32 solve redone in float-float below this
+using namespace fpca_sweep;
 
 struct TapParams {
   int d;
@@ -66,173 +61,6 @@ int host_taps(double h, int M) {
   for (int j = M - 1; j >= 1; --j)
     if ((double)j / hm < 1.0) return j;
   return 0;
-}
-
-// ---------------------------------------------------------------------------
-// natural-order symmetric elimination: beta_0 and the smallest pivot ratio
-// (Schur-complement diagonal / original diagonal), i.e. the Cholesky pivots
-// ---------------------------------------------------------------------------
-template <int D, typename T>
-__device__ __forceinline__ T elim_solve(T (&A)[D][D], T (&r)[D], double& minratio) {
-  T diag[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) diag[i] = A[i][i];
-  minratio = 1e300;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const T piv = A[k][k];
-    const double ratio = diag[k] > T(0) ? (double)piv / (double)diag[k] : -1.0;
-    minratio = fmin(minratio, ratio);
-    if (!(piv > T(0))) {
-      minratio = -1.0;
-      return T(0);
-    }
-    const T inv = T(1) / piv;
-#pragma unroll
-    for (int i = k + 1; i < D; ++i) {
-      const T l = A[k][i] * inv;
-#pragma unroll
-      for (int j = i; j < D; ++j) A[i][j] -= l * A[k][j];
-      r[i] -= l * r[k];
-    }
-  }
-  T x[D];
-#pragma unroll
-  for (int k = D - 1; k >= 0; --k) {
-    T s = r[k];
-#pragma unroll
-    for (int j = k + 1; j < D; ++j) s -= A[k][j] * x[j];
-    x[k] = s / A[k][k];
-  }
-  return x[0];
-}
-
-// Status and value of one local fit from its normal equations (in T) and the
-// number of non-empty bins in the window.
-template <int D, typename T>
-__device__ __forceinline__ double fit_point(T (&A)[D][D], T (&r)[D], double nonempty,
-                                            uint8_t& st) {
-  if (!(A[0][0] > T(0))) {
-    st = FPCA_PT_EMPTY;
-    return __longlong_as_double(0x7ff8000000000000ll);
-  }
-  const double lc = (double)r[0] / (double)A[0][0];
-  if (nonempty < (double)D) {
-    st = FPCA_PT_FALLBACK;
-    return lc;
-  }
-  if constexpr (sizeof(T) == 8) {
-    double ratio;
-    const double b = elim_solve<D, T>(A, r, ratio);
-    if (ratio <= PIVOT_RTOL_F64) {
-      st = FPCA_PT_FALLBACK;
-      return lc;
-    }
-    st = FPCA_PT_OK;
-    return b;
-  } else {
-    T Ac[D][D], rc[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      rc[i] = r[i];
-#pragma unroll
-      for (int j = 0; j < D; ++j) Ac[i][j] = A[i][j];
-    }
-    double ratio;
-    const T b = elim_solve<D, T>(A, r, ratio);
-    if (ratio >= ESCALATE_F32) {
-      st = FPCA_PT_OK;
-      return (double)b;
-    }
-    double Ad[D][D], rd[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      rd[i] = (double)rc[i];
-#pragma unroll
-      for (int j = 0; j < D; ++j) Ad[i][j] = (double)Ac[i][j];
-    }
-    const double bd = elim_solve<D, double>(Ad, rd, ratio);
-    if (ratio <= PIVOT_RTOL_F32) {
-      st = FPCA_PT_FALLBACK;
-      return lc;
-    }
-    st = FPCA_PT_OK;
-    return bd;
-  }
-}
-
-// FP32 fit without FP64 arithmetic on the common path: pivot tests by
-// multiplication (pivot < thr * diagonal) and FP32 divisions; the FP64
-// elimination runs only for the rare escalated systems.
-// Status code returned when the system must be re-solved at higher precision.
-constexpr uint8_t PT_ESCALATE = 255;
-
-template <int D, bool INLINE_FP64 = true>
-__device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], float nonempty,
-                                               uint8_t& st) {
-  if (!(A[0][0] > 0.f)) {
-    st = FPCA_PT_EMPTY;
-    return __int_as_float(0x7fc00000);
-  }
-  if (nonempty < (float)D) {
-    st = FPCA_PT_FALLBACK;
-    return r[0] / A[0][0];
-  }
-  float Ac[D][D], rc[D], diag[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    rc[i] = r[i];
-    diag[i] = A[i][i];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Ac[i][j] = A[i][j];
-  }
-  bool escalate = false;
-  float invp[D];  // 1 / pivot, reused by the back substitution
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float piv = A[k][k];
-    if (!(piv >= (float)ESCALATE_F32 * diag[k])) escalate = true;
-    const float inv = piv > 0.f ? 1.f / piv : 0.f;
-    invp[k] = inv;
-#pragma unroll
-    for (int i = k + 1; i < D; ++i) {
-      const float l = A[k][i] * inv;
-#pragma unroll
-      for (int j = i; j < D; ++j) A[i][j] = fmaf(-l, A[k][j], A[i][j]);
-      r[i] = fmaf(-l, r[k], r[i]);
-    }
-  }
-  if (!escalate) {
-    float x[D];
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-      float sacc = r[k];
-#pragma unroll
-      for (int j = k + 1; j < D; ++j) sacc = fmaf(-A[k][j], x[j], sacc);
-      x[k] = sacc * invp[k];
-    }
-    st = FPCA_PT_OK;
-    return x[0];
-  }
-  if constexpr (!INLINE_FP64) {
-    st = PT_ESCALATE;
-    return 0.f;
-  }
-  double Ad[D][D], rd[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    rd[i] = (double)rc[i];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Ad[i][j] = (double)Ac[i][j];
-  }
-  double ratio;
-  const double bd = elim_solve<D, double>(Ad, rd, ratio);
-  if (ratio <= PIVOT_RTOL_F32) {
-    st = FPCA_PT_FALLBACK;
-    return rc[0] / Ac[0][0];
-  }
-  st = FPCA_PT_OK;
-  return (float)bd;
 }
 
 // ---------------------------------------------------------------------------
@@ -349,85 +177,6 @@ __global__ void k_sigma2_mean(int P, const double* __restrict__ sig, const int32
 }
 
 // ---------------------------------------------------------------------------
-// covariance: moment bookkeeping
-// ---------------------------------------------------------------------------
-// Arrays after the s-side passes (d = 2): W with s-exponents (s1,s2) =
-// (0,0) (1,0) (2,0) (0,1) (1,1) (0,2); V with (0,0) (1,0) (0,1); the
-// indicator.  Moment slots: S over exponents (s1,s2,t1,t2) with |e| <= 2 in
-// the order 1, s1, s2, t1, t2, s1s1, s1s2, s1t1, s1t2, s2s2, s2t1, s2t2,
-// t1t1, t1t2, t2t2 (0..14); T with |e| <= 1: 1, s1, s2, t1, t2 (15..19);
-// the non-empty count (20).
-__host__ __device__ constexpr int narr(int d) { return d == 2 ? 10 : 6; }
-__host__ __device__ constexpr int nslot(int d) { return d == 2 ? 21 : 10; }
-// largest t-degree of array a
-__host__ __device__ constexpr int maxdeg(int d, int a) {
-  return d == 2 ? (a == 0 ? 2 : (a == 1 || a == 3 || a == 6) ? 1 : 0)
-                : (a == 0 ? 2 : (a == 1 || a == 3) ? 1 : 0);
-}
-__host__ __device__ constexpr bool is_indicator(int d, int a) { return a == narr(d) - 1; }
-// slot of t-exponents (a1 across t-plane rows, a2 along them) of array a
-__host__ __device__ constexpr int slot_of(int d, int a, int a1, int a2) {
-  if (d == 2) {
-    switch (a * 9 + a1 * 3 + a2) {
-      case 0 * 9 + 0: return 0;
-      case 0 * 9 + 1: return 4;
-      case 0 * 9 + 2: return 14;
-      case 0 * 9 + 3: return 3;
-      case 0 * 9 + 4: return 13;
-      case 0 * 9 + 6: return 12;
-      case 1 * 9 + 0: return 1;
-      case 1 * 9 + 1: return 8;
-      case 1 * 9 + 3: return 7;
-      case 2 * 9 + 0: return 5;
-      case 3 * 9 + 0: return 2;
-      case 3 * 9 + 1: return 11;
-      case 3 * 9 + 3: return 10;
-      case 4 * 9 + 0: return 6;
-      case 5 * 9 + 0: return 9;
-      case 6 * 9 + 0: return 15;
-      case 6 * 9 + 1: return 19;
-      case 6 * 9 + 3: return 18;
-      case 7 * 9 + 0: return 16;
-      case 8 * 9 + 0: return 17;
-      case 9 * 9 + 0: return 20;
-      default: return -1;
-    }
-  }
-  // d = 1: arrays W s^0, W s^1, W s^2, V s^0, V s^1, indicator; a1 is always 0
-  switch (a * 3 + a2) {
-    case 0 * 3 + 0: return 0;
-    case 0 * 3 + 1: return 2;
-    case 0 * 3 + 2: return 5;
-    case 1 * 3 + 0: return 1;
-    case 1 * 3 + 1: return 4;
-    case 2 * 3 + 0: return 3;
-    case 3 * 3 + 0: return 6;
-    case 3 * 3 + 1: return 8;
-    case 4 * 3 + 0: return 7;
-    case 5 * 3 + 0: return 9;
-    default: return -1;
-  }
-}
-// slot of normal-matrix entry (i, j), i <= j (unknown order [1, s.., t..])
-__host__ __device__ constexpr int aslot(int d, int i, int j) {
-  return d == 2 ? (i == 0 ? j : i == 1 ? 4 + j : i == 2 ? 7 + j : i == 3 ? 9 + j : 14)
-                : (i == 0 ? j : i == 1 ? 2 + j : 5);
-}
-__host__ __device__ constexpr int rslot(int d, int i) { return d == 2 ? 15 + i : 6 + i; }
-
-template <typename T, bool COMP>
-__device__ __forceinline__ void kadd(T& s, T& c, T w, T x) {
-  if constexpr (COMP) {
-    const T y = fma(w, x, -c);
-    const T t = s + y;
-    c = (t - s) - y;
-    s = t;
-  } else {
-    s = fma(w, x, s);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // vertical pass: 1-D sums along the row index of P x P arrays
 // ---------------------------------------------------------------------------
 // One input array per job; the value read is in[e] - sub[e] (sub may be
@@ -507,46 +256,6 @@ __global__ void __launch_bounds__(VCOLS)
     if (jb.npow > 1) static_cast<T*>(jb.out[1])[o] = s1;
     if (jb.npow > 2) static_cast<T*>(jb.out[2])[o] = s2;
   }
-}
-
-// ---------------------------------------------------------------------------
-// horizontal t-side sweep + per-point solve + epilogues
-// ---------------------------------------------------------------------------
-// Optional outputs besides Gamma_hat and status:
-//  y += G Omega   (row x_s of y gets sum_t G(x_s, t) Omega(t, :); EMPTY = 0)
-//  cv terms of one fold f: err = sum (Q_f - 2 G V_f + G^2 W_f) and w_in =
-//  sum W_f over non-EMPTY points, w_out = sum W_f over EMPTY points.
-template <typename T>
-struct Epilogue {
-  const float* omega;  // P x l or NULL
-  int l;
-  float* y;            // P x l (accumulated with atomics)
-  const T* wf;         // held-out fold's bins (P x P) or NULL
-  const T* vf;
-  const T* qf;
-  double* cvacc;       // [3]: err, w_in, w_out
-  // Escalated fits (FP32 pivots below the escalation threshold) are queued
-  // here and solved in float-float (about 48 bits) by a separate kernel:
-  // entry e holds the 21 moment slots of the point in esc_slots[e*21 ..] and
-  // its (xs, xt).
-  float* esc_slots;
-  int2* esc_idx;
-  unsigned* esc_count;
-  int esc_cap;
-};
-
-constexpr int MAXL = 64;
-
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
-  __syncthreads();
-  return s;
 }
 
 // Block: output row x_s (blockIdx.y), t-plane rows [a0, a0 + th) (blockIdx.x).
@@ -713,22 +422,6 @@ __global__ void __launch_bounds__(NT)
 // columns are zero in shared memory), so the inner loops carry no bounds
 // checks.  With COMP, every 4-tap partial is added to the running sum with
 // Kahan compensation.
-constexpr int HT = 8;     // t-plane rows per block
-constexpr int SEG = 8;    // columns per phase-2 item
-constexpr int NT2 = 256;  // threads per block
-constexpr int NMID = 15;  // mid arrays (d = 2)
-constexpr int NSL = 21;   // moment slots (d = 2)
-
-// mid array m -> (s-side array a, t1 power a1; 3 = box weights);
-// slot s -> (mid array, t2 power; 3 = box weights).  Items of one warp share
-// m (phase 1) or s (phase 2), so the constant-cache reads broadcast.
-__constant__ int8_t c_mid_array[NMID] = {0, 0, 0, 1, 1, 2, 3, 3, 4, 5, 6, 6, 7, 8, 9};
-__constant__ int8_t c_mid_pow[NMID] = {0, 1, 2, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 3};
-__constant__ int8_t c_slot_mid[NSL] = {0, 3, 6, 1, 0, 5, 8, 4, 3, 9, 7,
-                                       6, 2, 1, 0, 10, 12, 13, 11, 10, 14};
-__constant__ int8_t c_slot_pow[NSL] = {0, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0,
-                                       1, 0, 1, 2, 0, 0, 0, 0, 1, 3};
-
 struct Hs2Geom {
   int P, R, C;
   int Tr, Tc;        // tap half-widths (t1, t2)
@@ -1008,114 +701,7 @@ __global__ void __launch_bounds__(NT2, 2)
   }
   __syncthreads();
 
-  // phase 3: per-point solve, write, epilogue terms (FP32; escalated systems
-  // are queued for the float-float kernel; FP64 for the block sums of the CV terms)
-  float cv_err = 0.f, cv_in = 0.f, cv_out = 0.f;
-  constexpr int PPT3 = (HT * C + NT2 - 1) / NT2;
-  float gval[PPT3];
-  int xts[PPT3];
-#pragma unroll
-  for (int j = 0; j < PPT3; ++j) {
-    const int e = threadIdx.x + j * NT2;
-    gval[j] = 0.f;
-    xts[j] = -1;
-    if (e >= th * C) continue;
-    const int i = e / C, c = e % C;
-    if (g.half && (a0 + i) * C + c < xs) continue;  // taken from the mirror (t, s)
-    const float* sl = slots + (size_t)i * g.SC + c;
-    float A[5][5], rv[5];
-#pragma unroll
-    for (int i2 = 0; i2 < 5; ++i2) {
-      rv[i2] = sl[(size_t)rslot(2, i2) * HT * g.SC];
-#pragma unroll
-      for (int j2 = i2; j2 < 5; ++j2) {
-        A[i2][j2] = sl[(size_t)aslot(2, i2, j2) * HT * g.SC];
-        A[j2][i2] = A[i2][j2];
-      }
-    }
-    const float cnt = sl[(size_t)(NSL - 1) * HT * g.SC];
-    uint8_t st;
-    float gv = fit_point_f32<5, false>(A, rv, cnt + 0.25f, st);
-    const int xt = (a0 + i) * C + c;
-    if (st == PT_ESCALATE) {
-      const unsigned slot = ep.esc_count ? atomicAdd(ep.esc_count, 1u) : 0xffffffffu;
-      if (slot < (unsigned)ep.esc_cap) {
-        float* dst = ep.esc_slots + (size_t)slot * NSL;
-        for (int q = 0; q < NSL; ++q) dst[q] = sl[(size_t)q * HT * g.SC];
-        ep.esc_idx[slot] = make_int2(xs, xt);
-        continue;  // the escalation kernel writes this point and its epilogue terms
-      }
-      // queue full: solve here
-      float A2[5][5], r2[5];
-#pragma unroll
-      for (int i2 = 0; i2 < 5; ++i2) {
-        r2[i2] = sl[(size_t)rslot(2, i2) * HT * g.SC];
-#pragma unroll
-        for (int j2 = i2; j2 < 5; ++j2) {
-          A2[i2][j2] = sl[(size_t)aslot(2, i2, j2) * HT * g.SC];
-          A2[j2][i2] = A2[i2][j2];
-        }
-      }
-      gv = fit_point_f32<5, true>(A2, r2, cnt + 0.25f, st);
-    }
-    if (mu_raw && st != FPCA_PT_EMPTY) gv -= (float)(mu_raw[xs] * mu_raw[xt]);
-    const long long o = (long long)xs * P + xt;
-    if (gamma) gamma[o] = gv;
-    if (status) status[o] = st;
-    xts[j] = xt;
-    gval[j] = st == FPCA_PT_EMPTY ? 0.f : gv;
-    if (ep.cvacc) {
-      // in half mode (s, t) also stands for (t, s): the CV bins are symmetric
-      const float mul = (g.half && xt != xs) ? 2.f : 1.f;
-      const float wf = ep.wf[o];
-      if (st == FPCA_PT_EMPTY) {
-        cv_out += mul * wf;
-      } else {
-        cv_err += mul * (ep.qf[o] - 2.f * gv * ep.vf[o] + gv * gv * wf);
-        cv_in += mul * wf;
-      }
-    }
-  }
-  if (ep.cvacc) {
-    const double s0 = block_sum<NT2>((double)cv_err, red);
-    const double s1 = block_sum<NT2>((double)cv_in, red);
-    const double s2 = block_sum<NT2>((double)cv_out, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(ep.cvacc + 0, s0);
-      atomicAdd(ep.cvacc + 1, s1);
-      atomicAdd(ep.cvacc + 2, s2);
-    }
-  }
-  if (ep.y) {
-    // y[s, :] += sum over this block's t of Gamma_hat(s, t) Omega[t, :].  The block's
-    // t form one contiguous run of Omega's rows, so thread (group, column c) walks
-    // every ng-th of them with coalesced loads; the ng partials of a column are
-    // then added in shared memory (which reuses the mid rows: phase 3 reads only
-    // the slots).  EMPTY and escalated points carry 0.
-    (void)xts;
-    float* gsm = mid;             // [HT * C]
-    float* part = mid + HT * C;   // [NT2]
-#pragma unroll
-    for (int j = 0; j < PPT3; ++j) {
-      const int e = threadIdx.x + j * NT2;
-      if (e < HT * C) gsm[e] = gval[j];
-    }
-    __syncthreads();
-    const int l = ep.l, ng = NT2 / l;
-    const int c = threadIdx.x % l, grp = threadIdx.x / l;
-    float acc = 0.f;
-    if (grp < ng) {
-      const float* om = ep.omega + (long long)a0 * C * l + c;
-      for (int t = grp; t < th * C; t += ng) acc = fmaf(gsm[t], om[(long long)t * l], acc);
-    }
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < l) {
-      float tot = 0.f;
-      for (int gi = 0; gi < ng; ++gi) tot += part[gi * l + threadIdx.x];
-      atomicAdd(ep.y + (long long)xs * l + threadIdx.x, tot);
-    }
-  }
+  tside_phase3<C, NT2>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red, mid);
 }
 
 // NO outputs x NP powers along a line from one sliding window:
@@ -1615,9 +1201,13 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     // Will the t-side run in half mode (FP32 sweep kernel, symmetric bins, no fused
     // y)?  Then the s-side passes only produce the band it reads (SBand).
     bool half2 = false;
+    bool use_ts = false;
     if constexpr (sizeof(T) == 4) {
+      use_ts = tsweep_built(M2, Tax[0], Tax[1]) &&
+               ts_smem(ts_geometry(P, M1, M2, Tax[0], Tax[1])) <= ctx->smem_optin &&
+               ctx->tside_kernel != 1;  // 1: the scalar sweep only
       if ((M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) && symmetric && !ep.y)
-        half2 = hs2_smem(hs2_geometry(P, M1, M2, Tax[0], Tax[1])) <= ctx->smem_optin;
+        half2 = use_ts || hs2_smem(hs2_geometry(P, M1, M2, Tax[0], Tax[1])) <= ctx->smem_optin;
     }
     const SBand band1{half2 ? 1 : 0, M1, M2, Tax[0]};
     const SBand band2{half2 ? 2 : 0, M1, M2, Tax[0]};
@@ -1643,38 +1233,87 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     FPCA_LAUNCHED(ctx, "cov_vpass_s1");
     // t-side + solve
     if constexpr (sizeof(T) == 4) {
-      if (M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) {
-        Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
-        const size_t sm2 = hs2_smem(hg);
-        if (sm2 <= ctx->smem_optin) {
+      Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
+      const bool hs_ok = (M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64) &&
+                         hs2_smem(hg) <= ctx->smem_optin;
+      if (use_ts || hs_ok) {
+        TsGeom tg = ts_geometry(P, M1, M2, Tax[0], Tax[1]);
+        // symmetric bins: t >= s only, the rest mirrored (the fused y = Gamma_hat Omega
+        // needs every row); decided above with the s-side band
+        tg.half = half2 ? 1 : 0;
+        hg.half = half2 ? 1 : 0;
+        const float* va = reinterpret_cast<const float*>(varr);
+        float* gm = reinterpret_cast<float*>(gamma);
+        const Epilogue<float>& ef = *reinterpret_cast<const Epilogue<float>*>(&ep);
+        auto run_ts = [&](const Epilogue<float>& e) {
+          return tsweep_launch(M2, ctx, COMP, Tax[0], ts_smem(tg), va, tg, tabk(0), tabk(1),
+                               mu_raw, gm, status, e);
+        };
+        auto run_hs = [&](const Epilogue<float>& e) {
           const dim3 grid((M1 + HT - 1) / HT, P);
-          const float* va = reinterpret_cast<const float*>(varr);
-          float* gm = reinterpret_cast<float*>(gamma);
-          const Epilogue<float>& ef = *reinterpret_cast<const Epilogue<float>*>(&ep);
-          // symmetric bins: t >= s only, the rest mirrored (the fused y = Gamma_hat Omega
-          // needs every row); decided above with the s-side band
-          hg.half = half2 ? 1 : 0;
-          if (ef.esc_count) cudaMemsetAsync(ef.esc_count, 0, sizeof(unsigned), ctx->stream);
+          const size_t sm2 = hs2_smem(hg);
           switch (M2) {
-            case 8: launch_hsolve2<COMP, 8>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
-            case 16: launch_hsolve2<COMP, 16>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
-            case 32: launch_hsolve2<COMP, 32>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
-            default: launch_hsolve2<COMP, 64>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, ef); break;
+            case 8: launch_hsolve2<COMP, 8>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, e); break;
+            case 16: launch_hsolve2<COMP, 16>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, e); break;
+            case 32: launch_hsolve2<COMP, 32>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, e); break;
+            default: launch_hsolve2<COMP, 64>(ctx, grid, sm2, va, hg, tabk(0), tabk(1), mu_raw, gm, status, e); break;
           }
-          FPCA_LAUNCHED(ctx, "cov_hpass_solve");
-          if (ef.esc_count) {
-            k_escalated<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-                P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef,
-                hg.half);
-            FPCA_LAUNCHED(ctx, "cov_escalated");
+          return true;
+        };
+        bool packed = use_ts;
+        if (use_ts && hs_ok && ctx->tside_kernel == 0) {
+          // autotune: both sweeps built for this grid and these windows; time each
+          // once (twice, keeping the faster run) and remember the faster in the context
+          const std::array<int, 6> key = {M1, M2, Tax[0], Tax[1], COMP ? 1 : 0, tg.half};
+          auto it = ctx->tside_choice.find(key);
+          if (it == ctx->tside_choice.end()) {
+            Epilogue<float> e = ef;  // no accumulating epilogues, escalations solved in place
+            e.cvacc = nullptr;
+            e.y = nullptr;
+            e.esc_count = nullptr;
+            cudaEvent_t ev[5];
+            for (auto& x : ev) cudaEventCreate(&x);
+            cudaEventRecord(ev[0], ctx->stream);
+            for (int rep = 0; rep < 2; ++rep) {
+              run_ts(e);
+              cudaEventRecord(ev[1 + 2 * rep], ctx->stream);
+              run_hs(e);
+              cudaEventRecord(ev[2 + 2 * rep], ctx->stream);
+            }
+            ctx->launches += 4;
+            fpca_status st = fpca_check_launch(ctx, "t-side autotune");
+            if (st == FPCA_OK && cudaEventSynchronize(ev[4]) != cudaSuccess)
+              st = fpca_check_launch(ctx, "t-side autotune");
+            float t[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]);
+            for (auto& x : ev) cudaEventDestroy(x);
+            if (st != FPCA_OK) return st;
+            const float tts = std::min(t[0], t[2]), ths = std::min(t[1], t[3]);
+            it = ctx->tside_choice.emplace(key, tts <= ths ? 2 : 1).first;
           }
-          if (hg.half && (gm || status)) {
-            const int nt = (P + 31) / 32;
-            k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>(P, gm, status);
-            FPCA_LAUNCHED(ctx, "cov_mirror");
-          }
-          return FPCA_OK;
+          packed = it->second == 2;
         }
+        if (ef.esc_count) cudaMemsetAsync(ef.esc_count, 0, sizeof(unsigned), ctx->stream);
+        if (packed) {
+          if (!run_ts(ef))
+            return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "t-side sweep: no kernel for T = %d", Tax[0]);
+          FPCA_LAUNCHED(ctx, "cov_tsweep");
+        } else {
+          run_hs(ef);
+          FPCA_LAUNCHED(ctx, "cov_hpass_solve");
+        }
+        if (ef.esc_count) {
+          k_escalated<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(
+              P, ef.esc_slots, ef.esc_idx, ef.esc_count, ef.esc_cap, mu_raw, gm, status, ef,
+              tg.half);
+          FPCA_LAUNCHED(ctx, "cov_escalated");
+        }
+        if (tg.half && (gm || status)) {
+          const int nt = (P + 31) / 32;
+          k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>(P, gm, status);
+          FPCA_LAUNCHED(ctx, "cov_mirror");
+        }
+        return FPCA_OK;
       }
     }
     constexpr int NT = 512, PPT = 2;

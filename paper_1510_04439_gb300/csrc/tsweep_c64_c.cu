@@ -1,0 +1,8 @@
+// Packed-pair t-side sweep kernels for t-planes 64 wide, half-widths 11..13.
+#include "tside.cuh"
+
+namespace fpca_sweep {
+
+bool tsweep_c64_c(FPCA_TSWEEP_PARAMS) { return tsweep_launch_range<64, 11, 13>(FPCA_TSWEEP_ARGS); }
+
+}  // namespace fpca_sweep

@@ -1,0 +1,8 @@
+// Packed-pair t-side sweep kernels for t-planes 64 wide, half-widths 17..19.
+#include "tside.cuh"
+
+namespace fpca_sweep {
+
+bool tsweep_c64_e(FPCA_TSWEEP_PARAMS) { return tsweep_launch_range<64, 17, 19>(FPCA_TSWEEP_ARGS); }
+
+}  // namespace fpca_sweep

@@ -217,3 +217,60 @@ def test_learned_bandwidth_gain(ctx):
     assert s["sine_grid_median"] < 0.5, s          # the fits do recover the eigenfunctions
     for r in rows:
         assert np.isfinite(r["sine_grid"]) and np.isfinite(r["sine_learned"])
+
+
+def test_mlp_init_is_he_normal_and_seeded(ctx):
+    """fpca_bw_mlp_init: biases zero, each layer's weights N(0, 2/fan_in) (sample
+    mean and variance within a few standard errors), same seed same vector."""
+    n = omlp.param_count()
+    a = torch.empty(n, dtype=torch.float32, device=DEV)
+    b = torch.empty_like(a)
+    c = torch.empty_like(a)
+    ctx.bw_mlp_init(a, 7)
+    ctx.bw_mlp_init(b, 7)
+    ctx.bw_mlp_init(c, 8)
+    ctx.sync()
+    assert torch.equal(a, b)
+    assert not torch.equal(a, c)
+    layers = omlp.unpack(host(a).astype(np.float64))
+    for (W, bias), (fi, fo) in zip(layers, omlp.LAYERS):
+        assert np.all(bias == 0.0)
+        var = 2.0 / fi
+        k = W.size
+        assert abs(W.mean()) <= 5.0 * np.sqrt(var / k)
+        assert abs(W.var() / var - 1.0) <= 5.0 * np.sqrt(2.0 / k)
+        # normal shape: the fraction inside one standard deviation is 0.6827
+        inside = np.mean(np.abs(W) <= np.sqrt(var))
+        assert abs(inside - 0.6827) <= 5.0 * np.sqrt(0.6827 * 0.3173 / k)
+
+
+def test_mlp_save_and_load_round_trip(ctx, tmp_path):
+    from paper_1510_04439_gb300 import binding as B
+    n = omlp.param_count()
+    th = torch.empty(n, dtype=torch.float32, device=DEV)
+    ctx.bw_mlp_init(th, 3)
+    mu = torch.linspace(-1, 1, 32, dtype=torch.float32, device=DEV)
+    sd = torch.linspace(0.5, 2, 32, dtype=torch.float32, device=DEV)
+    path = tmp_path / "net.bin"
+    ctx.bw_mlp_io(th, path, True, mu, sd)
+    th2 = torch.zeros_like(th)
+    mu2 = torch.zeros_like(mu)
+    sd2 = torch.zeros_like(sd)
+    ctx.bw_mlp_io(th2, path, False, mu2, sd2)
+    ctx.sync()
+    assert torch.equal(th, th2) and torch.equal(mu, mu2) and torch.equal(sd, sd2)
+    # the loaded network predicts what the saved one did
+    X = torch.randn(16, 32, device=DEV)
+    o1 = torch.empty(16, 6, device=DEV)
+    o2 = torch.empty(16, 6, device=DEV)
+    ctx.bw_predict(th, X, o1)
+    ctx.bw_predict(th2, X, o2)
+    ctx.sync()
+    assert torch.equal(o1, o2)
+    # a file of another layout is refused and leaves the arrays alone
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"FPCABW01" + (123).to_bytes(8, "little") + bytes(64))
+    with pytest.raises(B.FpcaError) as e:
+        ctx.bw_mlp_io(th2, bad, False)
+    assert e.value.status == B.E_INVALID_ARG
+    assert torch.equal(th, th2)

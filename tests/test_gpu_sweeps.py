@@ -1,0 +1,166 @@
+"""The two t-side sweeps of the FP32 d = 2 covariance smoother against the oracle.
+
+fpca_smooth_cov_project (FPCA_F32 / FPCA_F32C) evaluates the t-side of the moment
+sums either with the scalar sweep (every grid and window) or with the packed-pair
+sweep (t-planes 32 or 64 wide, the same half-width on both t axes, up to 39
+taps), and by default times both once per grid and window and keeps the faster.
+Each choice is compared element by element with the FP64 oracle
+(oracle/grid.py, pinned to the per-point smoother) on grids that leave a ragged
+last block of t1-rows, from 7 to 39 taps, in the t >= s half mode (symmetric
+bins, mirrored), with the fused projection y = Gamma_hat Omega (every pair
+fitted) and with the K-fold CV epilogue.
+
+Tolerances: FP32 moments rel-L2 <= 1e-5 on points both sides fit with the full
+local linear model; statuses equal outside the pivot band (assert_status_band);
+CV score rel 1e-4 with the same argmin; y rel-L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import fpca_synth as fs
+from oracle import cv as ocv
+from oracle import grid as og
+from oracle import smoother as sm
+from parity_helpers import assert_status_band, grid_pairs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1510_04439_gb300 import binding
+    return binding
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def same_taps_h(m, T):
+    """Bandwidths with exactly T taps each side on every axis: T < h M <= T + 1."""
+    return tuple((T + 0.5) / mk for mk in m)
+
+
+def dense_bins(m, n, seed):
+    D = fs.make_dense(2, m, n, [2.0, 1.0, 0.5], sigma=0.3, seed=seed, dropout=0.2, domain="disk")
+    cnt, Wm, Vm, _ = sm.bin_mean_dense(D.y, D.mask, D.m)
+    mu, _ = sm.smooth_mean(D.m, (0.2, 0.2), cnt, Wm, Vm)
+    mu = np.where(np.isnan(mu), 0.0, mu)
+    return sm.bin_cov_dense(sm.residuals_dense(D.y, D.mask, mu), D.mask)
+
+
+@pytest.mark.parametrize("m,T", [((21, 32), 3), ((21, 32), 12), ((11, 64), 9), ((9, 64), 5),
+                                 ((20, 64), 19)])
+def test_sweeps_vs_oracle(B, m, T):
+    ctx = B.Context(0)
+    h = same_taps_h(m, T)
+    C, W, V = dense_bins(m, 60, seed=m[0] * 100 + T)
+    P = m[0] * m[1]
+    rG, rst = og.smooth_cov(m, h, C, W, V)
+    results = {}
+    for kern in (1, 2, 0):
+        ctx.set_sweep_kernel(kern)
+        for prec in (B.F32, B.F32C):
+            G = torch.empty(P, P, dtype=torch.float32, device=DEV)
+            st = torch.empty(P, P, dtype=torch.uint8, device=DEV)
+            ctx.smooth_cov_project(m, dev(C, torch.int32), dev(W, torch.float32),
+                                   dev(V, torch.float32), [h], prec, gamma=G, status=st)
+            ctx.sync()
+            g = G.cpu().numpy().astype(np.float64)
+            s = st.cpu().numpy()
+            assert_status_band(s, rst, grid_pairs(P), m, h, C, W, V, max_mismatch=P * P // 1000)
+            ok = (rst == sm.STATUS_OK) & (s == sm.STATUS_OK)
+            assert rel_l2(g[ok], rG[ok]) <= 1e-5, (kern, prec)
+            fb = (rst == sm.STATUS_FALLBACK) & (s == sm.STATUS_FALLBACK)
+            if fb.any():
+                assert rel_l2(g[fb], rG[fb]) <= 1e-5
+            assert np.array_equal(np.isnan(g), rst == sm.STATUS_EMPTY)
+            results[(kern, prec)] = (g, s)
+    # the two sweeps add the same terms in different groupings: equal statuses
+    # outside the band, values within the FP32 tolerance of each other
+    for prec in (B.F32, B.F32C):
+        g1, s1 = results[(1, prec)]
+        g2, s2 = results[(2, prec)]
+        ok = (s1 == sm.STATUS_OK) & (s2 == sm.STATUS_OK)
+        assert np.mean(s1 == s2) > 0.999
+        assert rel_l2(g2[ok], g1[ok]) <= 1e-5
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_sweeps_projection_epilogue(B, kern):
+    """y = Gamma_hat Omega fused into the sweep (every pair fitted, no mirror)."""
+    ctx = B.Context(0)
+    ctx.set_sweep_kernel(kern)
+    m, T, l = (13, 64), 7, 18
+    h = same_taps_h(m, T)
+    C, W, V = dense_bins(m, 50, seed=5)
+    P = m[0] * m[1]
+    om = fs.gaussian_test_matrix(P, l, 3).astype(np.float32)
+    y = torch.empty(P, l, dtype=torch.float32, device=DEV)
+    G = torch.empty(P, P, dtype=torch.float32, device=DEV)
+    ctx.smooth_cov_project(m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32),
+                           [h], B.F32C, omega=dev(om), y=y, gamma=G)
+    ctx.sync()
+    rG, rst = og.smooth_cov(m, h, C, W, V)
+    ref = np.where(np.isnan(rG), 0.0, rG) @ om.astype(np.float64)
+    assert rel_l2(y.cpu().numpy().astype(np.float64), ref) <= 1e-5
+    # y is the product of the surface the same call wrote
+    g = np.nan_to_num(G.cpu().numpy().astype(np.float64))
+    assert rel_l2(y.cpu().numpy().astype(np.float64), g @ om.astype(np.float64)) <= 1e-5
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_sweeps_cv_epilogue(B, kern):
+    """K-fold CV scores through either sweep against the oracle's CV."""
+    ctx = B.Context(0)
+    ctx.set_sweep_kernel(kern)
+    m = (16, 32)
+    D = fs.make_sparse(2, m, 3000, [2.0, 1.0], nmin=5, nmax=20, sigma=0.5, seed=12, nfold=5)
+    mu = np.linspace(-0.2, 0.3, D.P)
+    r = sm.residuals_sparse(D.t, D.y, mu, m)
+    C, W, V, Q = sm.bin_cov_sparse(D.offs, D.t, r, m, D.fold, 5)
+    Ts = [2, 4, 8]
+    hs = [same_taps_h(m, T) for T in Ts]
+    cv = torch.empty(len(hs), dtype=torch.float64, device=DEV)
+    ctx.smooth_cov_project(m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32),
+                           hs, B.F32C, q=dev(Q, torch.float32), nfold=5, cv=cv)
+    ctx.sync()
+    ref = np.array([ocv.cv_score(m, list(h), C, W, V, Q, smooth=og.smooth_cov) for h in hs])
+    got = cv.cpu().numpy()
+    assert np.array_equal(np.isfinite(got), np.isfinite(ref))
+    fin = np.isfinite(ref)
+    assert np.allclose(got[fin], ref[fin], rtol=1e-4)
+    assert np.argmin(np.where(fin, got, np.inf)) == np.argmin(np.where(fin, ref, np.inf))
+
+
+def test_sweep_choice_is_remembered(B):
+    """Automatic mode times both sweeps once per grid and window: the second call
+    launches no timing runs."""
+    ctx = B.Context(0)
+    m, T = (16, 64), 9
+    h = same_taps_h(m, T)
+    C, W, V = dense_bins(m, 30, seed=9)
+    P = m[0] * m[1]
+    G = torch.empty(P, P, dtype=torch.float32, device=DEV)
+    args = (m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32), [h], B.F32C)
+    l0 = ctx.launches
+    ctx.smooth_cov_project(*args, gamma=G)
+    first = ctx.launches - l0
+    ctx.sync()
+    g1 = G.clone()
+    l0 = ctx.launches
+    ctx.smooth_cov_project(*args, gamma=G)
+    second = ctx.launches - l0
+    ctx.sync()
+    assert first == second + 4      # two timing runs of each sweep, once
+    assert torch.equal(G, g1)       # the remembered choice gives the same surface
