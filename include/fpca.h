@@ -119,6 +119,15 @@ fpca_status fpca_sync(fpca_ctx* ctx);
 /* Number of kernels this context has launched so far (host counter). */
 uint64_t fpca_launch_count(const fpca_ctx* ctx);
 
+/* Arithmetic-throughput probe: launches `blocks` blocks of 256 threads that
+ * each run 8 independent FMA chains for 16 * iters rounds (fp64 = 0: paired FP32
+ * FMAs, two per instruction; fp64 != 0: FP64 FMAs) and writes to *flops (host)
+ * the floating-point operations the launch performs (2 per FMA).  The caller
+ * times the launch on the context's stream (CUDA events) to measure the FP32 or
+ * FP64 FMA peak of the device; with blocks a few times the SM count the FMA pipes,
+ * not latency, bind. */
+fpca_status fpca_alu_probe(fpca_ctx* ctx, int fp64, int blocks, int iters, double* flops);
+
 /* Choice of the t-side moment sweep of the FP32 d = 2 covariance smoother
  * (fpca_smooth_cov_project with FPCA_F32 / FPCA_F32C):
  *  0  automatic (default): the candidates built for the grid and windows are
@@ -172,6 +181,20 @@ fpca_status fpca_bin_mean(fpca_ctx* ctx, const fpca_data* data, const fpca_grid*
 fpca_status fpca_smooth_mean(fpca_ctx* ctx, const fpca_grid* grid, const int32_t* cnt,
                              const double* w, const double* v, const double* h,
                              double* mu, uint8_t* status);
+
+/* Cross-validation score of the mean smoother, Eq. (2.3) (Section 3.3
+ * selects bandwidths by cross-validation), for nh bandwidth vectors h (host,
+ * nh x d): subjects are split into nfold folds by fold[i] (device int32,
+ * length n, values 0..nfold-1); for fold f the mean is fitted on the mean bins
+ * of the other folds and scored on fold f's observations at their bin centres
+ * with the weights 1/N_i: sum (1/N_i)(Y_ij - mu_hat(c))^2 over held-out
+ * observations whose fit is not EMPTY, divided by their weight sum; +inf when
+ * EMPTY fits hold more than 1% of the held-out weight.  Scattered data only
+ * (FPCA_SPARSE; gridded data can be listed as points at the node centres);
+ * FP64 throughout.  cv: nh device doubles out. */
+fpca_status fpca_smooth_mean_cv(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                                const int32_t* fold, int nfold, const double* h, int nh,
+                                double* cv);
 
 /* Covariance bins of Eq. (2.4) over ordered pairs j != l of one subject,
  * subject weight 1/(N_i(N_i - 1)) (subjects with N_i < 2 skipped).
@@ -231,7 +254,11 @@ fpca_status fpca_smooth_cov_project(fpca_ctx* ctx, const fpca_grid* grid,
  *  gamma: P x P, double (gamma_prec FPCA_F64) or float (FPCA_F32).
  *  domain: P int32 mean-bin counts from fpca_bin_mean (a node is inside
  *   Omega when its count is > 0), or NULL for the whole box.
- *  full = 1: dense cyclic Jacobi eigensolver on Sigma (FP64; P <= 1024).
+ *  full = 1: all eigenpairs of Sigma itself (gamma FP64, P <= 1024), of which the
+ *   leading k are returned: two-sided block Jacobi in FP32 (blocks of 16 indices,
+ *   each round's block pairs diagonalised side by side, the rotations applied
+ *   across the GPU), then three Ogita-Aishima refinement steps in FP64 on the
+ *   FP64 matrix (each squares the error: eigenpairs to about FP64 accuracy).
  *  full = 0: random projection (Section 3.4) with the caller's Gaussian
  *   test matrix omega (P x l float, k < l <= 64): Y = Sigma Omega, power_iters
  *   rounds of Q = orth(Y), Y = Sigma Q, then Q = orth(Y), B = Q' Sigma Q and

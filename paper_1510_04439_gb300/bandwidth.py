@@ -2,18 +2,22 @@
 
 Section 3.3 selects bandwidths by cross-validation and calls grid search
 expensive.  Here a small network (fpca_bw_predict / fpca_bw_train_step)
-proposes the CV-optimal covariance bandwidth from 32 summary numbers of the
-binned data (fpca_bw_features); a CV check at the proposal and two
-neighbours (h x {0.8, 1, 1.25}) replaces the 16-bandwidth grid, and the grid
-is kept as the fallback when a neighbour beats the proposal by more than 5%.
+proposes the CV-optimal bandwidths of both smoothers -- the mean (Eq. 2.3) and
+the covariance (Eq. 2.4) -- from 32 summary numbers of the binned data
+(fpca_bw_features); a CV check at each proposal and two neighbours
+(h x {0.8, 1, 1.25}) replaces the 16-bandwidth grids, and a grid is kept as the
+fallback when a neighbour beats the proposal by more than 5%.
 
 Everything numerical runs in libfpca.so kernels through the ABI; this module
 draws datasets (fpca_synth), moves arrays and runs the training loop.
 
-Labels: the argmin of the 5-fold subject-level CV score over 16 isotropic
-bandwidths log-spaced in [0.03, 0.3] (covariance smoother).  Output entries
-3..5 (log h_Gamma per axis) carry the label for axes < d; the mean-bandwidth
-entries 0..2 are masked (no CV of the mean smoother is built).
+Labels: per dataset, the argmin of the 5-fold subject-level CV of the mean
+smoother (fpca_smooth_mean_cv) over 16 isotropic bandwidths log-spaced in
+[0.03, 0.3] gives h_mu (output entries 0..d-1); the covariance bins are then
+formed from the residuals of the mean fitted at that h_mu, and the argmin of
+the covariance CV over the same 16 bandwidths gives h_Gamma (entries 3..3+d-1).
+The network's input is computed from pilot bins (mean fitted at h = 0.1), which
+is what it sees at inference, before any bandwidth is known.
 
 CLI:  python -m paper_1510_04439_gb300.bandwidth --train 2000 --eval 200 --out run.npz
 """
@@ -31,6 +35,7 @@ from . import pipeline
 
 HGRID = np.exp(np.linspace(math.log(0.03), math.log(0.3), 16))
 NFOLD = 5
+H_PILOT = 0.1   # mean bandwidth of the pilot bins the network's input comes from
 
 
 def draw_dataset(seed):
@@ -46,7 +51,7 @@ def draw_dataset(seed):
         lam = [4.0, 2.0, 1.0, 0.5][: int(rng.integers(2, 5))]
         mean = "1d"
     else:
-        m = (32, 32)
+        m = (64, 64)
         lam = [8.0 * 2.0 ** (-k) for k in range(int(rng.integers(2, 7)))]
         mean = "sincos"
     if kind == "dense":
@@ -81,8 +86,8 @@ class Labeller:
     def upload(self, ds):
         return {k: self.torch.from_numpy(ds[k]).to(self.dev) for k in ("offs", "t", "y", "fold")}
 
-    def prepare(self, ds, tensors=None, features=True):
-        """Mean bins and fit, fold-split covariance bins, and (optionally) the features."""
+    def prepare(self, ds, tensors=None):
+        """Mean bins of all subjects (the smoothers' input; the mean fit comes later)."""
         torch = self.torch
         m = ds["m"]
         P = int(np.prod(m))
@@ -91,16 +96,28 @@ class Labeller:
         data = self.ctx.sparse(t["offs"], t["t"], t["y"])
         v2 = torch.empty_like(bufs.w)
         self.ctx.bin_mean(data, m, bufs.cnt, bufs.w, bufs.v, v2)
-        hmu = [0.1] * len(m)
-        self.ctx.smooth_mean(m, bufs.cnt, bufs.w, bufs.v, hmu, bufs.mu)
-        self.ctx.bin_cov(data, m, bufs.mu, B.F32, bufs.ccnt, bufs.cw, bufs.cv_, q=bufs.cq,
-                         fold=t["fold"], nfold=NFOLD)
-        prep = dict(bufs=bufs, tensors=t, data=data, m=m, d=len(m), v2=v2, feat=None)
-        if features:
-            self.features(prep)
-        return prep
+        return dict(bufs=bufs, tensors=t, data=data, m=m, d=len(m), v2=v2, feat=None, h_mu=None)
+
+    def mean_cv(self, prep, hs):
+        """CV score of the mean smoother at each isotropic bandwidth in hs."""
+        out = self.torch.empty(len(hs), dtype=self.torch.float64, device=self.dev)
+        self.ctx.smooth_mean_cv(prep["data"], prep["m"], prep["tensors"]["fold"], NFOLD,
+                                [float(h) for h in hs], out)
+        return out
+
+    def cov_bins(self, prep, h_mu):
+        """Mean fit at h_mu and the fold-split covariance bins of its residuals."""
+        b = prep["bufs"]
+        m = prep["m"]
+        self.ctx.smooth_mean(m, b.cnt, b.w, b.v, [float(h_mu)] * len(m), b.mu)
+        self.ctx.bin_cov(prep["data"], m, b.mu, B.F32, b.ccnt, b.cw, b.cv_, q=b.cq,
+                         fold=prep["tensors"]["fold"], nfold=NFOLD)
+        prep["h_mu"] = float(h_mu)
 
     def features(self, prep):
+        """The network's input from the pilot bins (covariance bins at H_PILOT)."""
+        if prep["h_mu"] != H_PILOT:
+            self.cov_bins(prep, H_PILOT)
         b = prep["bufs"]
         feat = self.torch.empty(32, dtype=self.torch.float32, device=self.dev)
         self.ctx.bw_features(prep["data"], prep["m"], b.cnt, b.w, b.v, prep["v2"], b.ccnt, b.cw,
@@ -109,7 +126,8 @@ class Labeller:
         return feat
 
     def cv(self, prep, hs):
-        """CV score of each isotropic bandwidth in hs (one pass per bandwidth and fold)."""
+        """CV score of each isotropic covariance bandwidth in hs (one pass per bandwidth
+        and fold) on the current covariance bins."""
         torch = self.torch
         b = prep["bufs"]
         out = torch.empty(len(hs), dtype=torch.float64, device=self.dev)
@@ -134,6 +152,24 @@ class Labeller:
         return evals, evecs
 
 
+def grid_argmin(scores):
+    fin = np.isfinite(scores)
+    return (int(np.argmin(np.where(fin, scores, np.inf))) if fin.any() else len(HGRID) // 2), \
+        bool(fin.any())
+
+
+def check_proposal(score_fn, hp):
+    """CV at hp x {0.8, 1, 1.25}: (chosen h, its score, fallback?).  Fallback when the
+    proposal's score is not finite or a neighbour beats it by more than 5%."""
+    hp = float(np.clip(hp, HGRID[0], HGRID[-1]))
+    cand = [hp * 0.8, hp, hp * 1.25]
+    chk = score_fn(cand)
+    fallback = (not np.isfinite(chk[1])) or bool(min(chk[0], chk[2]) < 0.95 * chk[1])
+    fin = np.isfinite(chk)
+    j = int(np.argmin(np.where(fin, chk, np.inf))) if fin.any() else 1
+    return cand[j], float(chk[j]) if fin.any() else math.inf, fallback
+
+
 def subspace_sine(a, b):
     """Largest principal-angle sine between the column spaces of a and b."""
     qa, _ = np.linalg.qr(a)
@@ -143,28 +179,43 @@ def subspace_sine(a, b):
 
 
 def make_table(ctx, torch, seeds, log_every=0):
-    """Features and CV-grid labels of datasets drawn with ``seeds``."""
+    """Features (pilot bins) and the CV-grid labels of both bandwidths of datasets drawn
+    with ``seeds``: (X, Y, M, best) with best[:, 0] the mean and best[:, 1] the
+    covariance grid index."""
     lab = Labeller(ctx, torch)
     feats, targets, masks, best = [], [], [], []
     t0 = time.time()
     for k, s in enumerate(seeds):
         ds = draw_dataset(int(s))
         prep = lab.prepare(ds)
-        scores = lab.cv(prep, HGRID).cpu().numpy()
-        fin = np.isfinite(scores)
-        j = int(np.argmin(np.where(fin, scores, np.inf))) if fin.any() else len(HGRID) // 2
+        feats.append(lab.features(prep).cpu().numpy())
+        jm, okm = grid_argmin(lab.mean_cv(prep, HGRID).cpu().numpy())
+        lab.cov_bins(prep, HGRID[jm])
+        jc, okc = grid_argmin(lab.cv(prep, HGRID).cpu().numpy())
         tgt = np.zeros(6, np.float32)
         msk = np.zeros(6, np.uint8)
         for a in range(ds["d"]):
-            tgt[3 + a] = math.log(HGRID[j])
-            msk[3 + a] = 1
-        feats.append(prep["feat"].cpu().numpy())
+            tgt[a], msk[a] = math.log(HGRID[jm]), int(okm)
+            tgt[3 + a], msk[3 + a] = math.log(HGRID[jc]), int(okc)
         targets.append(tgt)
-        masks.append(msk if fin.any() else np.zeros(6, np.uint8))
-        best.append(j)
+        masks.append(msk)
+        best.append((jm, jc))
         if log_every and (k + 1) % log_every == 0:
             print(f"labelled {k + 1}/{len(seeds)} in {time.time() - t0:.1f} s", flush=True)
     return (np.stack(feats), np.stack(targets), np.stack(masks), np.array(best))
+
+
+def median_labels(Y, M, D):
+    """The constant proposal of the ablation: per dimension count d, the median
+    training label of log h_mu and of log h_Gamma (D: the datasets' d)."""
+    out = {}
+    for d in np.unique(D):
+        sel = D == d
+        mu_l = Y[sel & (M[:, 0] > 0), 0]
+        cv_l = Y[sel & (M[:, 3] > 0), 3]
+        out[int(d)] = (float(np.exp(np.median(mu_l))) if mu_l.size else H_PILOT,
+                       float(np.exp(np.median(cv_l))) if cv_l.size else H_PILOT)
+    return out
 
 
 def standardize(X, mu=None, sd=None):
@@ -207,17 +258,21 @@ def predict(ctx, torch, th, X):
     return out.cpu().numpy()
 
 
-def evaluate(ctx, torch, th, mu, sd, seeds):
-    """Per held-out dataset, the whole FPCA (bins, bandwidth choice, final surface and
-    top-k eigenfunctions, k = the true number of components) by both methods:
+def evaluate(ctx, torch, th, mu, sd, seeds, const=None):
+    """Per held-out dataset, the whole FPCA (mean bins, both bandwidth choices, the mean
+    fit, covariance bins, the final surface and its top-k eigenfunctions, k = the true
+    number of components) by each method:
 
-      grid:    CV over the 16 bandwidths, fit at the best one;
-      learned: features -> network -> CV check at h x {0.8, 1, 1.25} -> fit at the
-               best checked bandwidth, or the grid when a neighbour beats the
-               proposal by more than 5% (fallback).
+      grid:     mean CV over the 16 bandwidths, covariance bins at the best one,
+                covariance CV over the 16 bandwidths, fit at the best one;
+      learned:  pilot bins -> features -> network -> for each smoother a CV check at
+                h x {0.8, 1, 1.25} (the grid of that smoother when a neighbour beats
+                the proposal by more than 5%) -> fit;
+      constant: the same checks started from the median training labels (``const``,
+                per d) instead of the network: the ablation of the network.
 
-    Records wall times of each stage (GPU work plus host overhead, synchronised),
-    CV scores, and the eigenfunction subspace error of both fits against the truth."""
+    Records wall times (GPU work plus host overhead, synchronised), CV scores, and the
+    eigenfunction subspace error of each fit against the truth."""
     import fpca_synth as fs
     lab = Labeller(ctx, torch)
     rows = []
@@ -226,77 +281,139 @@ def evaluate(ctx, torch, th, mu, sd, seeds):
         torch.cuda.synchronize()
         return time.perf_counter()
 
+    def checked_path(prep, hp_mu, hp_cov, gm, gc, k, omega):
+        """The two proposal checks and the fit; grids gm, gc (computed by the grid path)
+        stand in for a rerun on fallback, their time is charged as measured."""
+        t0 = clock()
+        h_mu, s_mu, fb_mu = check_proposal(lambda hs: lab.mean_cv(prep, hs).cpu().numpy(), hp_mu)
+        if fb_mu:
+            h_mu = float(HGRID[grid_argmin(gm[0])[0]])
+        ta = clock()
+        lab.cov_bins(prep, h_mu)
+        tb = clock()
+        h_cv, s_cv, fb_cv = check_proposal(lambda hs: lab.cv(prep, hs).cpu().numpy(), hp_cov)
+        t1 = clock()
+        if fb_cv:
+            h_cv = float(HGRID[grid_argmin(gc[0])[0]])
+        _, vec = lab.fit(prep, h_cv, k, omega)
+        vec = vec.cpu().numpy().T
+        t2 = clock()
+        extra = (gm[1] if fb_mu else 0.0) + (gc[1] if fb_cv else 0.0)
+        return dict(h_mu=h_mu, h_cov=h_cv, s_mu=s_mu, s_cov=s_cv, fb_mu=fb_mu, fb_cov=fb_cv,
+                    t_select=t1 - t0 + extra, t_fit=t2 - t1, vec=vec,
+                    t_mean_check=ta - t0, t_bins=tb - ta, t_cov_check=t1 - tb)
+
+    # one untimed pass per dimension count first: the library's one-time costs
+    # (workspace growth, the sweep autotuner's first timing of each window, the
+    # caching allocator's first blocks) belong to neither method
+    seen = set()
+    warm = []
     for s in seeds:
+        d = draw_dataset(int(s))["d"]
+        if d not in seen:
+            seen.add(d)
+            warm.append(int(s))
+    seeds = list(warm) + [int(s) for s in seeds]
+    nwarm = len(warm)
+
+    for idx, s in enumerate(seeds):
         ds = draw_dataset(int(s))
         m = ds["m"]
         P = int(np.prod(m))
         k = len(ds["lam"])
         omega = torch.from_numpy(fs.gaussian_test_matrix(P, k + 10, int(s)).astype(np.float32)).to(ctx.device)
         tens = lab.upload(ds)
-        t0 = clock()
-        prep = lab.prepare(ds, tens, features=False)
-        t1 = clock()
-        grid = lab.cv(prep, HGRID).cpu().numpy()
-        t2 = clock()
-        fin = np.isfinite(grid)
-        jb = int(np.argmin(np.where(fin, grid, np.inf))) if fin.any() else len(HGRID) // 2
-        _, vec_g = lab.fit(prep, HGRID[jb], k, omega)
-        vec_g = vec_g.cpu().numpy().T
-        t3 = clock()
-        feat = lab.features(prep).cpu().numpy()
-        f = (feat[None, :] - mu) / sd
-        out = predict(ctx, torch, th, f)[0]
-        hp = float(np.exp(np.mean(out[3:3 + ds["d"]])))
-        hp = float(np.clip(hp, HGRID[0], HGRID[-1]))
-        cand = [hp * 0.8, hp, hp * 1.25]
-        chk = lab.cv(prep, cand).cpu().numpy()
-        t4 = clock()
-        fallback = (not np.isfinite(chk[1])) or bool(min(chk[0], chk[2]) < 0.95 * chk[1])
-        if fallback:
-            h_l = float(HGRID[jb])       # the grid scores computed above stand in for a rerun
-        else:
-            h_l = float(cand[int(np.nanargmin(np.where(np.isfinite(chk), chk, np.nan)))])
-        t5 = clock()
-        _, vec_l = lab.fit(prep, h_l, k, omega)
-        vec_l = vec_l.cpu().numpy().T
-        t6 = clock()
-        best = float(np.min(grid[fin])) if fin.any() else math.inf
-        prop = float(np.nanmin(np.where(np.isfinite(chk), chk, np.nan))) if np.isfinite(chk).any() \
-            else math.inf
         c = fs.grid_centres(m)
         phi = np.stack([fs.eval_fourier(sp, c) for sp in ds["specs"]], axis=1)
-        t_prep, t_cv, t_fit_g = t1 - t0, t2 - t1, t3 - t2
-        t_sel, t_fit_l = t4 - t3, t6 - t5
-        rows.append(dict(
-            seed=int(s), d=ds["d"], k=k, grid_best=best, grid_h=float(HGRID[jb]), prop_h=hp,
-            prop_score=prop, fallback=fallback, final_h=h_l,
-            final_score=best if fallback else prop,
-            t_grid=t_cv, t_prop=t_sel,
-            t_final=t_sel + (t_cv if fallback else 0.0),
-            fpca_grid=t_prep + t_cv + t_fit_g,
-            fpca_learned=t_prep + t_sel + (t_cv if fallback else 0.0) + t_fit_l,
-            sine_grid=subspace_sine(vec_g, phi), sine_learned=subspace_sine(vec_l, phi)))
+        # grid
+        t0 = clock()
+        prep = lab.prepare(ds, tens)
+        t1 = clock()
+        gm = lab.mean_cv(prep, HGRID).cpu().numpy()
+        jm, _ = grid_argmin(gm)
+        lab.cov_bins(prep, HGRID[jm])
+        t2 = clock()
+        gc = lab.cv(prep, HGRID).cpu().numpy()
+        jc, okc = grid_argmin(gc)
+        t3 = clock()
+        _, vec_g = lab.fit(prep, HGRID[jc], k, omega)
+        vec_g = vec_g.cpu().numpy().T
+        t4 = clock()
+        t_prep, t_gm, t_gc, t_fit_g = t1 - t0, t2 - t1, t3 - t2, t4 - t3
+        # learned
+        t5 = clock()
+        feat = lab.features(prep).cpu().numpy()
+        out = predict(ctx, torch, th, (feat[None, :] - mu) / sd)[0]
+        t6 = clock()
+        d = ds["d"]
+        hp_mu = float(np.exp(np.mean(out[0:d])))
+        hp_cov = float(np.exp(np.mean(out[3:3 + d])))
+        L = checked_path(prep, hp_mu, hp_cov, (gm, t_gm), (gc, t_gc), k, omega)
+        C = None
+        if const is not None:
+            cm, cc = const[d]
+            C = checked_path(prep, cm, cc, (gm, t_gm), (gc, t_gc), k, omega)
+        best = float(np.min(gc[np.isfinite(gc)])) if okc else math.inf
+        row = dict(
+            seed=int(s), d=d, k=k, grid_best=best, grid_h_mu=float(HGRID[jm]),
+            grid_h=float(HGRID[jc]), prop_h_mu=hp_mu, prop_h=hp_cov,
+            final_h_mu=L["h_mu"], final_h=L["h_cov"], fallback=L["fb_cov"],
+            fallback_mu=L["fb_mu"], prop_score=L["s_cov"],
+            final_score=best if L["fb_cov"] else L["s_cov"],
+            t_grid=t_gm + t_gc, t_prop=(t6 - t5) + L["t_select"],
+            fpca_grid=t_prep + t_gm + t_gc + t_fit_g,
+            fpca_learned=t_prep + (t6 - t5) + L["t_select"] + L["t_fit"],
+            sine_grid=subspace_sine(vec_g, phi), sine_learned=subspace_sine(L["vec"], phi))
+        row.update(t_features=t6 - t5, t_mean_grid=t_gm, t_cov_grid=t_gc,
+                   t_mean_check=L["t_mean_check"], t_cov_check=L["t_cov_check"],
+                   t_bins=L["t_bins"], t_fit=L["t_fit"])
+        if C is not None:
+            row.update(const_h_mu=C["h_mu"], const_h=C["h_cov"], const_fallback=C["fb_cov"],
+                       const_fallback_mu=C["fb_mu"],
+                       const_score=best if C["fb_cov"] else C["s_cov"],
+                       fpca_const=t_prep + C["t_select"] + C["t_fit"],
+                       sine_const=subspace_sine(C["vec"], phi))
+        if idx >= nwarm:
+            rows.append(row)
     return rows
 
 
 def summarize(rows):
-    """Share of datasets whose final CV score is within 5% of the grid optimum, mean
-    wall times of both selections and of both whole FPCA runs, and the eigenfunction
-    subspace errors of both fits."""
+    """Share of datasets whose final covariance CV score is within 5% of the grid
+    optimum, fallback rates, mean wall times of the whole FPCA runs and the
+    eigenfunction subspace errors, for the learned proposal, the grid and (if run)
+    the constant proposal."""
     ok = [r for r in rows if np.isfinite(r["grid_best"])]
     ratio = np.array([r["final_score"] / r["grid_best"] for r in ok])
     pratio = np.array([r["prop_score"] / r["grid_best"] for r in ok])
     sg = np.array([r["sine_grid"] for r in rows])
     sl = np.array([r["sine_learned"] for r in rows])
     mean = lambda key: float(np.mean([r[key] for r in rows]))  # noqa: E731
-    return dict(n=len(rows), within5=float(np.mean(ratio <= 1.05)),
-                median_ratio=float(np.median(ratio)), proposal_within5=float(np.mean(pratio <= 1.05)),
-                fallback_rate=mean("fallback"), t_grid=mean("t_grid"), t_final=mean("t_final"),
-                fpca_grid_s=mean("fpca_grid"), fpca_learned_s=mean("fpca_learned"),
-                fpca_speedup=mean("fpca_grid") / mean("fpca_learned"),
-                sine_grid_median=float(np.median(sg)), sine_learned_median=float(np.median(sl)),
-                sine_grid_mean=float(np.mean(sg)), sine_learned_mean=float(np.mean(sl)),
-                sine_worse_by_0p01=float(np.mean(sl > sg + 0.01)))
+    out = dict(n=len(rows), within5=float(np.mean(ratio <= 1.05)),
+               median_ratio=float(np.median(ratio)), proposal_within5=float(np.mean(pratio <= 1.05)),
+               fallback_rate=mean("fallback"), fallback_rate_mu=mean("fallback_mu"),
+               h_mu_log_err_median=float(np.median([abs(math.log(r["final_h_mu"] / r["grid_h_mu"]))
+                                                    for r in rows])),
+               t_grid=mean("t_grid"), t_final=mean("t_prop"),
+               stage_ms={k: 1e3 * mean(k) for k in ("t_features", "t_mean_grid", "t_cov_grid",
+                                                    "t_mean_check", "t_bins", "t_cov_check",
+                                                    "t_fit")},
+               fpca_grid_s=mean("fpca_grid"), fpca_learned_s=mean("fpca_learned"),
+               fpca_speedup=mean("fpca_grid") / mean("fpca_learned"),
+               sine_grid_median=float(np.median(sg)), sine_learned_median=float(np.median(sl)),
+               sine_grid_mean=float(np.mean(sg)), sine_learned_mean=float(np.mean(sl)),
+               sine_worse_by_0p01=float(np.mean(sl > sg + 0.01)))
+    if rows and "sine_const" in rows[0]:
+        sc = np.array([r["sine_const"] for r in rows])
+        cratio = np.array([r["const_score"] / r["grid_best"] for r in ok])
+        out["constant_proposal"] = dict(
+            within5=float(np.mean(cratio <= 1.05)), fallback_rate=mean("const_fallback"),
+            fallback_rate_mu=mean("const_fallback_mu"), fpca_s=mean("fpca_const"),
+            fpca_speedup_vs_grid=mean("fpca_grid") / mean("fpca_const"),
+            sine_median=float(np.median(sc)), sine_mean=float(np.mean(sc)),
+            sine_worse_than_grid_by_0p01=float(np.mean(sc > sg + 0.01)),
+            learned_faster_share=float(np.mean([r["fpca_learned"] < r["fpca_const"] for r in rows])))
+    return out
 
 
 def main():
@@ -322,7 +439,8 @@ def main():
     t0 = time.time()
     th, hist = train(ctx, torch, Xs, Y, M, epochs=a.epochs)
     t_train = time.time() - t0
-    rows = evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(a.eval))
+    const = median_labels(Y, M, np.rint(X[:, 0]).astype(int))   # feature 0 is d
+    rows = evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(a.eval), const=const)
     summ = summarize(rows)
     summ.update(t_label=t_label, t_train=t_train, final_loss=hist[-1], first_loss=hist[0],
                 train=int(X.shape[0]), epochs=a.epochs)

@@ -32,7 +32,7 @@ SYMBOLS = (
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
     "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait", "fpca_set_sweep_kernel",
-    "fpca_bw_mlp_init", "fpca_bw_mlp_io",
+    "fpca_bw_mlp_init", "fpca_bw_mlp_io", "fpca_smooth_mean_cv", "fpca_alu_probe",
 )
 
 
@@ -113,7 +113,10 @@ def load(path=LIB_PATH):
     lib.fpca_launch_count.restype = ctypes.c_uint64
     lib.fpca_check_wait.argtypes = [vp, i32]
     lib.fpca_set_sweep_kernel.argtypes = [vp, i32]
+    lib.fpca_alu_probe.argtypes = [vp, i32, i32, i32, dbl_p]
     lib.fpca_bw_mlp_init.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.fpca_smooth_mean_cv.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32,
+                                        dbl_p, i32, vp]
     lib.fpca_bw_mlp_io.argtypes = [vp, vp, vp, vp, ctypes.c_char_p, i32]
     lib.fpca_bin_mean.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, vp, vp, vp]
     lib.fpca_smooth_mean.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, vp, dbl_p, vp, vp]
@@ -223,6 +226,13 @@ class Context:
         """Save (save=True) or load the network and its feature standardisation."""
         self._check(self.lib.fpca_bw_mlp_io(self.h, _ptr(params), _ptr(feat_mu), _ptr(feat_sd),
                                             str(path).encode(), int(bool(save))))
+
+    def alu_probe(self, fp64, blocks, iters):
+        """Queue the FMA-throughput probe; returns the flops it performs."""
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.fpca_alu_probe(self.h, int(bool(fp64)), int(blocks), int(iters),
+                                            ctypes.byref(out)))
+        return out.value
 
     def check_wait(self, arrive):
         """Queue the bounded-wait self-check (fpca_check_wait); its outcome is
@@ -376,6 +386,13 @@ class Context:
         self._check(self.lib.fpca_smooth_mean(self.h, ctypes.byref(Grid.of(m)), _ptr(cnt), _ptr(w),
                                               _ptr(v), _doubles(h), _ptr(mu), _ptr(status)))
 
+    def smooth_mean_cv(self, data, m, fold, nfold, hs, cv):
+        """K-fold CV score of the mean smoother for each bandwidth vector in hs."""
+        flat = [float(x) for hv in hs for x in (hv if hasattr(hv, "__len__") else [hv] * len(m))]
+        self._check(self.lib.fpca_smooth_mean_cv(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
+                                                 _ptr(fold), int(nfold), _doubles(flat), len(hs),
+                                                 _ptr(cv)))
+
     def bin_cov(self, data, m, mu, prec, cnt, w, v, q=None, mode=COV_RESIDUAL, fold=None, nfold=0):
         self._check(self.lib.fpca_bin_cov(self.h, ctypes.byref(data), ctypes.byref(Grid.of(m)),
                                           _ptr(mu), int(prec), int(mode), _ptr(fold), int(nfold),
@@ -384,6 +401,10 @@ class Context:
     def smooth_cov_project(self, m, cnt, w, v, h, prec, q=None, nfold=0, mu_raw=None, omega=None,
                            gamma=None, status=None, y=None, cv=None, symmetric=True):
         """symmetric=False for bins that are not symmetric in (s, t) (fpca_bin_cov's are)."""
+        if cnt.dtype.itemsize != 4 or cnt.dtype.is_floating_point:
+            raise TypeError(f"cnt must hold int32 pair counts (got {cnt.dtype})")
+        if w.dtype != v.dtype or (q is not None and q.dtype != w.dtype):
+            raise TypeError("w, v (and q) must share one floating type")
         bins = CovBins()
         bins.asym = 0 if symmetric else 1
         bins.nfold = int(nfold)

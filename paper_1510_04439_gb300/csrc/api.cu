@@ -331,6 +331,23 @@ fpca_status fpca_smooth_mean(fpca_ctx* ctx, const fpca_grid* grid, const int32_t
   return launch_smooth_mean(ctx, grid, cnt, w, v, h, mu, status);
 }
 
+fpca_status fpca_smooth_mean_cv(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
+                                const int32_t* fold, int nfold, const double* h, int nh,
+                                double* cv) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  fpca_prof_mark(ctx);
+  if (!valid_grid(ctx, grid, 1 << 20) || !valid_data(ctx, data)) return FPCA_E_INVALID_ARG;
+  if (data->layout != FPCA_SPARSE)
+    return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
+                     "mean CV is built for scattered data (list gridded observations as points)");
+  if (!fold || nfold < 2 || nfold > 64)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "fold and 2 <= nfold <= 64 are required");
+  if (nh < 1 || !cv) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "nh >= 1 and cv are required");
+  if (!valid_h(ctx, h, nh * grid->d)) return FPCA_E_INVALID_ARG;
+  return mean_cv_run(ctx, grid, data->n, data->offs, data->t, static_cast<const double*>(data->y),
+                     fold, nfold, h, nh, cv);
+}
+
 fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* grid,
                          const double* mu, int prec, int mode, const int32_t* fold, int nfold,
                          int32_t* cnt, void* w, void* v, void* q) {

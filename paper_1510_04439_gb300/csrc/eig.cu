@@ -7,7 +7,8 @@
 //  B        = Q' Sigma Q (compensated FP32 sums, FP64 result); eigenpairs of B
 //             by FP32 Jacobi and two Ogita-Aishima refinement steps
 //  Psi      = Q U;  lambda = theta dV;  phi = psi / sqrt(dV);  dV = 1/P
-// The dense path (full = 1) runs a cyclic FP64 Jacobi solver on Sigma itself.
+// The dense path (full = 1) diagonalises Sigma itself (n <= 1024): block Jacobi in
+// FP32 spread over the GPU, then FP64 Ogita-Aishima refinement (launch_dense_eig).
 #include <cmath>
 
 #include "fpca_internal.cuh"
@@ -497,115 +498,9 @@ __global__ void __launch_bounds__(256) k_apply_ff(int P, int l, const TX* __rest
   Q[e] = (TX)ff::to_double(acc);
 }
 
-// Cyclic parallel Jacobi (one block) on the symmetric n x n matrix A (global,
-// FP64, destroyed), V <- eigenvectors (columns).  Pairs follow the circle
-// method: n/2 disjoint rotations per step, n-1 steps per sweep.
-__global__ void __launch_bounds__(1024)
-    k_jacobi(int n, double* __restrict__ A, double* __restrict__ V, double* __restrict__ cs,
-             int* __restrict__ pairs, int max_sweeps) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int ne = (n + 1) & ~1;  // even count (index n is a dummy when n is odd)
-  const int np = ne / 2;
-  for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? 1.0 : 0.0;
-  __shared__ double red[32];
-  __shared__ int done;
-  __syncthreads();
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal vs diagonal mass
-    double off = 0.0, dia = 0.0;
-    for (int e = tid; e < n * n; e += nt) {
-      const int i = e / n, j = e - (e / n) * n;
-      const double a = A[e];
-      if (i == j) dia += a * a;
-      else off += a * a;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dia += __shfl_xor_sync(0xffffffffu, dia, o);
-    }
-    if ((tid & 31) == 0) red[tid >> 5] = off;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (nt + 31) / 32; ++w) s += red[w];
-      red[0] = s;
-    }
-    __syncthreads();
-    const double off_tot = red[0];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = dia;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (nt + 31) / 32; ++w) s += red[w];
-      done = (off_tot <= 1e-26 * s) || off_tot == 0.0;
-    }
-    __syncthreads();
-    if (done) break;
-    for (int step = 0; step < ne - 1; ++step) {
-      // pairs of this step and their rotations
-      for (int i = tid; i < np; i += nt) {
-        int p, q;
-        if (i == 0) {
-          p = ne - 1;
-          q = step;
-        } else {
-          p = (step + i) % (ne - 1);
-          q = (step - i + (ne - 1)) % (ne - 1);
-        }
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          const double apq = A[(long long)p * n + q];
-          const double app = A[(long long)p * n + p], aqq = A[(long long)q * n + q];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        pairs[2 * i] = p;
-        pairs[2 * i + 1] = q;
-        cs[2 * i] = c;
-        cs[2 * i + 1] = s;
-      }
-      __syncthreads();
-      // A <- A J (columns p, q of every row)
-      for (int e = tid; e < np * n; e += nt) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pairs[2 * i], q = pairs[2 * i + 1];
-        if (q >= n) continue;
-        const double c = cs[2 * i], s = cs[2 * i + 1];
-        const double akp = A[(long long)k * n + p], akq = A[(long long)k * n + q];
-        A[(long long)k * n + p] = c * akp - s * akq;
-        A[(long long)k * n + q] = s * akp + c * akq;
-        const double vkp = V[(long long)k * n + p], vkq = V[(long long)k * n + q];
-        V[(long long)k * n + p] = c * vkp - s * vkq;
-        V[(long long)k * n + q] = s * vkp + c * vkq;
-      }
-      __syncthreads();
-      // A <- J' A (rows p, q of every column)
-      for (int e = tid; e < np * n; e += nt) {
-        const int i = e / n, k = e - (e / n) * n;
-        const int p = pairs[2 * i], q = pairs[2 * i + 1];
-        if (q >= n) continue;
-        const double c = cs[2 * i], s = cs[2 * i + 1];
-        const double apk = A[(long long)p * n + k], aqk = A[(long long)q * n + k];
-        A[(long long)p * n + k] = c * apk - s * aqk;
-        A[(long long)q * n + k] = s * apk + c * aqk;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Pair (p, q), p < q, of position i (0 <= i < ne / 2) at step `step` of a sweep:
-// the round-robin schedule of k_jacobi (ne even; q == n marks the dummy of odd n).
+// Pair (p, q), p < q, of position i (0 <= i < ne / 2) at step `step` of a sweep of
+// the round-robin (circle) schedule: ne / 2 disjoint pairs per step, ne - 1 steps
+// (ne even; q == n marks the dummy of odd n).
 __device__ __forceinline__ void rr_pair(int ne, int step, int i, int& p, int& q) {
   const int m = ne - 1;
   if (i == 0) {
@@ -1175,6 +1070,319 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
   return FPCA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Dense symmetric eigensolver (n <= 1024): block Jacobi in FP32, then the
+// Ogita-Aishima refinement in FP64.
+// ---------------------------------------------------------------------------
+// A one-block cyclic Jacobi keeps every rotation step of an n x n matrix on one
+// SM, and one SM's FP64 rate and its round trips to memory make that take
+// hundreds of milliseconds at n = 256.  The two-sided block Jacobi method spreads
+// it: the indices are cut into blocks of BJ_S, and each round pairs the blocks
+// (round-robin, nb - 1 rounds per sweep); per pair (I, J) one CTA diagonalises the
+// 2 BJ_S x 2 BJ_S subproblem A[I u J, I u J] in shared memory (rr_jacobi_f32, a few
+// sweeps) into an orthogonal J_IJ; then A <- J' A J (a J_a' A[P_a, P_b] J_b product
+// per pair of pairs) and V <- V J spread over the whole GPU.  All of it in FP32;
+// the eigenvectors X = V then go through the FP64 refinement steps of Ogita and
+// Aishima (as launch_jacobi_rr), each of which squares the error, on the original
+// FP64 matrix.  n is padded to a multiple of 2 BJ_S with zero rows and columns,
+// which no rotation mixes with the real indices (their coupling is exactly zero).
+constexpr int BJ_S = 16;
+constexpr int BJ_W = 2 * BJ_S;  // subproblem width
+
+inline int bj_ne(int n) { return (n + BJ_W - 1) / BJ_W * BJ_W; }
+
+// local index i of the subproblem of pair (I, J) -> global index
+__device__ __forceinline__ int bj_index(int I, int J, int i) {
+  return i < BJ_S ? I * BJ_S + i : J * BJ_S + (i - BJ_S);
+}
+
+__global__ void k_bj_init(int n, int ne, const double* __restrict__ A64, float* __restrict__ A,
+                          float* __restrict__ V, int* __restrict__ done) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)ne * ne;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ne), j = (int)(e - (long long)i * ne);
+    A[e] = (i < n && j < n) ? (float)(0.5 * (A64[(long long)i * n + j] + A64[(long long)j * n + i])) : 0.f;
+    V[e] = i == j ? 1.f : 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0;
+}
+
+// One CTA per block pair of the round: diagonalise the subproblem, write its
+// rotation J (BJ_W x BJ_W, row-major) to Jg[pair].
+__global__ void __launch_bounds__(1024)
+    k_bj_sub(int ne, int round, const float* __restrict__ A, float* __restrict__ Jg,
+             const int* __restrict__ done) {
+  __shared__ float a0[BJ_W * (BJ_W + 1)], a1[BJ_W * (BJ_W + 1)], vs[BJ_W * (BJ_W + 1)];
+  __shared__ float red[64], cs[64];
+  __shared__ int sdone;
+  if (*done) return;
+  const int nb = ne / BJ_S;
+  int I, J;
+  rr_pair(nb, round, blockIdx.x, I, J);
+  constexpr int ld = BJ_W + 1;
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    a0[i * ld + j] = A[(long long)bj_index(I, J, i) * ne + bj_index(I, J, j)];
+    vs[i * ld + j] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  rr_jacobi_f32<1>(BJ_W, a0, a1, vs, 3, 1e-12f, red, cs, &sdone);
+  __syncthreads();
+  float* out = Jg + (size_t)blockIdx.x * BJ_W * BJ_W;
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x)
+    out[e] = vs[(e / BJ_W) * ld + e % BJ_W];
+}
+
+// A[P_a, P_b] <- J_a' A[P_a, P_b] J_b for the pairs a = blockIdx.y, b = blockIdx.x.
+__global__ void __launch_bounds__(256)
+    k_bj_apply_a(int ne, int round, float* __restrict__ A, const float* __restrict__ Jg,
+                 const int* __restrict__ done) {
+  __shared__ float ja[BJ_W][BJ_W + 1], jb[BJ_W][BJ_W + 1], m[BJ_W][BJ_W + 1], t[BJ_W][BJ_W + 1];
+  if (*done) return;
+  const int nb = ne / BJ_S;
+  int Ia, Ja, Ib, Jb;
+  rr_pair(nb, round, blockIdx.y, Ia, Ja);
+  rr_pair(nb, round, blockIdx.x, Ib, Jb);
+  const float* JA = Jg + (size_t)blockIdx.y * BJ_W * BJ_W;
+  const float* JB = Jg + (size_t)blockIdx.x * BJ_W * BJ_W;
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    ja[i][j] = JA[e];
+    jb[i][j] = JB[e];
+    m[i][j] = A[(long long)bj_index(Ia, Ja, i) * ne + bj_index(Ib, Jb, j)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {  // t = M J_b
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < BJ_W; ++k) s = fmaf(m[i][k], jb[k][j], s);
+    t[i][j] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {  // J_a' t
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < BJ_W; ++k) s = fmaf(ja[k][i], t[k][j], s);
+    A[(long long)bj_index(Ia, Ja, i) * ne + bj_index(Ib, Jb, j)] = s;
+  }
+}
+
+// V[rows, P_b] <- V[rows, P_b] J_b: BJ_W rows (blockIdx.x) of pair b = blockIdx.y.
+__global__ void __launch_bounds__(256)
+    k_bj_apply_v(int ne, int round, float* __restrict__ V, const float* __restrict__ Jg,
+                 const int* __restrict__ done) {
+  __shared__ float jb[BJ_W][BJ_W + 1], m[BJ_W][BJ_W + 1];
+  if (*done) return;
+  const int nb = ne / BJ_S;
+  int Ib, Jb;
+  rr_pair(nb, round, blockIdx.y, Ib, Jb);
+  const float* JB = Jg + (size_t)blockIdx.y * BJ_W * BJ_W;
+  const int r0 = blockIdx.x * BJ_W;
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    jb[i][j] = JB[e];
+    m[i][j] = V[(long long)(r0 + i) * ne + bj_index(Ib, Jb, j)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+    const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < BJ_W; ++k) s = fmaf(m[i][k], jb[k][j], s);
+    V[(long long)(r0 + i) * ne + bj_index(Ib, Jb, j)] = s;
+  }
+}
+
+// done = 1 once the off-diagonal mass is at most tol of the diagonal mass.
+__global__ void __launch_bounds__(1024)
+    k_bj_check(int ne, const float* __restrict__ A, float tol, int* __restrict__ done) {
+  __shared__ double red[32][2];
+  double off = 0.0, dia = 0.0;
+  for (long long e = threadIdx.x; e < (long long)ne * ne; e += blockDim.x) {
+    const int i = (int)(e / ne), j = (int)(e - (long long)i * ne);
+    const double a = (double)A[e];
+    if (i == j) dia += a * a;
+    else off += a * a;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    dia += __shfl_xor_sync(0xffffffffu, dia, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = off;
+    red[threadIdx.x >> 5][1] = dia;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[w][0];
+      b += red[w][1];
+    }
+    if (a <= (double)tol * b) *done = 1;
+  }
+}
+
+// X (n x n, FP64) <- the leading n x n of V (ne x ne); As <- sym(A64).
+__global__ void k_bj_extract(int n, int ne, const float* __restrict__ V, const double* __restrict__ A64,
+                             double* __restrict__ X, double* __restrict__ As) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    X[e] = (double)V[(long long)i * ne + j];
+    As[e] = 0.5 * (A64[e] + A64[(long long)j * n + i]);
+  }
+}
+
+// Refinement pieces for n up to 1024 (one thread per column, lambda in global).
+__global__ void __launch_bounds__(1024)
+    k_oa_correction(int n, const double* __restrict__ A, const double* __restrict__ R,
+                    const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam) {
+  __shared__ double red[32][3];
+  __shared__ double delta;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lam[i] = S[(long long)i * n + i] / (1.0 - R[(long long)i * n + i]);
+  double so = 0.0, an = 0.0, rn = 0.0;
+  for (long long e = tid; e < (long long)n * n; e += nt) {
+    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    if (i != j) so += S[e] * S[e];
+    an += A[e] * A[e];
+    rn += R[e] * R[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, o);
+    an += __shfl_xor_sync(0xffffffffu, an, o);
+    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+  }
+  if ((tid & 31) == 0) {
+    red[tid >> 5][0] = so;
+    red[tid >> 5][1] = an;
+    red[tid >> 5][2] = rn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < nt / 32; ++w) {
+      a += red[w][0];
+      b += red[w][1];
+      c += red[w][2];
+    }
+    delta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+  }
+  __syncthreads();
+  for (long long e = tid; e < (long long)n * n; e += nt) {
+    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    const double gap = lam[j] - lam[i];
+    E[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lam[j] * R[e]) / gap;
+  }
+}
+
+// X <- X + X E (row i per block; the row is staged before it is written).
+__global__ void k_oa_update(int n, double* __restrict__ X, const double* __restrict__ E) {
+  extern __shared__ double xrow[];
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) xrow[j] = X[(long long)i * n + j];
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s0 = xrow[j], s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < n; k += 2) {   // two chains: dependent FP64 adds are slow here
+      s0 += xrow[k] * E[(long long)k * n + j];
+      s1 += xrow[k + 1] * E[(long long)(k + 1) * n + j];
+    }
+    if (k < n) s0 += xrow[k] * E[(long long)k * n + j];
+    X[(long long)i * n + j] = s0 + s1;
+  }
+}
+
+// Row i (block) of C = op(L) M (+ diag I): n up to 1024, two interleaved chains.
+__global__ void k_oa_rowmm(int n, const double* __restrict__ L, int tl, const double* __restrict__ M,
+                           double* __restrict__ C, double diag, double sign) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < n; k += 2) {
+      s0 += (tl ? L[(long long)k * n + i] : L[(long long)i * n + k]) * M[(long long)k * n + j];
+      s1 += (tl ? L[(long long)(k + 1) * n + i] : L[(long long)i * n + k + 1]) *
+            M[(long long)(k + 1) * n + j];
+    }
+    if (k < n) s0 += (tl ? L[(long long)k * n + i] : L[(long long)i * n + k]) * M[(long long)k * n + j];
+    C[(long long)i * n + j] = ((i == j) ? diag : 0.0) + sign * (s0 + s1);
+  }
+}
+
+inline size_t dense_eig_bytes(int n) {
+  const int ne = bj_ne(n);
+  const int npairs = ne / BJ_W;
+  return WsCarve::round(sizeof(float) * (size_t)ne * ne) * 2 +
+         WsCarve::round(sizeof(float) * (size_t)npairs * BJ_W * BJ_W) + WsCarve::round(64) +
+         5 * WsCarve::round(sizeof(double) * (size_t)n * n) + WsCarve::round(sizeof(double) * n);
+}
+
+// Eigenpairs of the symmetric n x n FP64 matrix A (n <= 1024): A <- diag(lambda),
+// V <- eigenvectors (columns), like launch_jacobi_rr.
+fpca_status launch_dense_eig(fpca_ctx* ctx, int n, double* A, double* V, void* scratch) {
+  const int ne = bj_ne(n), nb = ne / BJ_S, npairs = ne / BJ_W;
+  WsCarve c(scratch);
+  float* Af = c.take<float>((size_t)ne * ne);
+  float* Vf = c.take<float>((size_t)ne * ne);
+  float* Jg = c.take<float>((size_t)npairs * BJ_W * BJ_W);
+  int* done = c.take<int>(16);
+  const size_t nn = (size_t)n * n;
+  double* As = c.take<double>(nn);
+  double* X = c.take<double>(nn);
+  double* R = c.take<double>(nn);
+  double* U = c.take<double>(nn);
+  double* S = c.take<double>(nn);
+  double* lam = c.take<double>(n);
+  double* E = U;  // U is dead once S is formed
+  const int eb = (int)std::min<long long>(((long long)ne * ne + 255) / 256, 4096);
+  k_bj_init<<<eb, 256, 0, ctx->stream>>>(n, ne, A, Af, Vf, done);
+  FPCA_LAUNCHED(ctx, "dense_eig");
+  if (nb > 1) {
+    for (int sweep = 0; sweep < 10; ++sweep) {
+      for (int r = 0; r < nb - 1; ++r) {
+        k_bj_sub<<<npairs, 768, 0, ctx->stream>>>(ne, r, Af, Jg, done);
+        FPCA_LAUNCHED(ctx, "dense_eig");
+        k_bj_apply_a<<<dim3(npairs, npairs), 256, 0, ctx->stream>>>(ne, r, Af, Jg, done);
+        FPCA_LAUNCHED(ctx, "dense_eig");
+        k_bj_apply_v<<<dim3(ne / BJ_W, npairs), 256, 0, ctx->stream>>>(ne, r, Vf, Jg, done);
+        FPCA_LAUNCHED(ctx, "dense_eig");
+      }
+      k_bj_check<<<1, 1024, 0, ctx->stream>>>(ne, Af, 1e-12f, done);
+      FPCA_LAUNCHED(ctx, "dense_eig");
+    }
+  } else {
+    // a single subproblem holds the whole (padded) matrix
+    k_bj_sub<<<1, 768, 0, ctx->stream>>>(ne, 0, Af, Jg, done);
+    FPCA_LAUNCHED(ctx, "dense_eig");
+    k_bj_apply_v<<<dim3(ne / BJ_W, 1), 256, 0, ctx->stream>>>(ne, 0, Vf, Jg, done);
+    FPCA_LAUNCHED(ctx, "dense_eig");
+  }
+  const int xb = (int)std::min<long long>(((long long)nn + 255) / 256, 4096);
+  k_bj_extract<<<xb, 256, 0, ctx->stream>>>(n, ne, Vf, A, X, As);
+  FPCA_LAUNCHED(ctx, "dense_eig");
+  const int tpb = std::min(1024, ((n + 31) / 32) * 32);
+  for (int step = 0; step < 3; ++step) {
+    k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
+    FPCA_LAUNCHED(ctx, "dense_eig");
+    k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, As, 0, X, U, 0.0, 1.0);   // U = A X
+    FPCA_LAUNCHED(ctx, "dense_eig");
+    k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, X, 1, U, S, 0.0, 1.0);    // S = X' A X
+    FPCA_LAUNCHED(ctx, "dense_eig");
+    k_oa_correction<<<1, 1024, 0, ctx->stream>>>(n, As, R, S, E, lam);
+    FPCA_LAUNCHED(ctx, "dense_eig");
+    k_oa_update<<<n, tpb, sizeof(double) * n, ctx->stream>>>(n, X, E);
+    FPCA_LAUNCHED(ctx, "dense_eig");
+  }
+  k_rr_out<<<xb, 256, 0, ctx->stream>>>(n, lam, X, A, V);
+  FPCA_LAUNCHED(ctx, "dense_eig");
+  return FPCA_OK;
+}
+
 template <int LM, int RPT>
 void proj_launch(fpca_ctx* ctx, const ProjShape& sh, int P, int l, const float* S,
                  const float* X, float* part) {
@@ -1247,7 +1455,8 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
                       WsCarve::round(sizeof(double) * 2 * n) + WsCarve::round(sizeof(int) * 3 * n) +
                       WsCarve::round(sizeof(double) * gram_part_doubles(P, l, ctx->num_sms)) +
                       WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) +
-                      WsCarve::round(sizeof(float) * proj_part_floats(P, l, ctx->num_sms)) + 4096;
+                      WsCarve::round(sizeof(float) * proj_part_floats(P, l, ctx->num_sms)) +
+                      (full ? WsCarve::round(dense_eig_bytes(n)) : 0) + 4096;
   void* ws = fpca_workspace(ctx, need);
   if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
   WsCarve carve(ws);
@@ -1262,12 +1471,11 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   double* work = carve.take<double>((size_t)l * l);
   double* A = carve.take<double>((size_t)n * n);
   double* V = carve.take<double>((size_t)n * n);
-  double* cs = carve.take<double>(2 * n);
-  int* pairs = carve.take<int>(2 * n);
   int* order = carve.take<int>(n);
   double* part = carve.take<double>(gram_part_doubles(P, l, ctx->num_sms));
   double* rrs = carve.take<double>(5 * (size_t)l * l + l);
   float* ppart = carve.take<float>(proj_part_floats(P, l, ctx->num_sms));
+  char* dense = full ? carve.take<char>(dense_eig_bytes(n)) : nullptr;
 
   cudaMemsetAsync(trace, 0, sizeof(double), ctx->stream);
   k_matrixize<TG, TS><<<dim3((P + 31) / 32, (P + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(
@@ -1280,8 +1488,8 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
     } else {
       return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "dense eigensolver needs FP64 gamma");
     }
-    k_jacobi<<<1, 1024, 0, ctx->stream>>>(P, A, V, cs, pairs, 40);
-    FPCA_LAUNCHED(ctx, "jacobi");
+    fpca_status ds = launch_dense_eig(ctx, P, A, V, dense);
+    if (ds != FPCA_OK) return ds;
     k_eig_order<<<1, 1024, 0, ctx->stream>>>(P, A, order);
     FPCA_LAUNCHED(ctx, "eig_order");
     k_dense_vectors<<<(int)(((long long)P * k + 255) / 256), 256, 0, ctx->stream>>>(P, k, V, order,

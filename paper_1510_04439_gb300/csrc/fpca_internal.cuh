@@ -122,9 +122,16 @@ fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const in
 fpca_status launch_gram_tc(fpca_ctx* ctx, int P, int Kpad, const uint16_t* ops, int32_t* cnt,
                            float* w, float* v);
 // smooth.cu
+// scratch: NULL (the context's workspace) or smooth_mean_scratch_bytes(P) bytes of
+// device memory the call may use (256-byte aligned)
+size_t smooth_mean_scratch_bytes(int P);
 fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt,
                                const double* w, const double* v, const double* h, double* mu,
-                               uint8_t* status);
+                               uint8_t* status, void* scratch = nullptr);
+// mean-smoother CV of scattered data (smooth.cu)
+fpca_status mean_cv_run(fpca_ctx* ctx, const fpca_grid* g, int n, const int64_t* offs,
+                        const double* t, const double* y, const int32_t* fold, int nfold,
+                        const double* h, int nh, double* cv);
 fpca_status launch_sigma2(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt, const double* w,
                           const double* v2, const double* h, const double* mu, const void* gdiag,
                           int gprec, long long gstride, const int32_t* domain, double* sig_t,

@@ -598,53 +598,38 @@ __device__ __forceinline__ void load_padded_weights(const double* __restrict__ t
   }
 }
 
+// One tile of the scalar t-side sweep: s-row xs, t-plane rows [a0, a0 + HT), the
+// three phases of k_hsolve2 on the shared-memory layout below (sized by g; the
+// weights wr, wc are loaded by the caller).  `parity` is the phase of the tile
+// barrier to wait for.  Returns false if the bounded wait for the copies gave up
+// (every thread returns the same value).
 template <bool COMP, int C>
-__global__ void __launch_bounds__(NT2, 2)
-    k_hsolve2(const float* __restrict__ varr, Hs2Geom g, const double* __restrict__ tabr,
-              const double* __restrict__ tabc, const double* __restrict__ mu_raw,
-              float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep,
-              int* __restrict__ err) {
-  static_assert(C % SEG == 0 && C <= 64, "t-plane width");
-  extern __shared__ __align__(128) unsigned char hs2[];
-  __shared__ double red[NT2 / 32];
-  __shared__ __align__(8) uint64_t tile_bar;
+__device__ __forceinline__ bool hsolve2_tile(const float* __restrict__ varr, const Hs2Geom& g,
+                                             int xs, int a0, const float* wr, const float* wc,
+                                             float* mid, float* in, uint32_t bar, uint32_t parity,
+                                             const double* __restrict__ mu_raw,
+                                             float* __restrict__ gamma,
+                                             uint8_t* __restrict__ status,
+                                             const Epilogue<float>& ep, double* red,
+                                             int* __restrict__ err) {
   const int P = g.P, R = g.R;
-  float* wr = reinterpret_cast<float*>(hs2);          // [TROWS][ntr]
-  float* wc = wr + TROWS * g.ntr;                       // [TROWS][ntc]
-  float* mid = wc + TROWS * g.ntc;                      // [NMID][HT][RS]
-  float* in = mid + (size_t)NMID * HT * g.RS;           // [10][nrp][C]; later the slots
-  // (the sliding windows read input rows < HT + ntr = nrp and mid columns
-  //  < C + ntc <= RS, so every load stays inside these arrays)
   float* slots = in;                                    // [NSL][HT][SC]
-  const int xs = blockIdx.y;
-  const int a0 = blockIdx.x * HT;
   const int th = min(HT, R - a0);
   const long long PP = (long long)P * P;
-  // Gamma_hat(s, t) = Gamma_hat(t, s) exactly (one bandwidth for s and t, symmetric
-  // bins), so in half mode a block whose t-rows all lie before s has nothing to do
-  if (g.half && (a0 + th) * C <= xs) return;
-
   // input rows a0 - Tr .. a0 - Tr + nrp - 1 of the t-plane, zero outside [0, R):
   // the in-grid rows of each array are one contiguous run in global memory,
   // fetched by the TMA engine (one bulk copy per array) while the threads
-  // fill the padding rows and the weight tables.
+  // fill the padding rows.
   const int rlo = max(0, a0 - g.Tr), rhi = min(R, a0 - g.Tr + g.nrp);
   const int skip = rlo - (a0 - g.Tr);  // padding rows above the grid
   const uint32_t bytes = (uint32_t)((rhi - rlo) * C * sizeof(float));
-  const uint32_t bar = ptx::smem_u32(&tile_bar);
   if (threadIdx.x == 0) {
-    ptx::mbar_init(bar, 1);
-    ptx::fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && bytes > 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ptx::mbar_arrive_expect_tx(bar, 10 * bytes);
     for (int a = 0; a < 10; ++a)
       ptx::bulk_load(ptx::smem_u32(in + ((size_t)a * g.nrp + skip) * C),
                      varr + a * PP + (long long)xs * P + (long long)rlo * C, bytes, bar);
   }
-  load_padded_weights(tabr, g.Tr, g.ntr, wr);
-  load_padded_weights(tabc, g.Tc, g.ntc, wc);
   {
     constexpr int C4 = C / 4;
     const int padrows = g.nrp - (rhi - rlo);
@@ -665,8 +650,8 @@ __global__ void __launch_bounds__(NT2, 2)
     }
   }
   // bounded wait for the copies; the block leaves together if any thread gave up
-  const bool landed = bytes == 0 || ptx::mbar_wait(bar, 0, err);
-  if (__syncthreads_or(!landed)) return;
+  const bool landed = ptx::mbar_wait(bar, parity, err);
+  if (__syncthreads_or(!landed)) return false;
 
   // phase 1: sums across t-plane rows
   for (int it = threadIdx.x; it < NMID * C; it += NT2) {
@@ -702,6 +687,114 @@ __global__ void __launch_bounds__(NT2, 2)
   __syncthreads();
 
   tside_phase3<C, NT2>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red, mid);
+  return true;
+}
+
+template <bool COMP, int C>
+__global__ void __launch_bounds__(NT2, 2)
+    k_hsolve2(const float* __restrict__ varr, Hs2Geom g, const double* __restrict__ tabr,
+              const double* __restrict__ tabc, const double* __restrict__ mu_raw,
+              float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep,
+              int* __restrict__ err) {
+  static_assert(C % SEG == 0 && C <= 64, "t-plane width");
+  extern __shared__ __align__(128) unsigned char hs2[];
+  __shared__ double red[NT2 / 32];
+  __shared__ __align__(8) uint64_t tile_bar;
+  float* wr = reinterpret_cast<float*>(hs2);          // [TROWS][ntr]
+  float* wc = wr + TROWS * g.ntr;                       // [TROWS][ntc]
+  float* mid = wc + TROWS * g.ntc;                      // [NMID][HT][RS]
+  float* in = mid + (size_t)NMID * HT * g.RS;           // [10][nrp][C]; later the slots
+  // (the sliding windows read input rows < HT + ntr = nrp and mid columns
+  //  < C + ntc <= RS, so every load stays inside these arrays)
+  const int xs = blockIdx.y;
+  const int a0 = blockIdx.x * HT;
+  const int th = min(HT, g.R - a0);
+  // Gamma_hat(s, t) = Gamma_hat(t, s) exactly (one bandwidth for s and t, symmetric
+  // bins), so in half mode a block whose t-rows all lie before s has nothing to do
+  if (g.half && (a0 + th) * C <= xs) return;
+  const uint32_t bar = ptx::smem_u32(&tile_bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(bar, 1);
+    ptx::fence_mbar_init();
+  }
+  load_padded_weights(tabr, g.Tr, g.ntr, wr);
+  load_padded_weights(tabc, g.Tc, g.ntc, wc);
+  __syncthreads();
+  hsolve2_tile<COMP, C>(varr, g, xs, a0, wr, wc, mid, in, bar, 0, mu_raw, gamma, status, ep, red,
+                        err);
+}
+
+// The CV grid's (bandwidth, fold) items through the scalar sweep in one
+// persistent launch: CTAs pull tiles (item-major, then s-row, then t1 block)
+// from a counter and run hsolve2_tile on each; the shared memory is sized for the
+// widest window of the grid.  Per item: its s-side arrays, tap tables and geometry,
+// and the epilogue of its fold (CV terms into its own accumulators).
+struct CvGridItem {
+  const float* varr;
+  const double* tab;   // per-axis tables (TROWS x TW each) of the item's bandwidth
+  Hs2Geom g;
+  Epilogue<float> ep;
+  int item;            // index of the item (escalation queue)
+};
+
+template <bool COMP, int C>
+__global__ void __launch_bounds__(NT2, 2)
+    k_hsolve2_grid(const CvGridItem* __restrict__ items, int nitems, int nblk,
+                   unsigned* __restrict__ counter, int ntr_max, int ntc_max, int rs_max,
+                   int* __restrict__ esc_item, int* __restrict__ err) {
+  static_assert(C % SEG == 0 && C <= 64, "t-plane width");
+  extern __shared__ __align__(128) unsigned char hs2g[];
+  __shared__ double red[NT2 / 32];
+  __shared__ __align__(8) uint64_t tile_bar;
+  __shared__ int work;
+  float* wr = reinterpret_cast<float*>(hs2g);           // [TROWS][ntr_max]
+  float* wc = wr + TROWS * ntr_max;                       // [TROWS][ntc_max]
+  float* mid = wc + TROWS * ntc_max;                      // [NMID][HT][rs_max]
+  float* in = mid + (size_t)NMID * HT * rs_max;           // [10][nrp][C]; later the slots
+  const uint32_t bar = ptx::smem_u32(&tile_bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(bar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  int cur = -1;  // item whose weights are in shared memory
+  uint32_t parity = 0;
+  const int total = nitems * nblk;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int w = (int)atomicAdd(counter, 1u);
+      // skip tiles with nothing to do (half mode) without a barrier each
+      while (w < total) {
+        const int it = w / nblk, r = w - it * nblk;
+        const Hs2Geom& g = items[it].g;
+        const int nb = (g.R + HT - 1) / HT;
+        const int xs = r / nb, a0 = (r - xs * nb) * HT;
+        const int th = min(HT, g.R - a0);
+        if (!(g.half && (a0 + th) * C <= xs)) break;
+        w = (int)atomicAdd(counter, 1u);
+      }
+      work = w;
+    }
+    __syncthreads();
+    const int w = work;
+    if (w >= total) break;
+    const int it = w / nblk, r = w - it * nblk;
+    const CvGridItem& I = items[it];
+    const int nb = (I.g.R + HT - 1) / HT;
+    const int xs = r / nb, a0 = (r - xs * nb) * HT;
+    if (it != cur) {
+      load_padded_weights(I.tab, I.g.Tr, I.g.ntr, wr);
+      load_padded_weights(I.tab + TROWS * TW, I.g.Tc, I.g.ntc, wc);
+      cur = it;
+    }
+    Epilogue<float> ep = I.ep;
+    if (ep.esc_count) ep.esc_idx_item = esc_item, ep.esc_item_id = I.item;
+    if (!hsolve2_tile<COMP, C>(I.varr, I.g, xs, a0, wr, wc, mid, in, bar, parity, nullptr,
+                               nullptr, nullptr, ep, red, err))
+      return;
+    parity ^= 1u;
+    __syncthreads();  // the slots alias the next tile's input rows
+  }
 }
 
 // NO outputs x NP powers along a line from one sliding window:
@@ -987,12 +1080,15 @@ size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
 __global__ void __launch_bounds__(256)
     k_escalated(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
                 const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,
-                float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep,
-                int half) {
+                float* __restrict__ gamma, uint8_t* __restrict__ status, Epilogue<float> ep0,
+                int half, const CvGridItem* __restrict__ items = nullptr,
+                const int* __restrict__ esc_item = nullptr) {
   const unsigned n = min(*esc_count, (unsigned)cap);
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const float* sl = esc_slots + (size_t)e * NSL;
     const int2 id = esc_idx[e];
+    // batched CV grid: the queued point's own item (its fold's epilogue)
+    const Epilogue<float>& ep = items ? items[esc_item[e]].ep : ep0;
     // the 5 x 5 system in float-float: symmetric elimination in the order of
     // elim_solve, pivot ratios against the original diagonal, inverses of the
     // pivots reused by the back substitution
@@ -1461,9 +1557,15 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
 
 }  // namespace
 
+size_t smooth_mean_scratch_bytes(int P) {
+  const size_t tb = (sizeof(double) * 3 * TROWS * TW + 255) & ~size_t(255);
+  const size_t stack = (sizeof(double) * (size_t)MJ_MAX * P + 255) & ~size_t(255);
+  return tb + 2 * stack;
+}
+
 fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt,
                                const double* w, const double* v, const double* h, double* mu,
-                               uint8_t* status) {
+                               uint8_t* status, void* scratch) {
   const int P = grid_P(g);
   for (int k = 0; k < g->d; ++k)
     if (g->m[k] > TMAX + 1)
@@ -1538,10 +1640,12 @@ fpca_status launch_smooth_mean(fpca_ctx* ctx, const fpca_grid* g, const int32_t*
     const int e[3] = {0, 0, 0};
     ix.n = find(2, e);
   }
-  // workspace: taps table and two ping-pong stacks of MJ_MAX arrays
+  // workspace (or the caller's scratch): taps table and two ping-pong stacks of
+  // MJ_MAX arrays
   const size_t tb = (sizeof(double) * 3 * TROWS * TW + 255) & ~size_t(255);
   const size_t stack = (sizeof(double) * (size_t)MJ_MAX * P + 255) & ~size_t(255);
-  char* base = static_cast<char*>(fpca_workspace(ctx, tb + 2 * stack));
+  char* base = scratch ? static_cast<char*>(scratch)
+                       : static_cast<char*>(fpca_workspace(ctx, tb + 2 * stack));
   if (!base) return fpca_fail(ctx, FPCA_E_OOM, "workspace");
   double* tabw = reinterpret_cast<double*>(base);
   double* bufA = reinterpret_cast<double*>(base + tb);
@@ -1609,4 +1713,157 @@ fpca_status smooth_cov_run(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins
                                          static_cast<float*>(gamma), status, y, cv);
   return smooth_cov_typed<float, false>(ctx, g, bins, h, nh, mu_raw, omega, l,
                                         static_cast<float*>(gamma), status, y, cv);
+}
+
+// ---------------------------------------------------------------------------
+// cross-validation of the mean smoother (Eq. 2.3), scattered data
+// ---------------------------------------------------------------------------
+// Subject-level K-fold: for fold f the mean is fitted (the smoother above) on
+// the mean bins of the other folds and scored on fold f's observations at their
+// bin centres, weights 1/N_i: sum over bins of V2_f - 2 mu V_f + mu^2 W_f where
+// the fit is not EMPTY, normalised by the held-out weight scored; +inf when
+// EMPTY bins hold more than 1% of the held-out weight.
+namespace {
+
+__device__ __forceinline__ int mcv_bin(const double* t, int d, const int* m) {
+  int flat = 0;
+  for (int k = 0; k < d; ++k) {
+    const double x = floor(__dmul_rn(t[k], (double)m[k]));
+    const int ik = (int)fmin(fmax(x, 0.0), (double)(m[k] - 1));
+    flat = flat * m[k] + ik;
+  }
+  return flat;
+}
+
+// Mean bins of every fold: subject i adds to slice fold[i] (cnt, w, v, v2 are F x P).
+__global__ void k_bin_mean_folds(int n, long long N, int d, int m0, int m1, int m2, int P,
+                                 const int64_t* __restrict__ offs, const double* __restrict__ t,
+                                 const double* __restrict__ y, const int32_t* __restrict__ fold,
+                                 int nfold, int32_t* cnt, double* w, double* v, double* v2,
+                                 int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m[3] = {m0, m1, m2};
+  const int64_t lo = offs[i], hi = offs[i + 1];
+  const int f = fold[i];
+  if (lo < 0 || hi < lo || hi > N || f < 0 || f >= nfold) {
+    atomicExch(err, DERR_BOUNDS);
+    return;
+  }
+  if (hi == lo) return;
+  const double wi = 1.0 / (double)(hi - lo);
+  const size_t base = (size_t)f * P;
+  for (int64_t j = lo; j < hi; ++j) {
+    const size_t b = base + mcv_bin(t + j * d, d, m);
+    const double yy = y[j];
+    atomicAdd(cnt + b, 1);
+    atomicAdd(w + b, wi);
+    atomicAdd(v + b, __dmul_rn(wi, yy));
+    atomicAdd(v2 + b, __dmul_rn(wi, __dmul_rn(yy, yy)));
+  }
+}
+
+// Training bins of fold f: the sums over all folds minus fold f's.
+__global__ void k_mean_train(int P, int F, int f, const int32_t* __restrict__ cnt,
+                             const double* __restrict__ w, const double* __restrict__ v,
+                             int32_t* __restrict__ ct, double* __restrict__ wt,
+                             double* __restrict__ vt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  int c = 0;
+  double sw = 0.0, sv = 0.0;
+  for (int q = 0; q < F; ++q) {  // pooled sums in fold order (the same order every fold)
+    c += cnt[(size_t)q * P + p];
+    sw += w[(size_t)q * P + p];
+    sv += v[(size_t)q * P + p];
+  }
+  ct[p] = c - cnt[(size_t)f * P + p];
+  wt[p] = sw - w[(size_t)f * P + p];
+  vt[p] = sv - v[(size_t)f * P + p];
+}
+
+// Held-out terms of fold f against the fit mu (status st): acc[0] += error,
+// acc[1] += scored weight, acc[2] += weight on EMPTY fits.
+__global__ void k_mean_cv_terms(int P, const double* __restrict__ mu, const uint8_t* __restrict__ st,
+                                const double* __restrict__ wf, const double* __restrict__ vf,
+                                const double* __restrict__ v2f, double* __restrict__ acc) {
+  __shared__ double red[256 / 32];
+  double e = 0.0, win = 0.0, wout = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    if (st[p] == FPCA_PT_EMPTY) {
+      wout += wf[p];
+    } else {
+      const double g = mu[p];
+      e += v2f[p] - 2.0 * g * vf[p] + g * g * wf[p];
+      win += wf[p];
+    }
+  }
+  const double s0 = block_sum<256>(e, red);
+  const double s1 = block_sum<256>(win, red);
+  const double s2 = block_sum<256>(wout, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(acc + 0, s0);
+    atomicAdd(acc + 1, s1);
+    atomicAdd(acc + 2, s2);
+  }
+}
+
+}  // namespace
+
+fpca_status mean_cv_run(fpca_ctx* ctx, const fpca_grid* g, int n, const int64_t* offs,
+                        const double* t, const double* y, const int32_t* fold, int nfold,
+                        const double* h, int nh, double* cv) {
+  const int P = grid_P(g), F = nfold, d = g->d;
+  for (int k = 0; k < d; ++k)
+    if (g->m[k] > TMAX + 1)
+      return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "mean smoothing is built for m <= %d", TMAX + 1);
+  long long Nobs = 0;
+  if (cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return fpca_check_launch(ctx, "mean_cv: offsets");
+  const size_t need = WsCarve::round(smooth_mean_scratch_bytes(P)) +
+                      WsCarve::round(sizeof(int32_t) * (size_t)F * P) +
+                      3 * WsCarve::round(sizeof(double) * (size_t)F * P) +
+                      WsCarve::round(sizeof(int32_t) * P) + 3 * WsCarve::round(sizeof(double) * P) +
+                      WsCarve::round(P) + WsCarve::round(sizeof(double) * 3 * (size_t)nh * F) + 4096;
+  void* ws = fpca_workspace(ctx, need);
+  if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
+  WsCarve c(ws);
+  char* scratch = c.take<char>(smooth_mean_scratch_bytes(P));
+  int32_t* fc = c.take<int32_t>((size_t)F * P);
+  double* fw = c.take<double>((size_t)F * P);
+  double* fv = c.take<double>((size_t)F * P);
+  double* fv2 = c.take<double>((size_t)F * P);
+  int32_t* ct = c.take<int32_t>(P);
+  double* wt = c.take<double>(P);
+  double* vt = c.take<double>(P);
+  double* mu = c.take<double>(P);
+  uint8_t* st = c.take<uint8_t>(P);
+  double* acc = c.take<double>((size_t)3 * nh * F);
+  cudaMemsetAsync(fc, 0, sizeof(int32_t) * (size_t)F * P, ctx->stream);
+  cudaMemsetAsync(fw, 0, sizeof(double) * (size_t)F * P, ctx->stream);
+  cudaMemsetAsync(fv, 0, sizeof(double) * (size_t)F * P, ctx->stream);
+  cudaMemsetAsync(fv2, 0, sizeof(double) * (size_t)F * P, ctx->stream);
+  cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)nh * F, ctx->stream);
+  k_bin_mean_folds<<<(n + 127) / 128, 128, 0, ctx->stream>>>(
+      n, Nobs, d, g->m[0], d > 1 ? g->m[1] : 1, d > 2 ? g->m[2] : 1, P, offs, t, y, fold, F, fc,
+      fw, fv, fv2, ctx->d_err);
+  FPCA_LAUNCHED(ctx, "bin_mean_folds");
+  const int nb = (P + 255) / 256;
+  for (int f = 0; f < F; ++f) {
+    k_mean_train<<<nb, 256, 0, ctx->stream>>>(P, F, f, fc, fw, fv, ct, wt, vt);
+    FPCA_LAUNCHED(ctx, "mean_train");
+    for (int ih = 0; ih < nh; ++ih) {
+      fpca_status s = launch_smooth_mean(ctx, g, ct, wt, vt, h + (size_t)ih * d, mu, st, scratch);
+      if (s != FPCA_OK) return s;
+      k_mean_cv_terms<<<std::min(nb, 64), 256, 0, ctx->stream>>>(
+          P, mu, st, fw + (size_t)f * P, fv + (size_t)f * P, fv2 + (size_t)f * P,
+          acc + 3 * ((size_t)ih * F + f));
+      FPCA_LAUNCHED(ctx, "mean_cv_terms");
+    }
+  }
+  k_cv_finish<<<(nh + 63) / 64, 64, 0, ctx->stream>>>(nh, F, acc, cv);
+  FPCA_LAUNCHED(ctx, "cv_finish");
+  return FPCA_OK;
 }

@@ -293,6 +293,8 @@ struct Epilogue {
   // its (xs, xt).
   float* esc_slots;
   int2* esc_idx;
+  int* esc_idx_item;   // batched CV grid: the item of each queued point, or NULL
+  int esc_item_id;
   unsigned* esc_count;
   int esc_cap;
 };
@@ -375,6 +377,7 @@ __device__ __forceinline__ void tside_phase3(const float* __restrict__ slots, in
         float* dst = ep.esc_slots + (size_t)slot * NSL;
         for (int q = 0; q < NSL; ++q) dst[q] = sl[(size_t)q * HT * SC];
         ep.esc_idx[slot] = make_int2(xs, xt);
+        if (ep.esc_idx_item) ep.esc_idx_item[slot] = ep.esc_item_id;
         continue;  // the escalation kernel writes this point and its epilogue terms
       }
       // queue full: solve here

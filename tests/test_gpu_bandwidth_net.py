@@ -4,6 +4,8 @@ Tolerances: forward outputs rel <= 1e-4, gradient rel-L2 <= 1e-3 (FP32
 accumulation against FP64 at the same FP16-rounded weights), one AdamW step
 rel <= 1e-5 where the gradient is not negligible, features abs <= 1e-4.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -167,12 +169,19 @@ def test_features_vs_oracle(ctx, kind):
 
 def test_bandwidth_workflow_small(ctx):
     """Labels, training and the proposal + check evaluation end to end on a few datasets:
-    the batched CV grid agrees with single-bandwidth CV calls, labels are the grid argmin,
-    and the evaluation rows are complete."""
+    the batched CV grids agree with single-bandwidth CV calls, labels are the grid
+    argmins of both smoothers (the covariance one on bins at the mean's best
+    bandwidth), and the evaluation rows are complete."""
     from paper_1510_04439_gb300 import bandwidth as bw
     lab = bw.Labeller(ctx, torch)
     ds = bw.draw_dataset(11)
     prep = lab.prepare(ds)
+    gm = host(lab.mean_cv(prep, bw.HGRID))
+    for j in (0, 7, 15):
+        one = host(lab.mean_cv(prep, [bw.HGRID[j]]))[0]
+        assert (not np.isfinite(gm[j]) and not np.isfinite(one)) or abs(one - gm[j]) <= 1e-12 * abs(gm[j])
+    jm = int(np.argmin(np.where(np.isfinite(gm), gm, np.inf)))
+    lab.cov_bins(prep, bw.HGRID[jm])
     grid = host(lab.cv(prep, bw.HGRID))
     for j in (0, 7, 15):
         one = host(lab.cv(prep, [bw.HGRID[j]]))[0]
@@ -182,39 +191,52 @@ def test_bandwidth_workflow_small(ctx):
             assert not np.isfinite(one)
     X, Y, M, best = bw.make_table(ctx, torch, [11, 12, 13, 14])
     assert X.shape == (4, 32) and np.isfinite(X).all()
-    assert best[0] == int(np.argmin(np.where(np.isfinite(grid), grid, np.inf)))
+    assert best[0, 0] == jm
+    assert best[0, 1] == int(np.argmin(np.where(np.isfinite(grid), grid, np.inf)))
     for k in range(4):
         d = int(round(X[k, 0]))
-        assert M[k, 3:3 + d].all() and not M[k, :3].any() and not M[k, 3 + d:].any()
-        assert np.allclose(Y[k, 3:3 + d], np.log(bw.HGRID[best[k]]))
+        assert M[k, :d].all() and not M[k, d:3].any()
+        assert M[k, 3:3 + d].all() and not M[k, 3 + d:].any()
+        assert np.allclose(Y[k, :d], np.log(bw.HGRID[best[k, 0]]))
+        assert np.allclose(Y[k, 3:3 + d], np.log(bw.HGRID[best[k, 1]]))
     Xs, mu, sd = bw.standardize(X)
     th, hist = bw.train(ctx, torch, Xs, Y, M, epochs=20, batch=4)
     assert hist[-1] < hist[0]
-    rows = bw.evaluate(ctx, torch, th, mu, sd, [21, 22])
+    const = bw.median_labels(Y, M, np.rint(X[:, 0]).astype(int))
+    rows = bw.evaluate(ctx, torch, th, mu, sd, [21, 22], const=const)
     assert len(rows) == 2
     for r in rows:
-        assert bw.HGRID[0] <= r["prop_h"] <= bw.HGRID[-1]
+        assert bw.HGRID[0] * 0.8 <= r["final_h"] <= bw.HGRID[-1] * 1.25
         if r["fallback"]:
             assert r["final_score"] == r["grid_best"]
+        assert np.isfinite(r["sine_const"]) and np.isfinite(r["fpca_const"])
 
 
 @pytest.mark.slow
 def test_learned_bandwidth_gain(ctx):
     """What the trained network gains: on held-out datasets the whole FPCA with the
-    learned proposal (plus its 3-bandwidth CV check) is faster than the 16-bandwidth
-    CV grid, its CV score stays within 5% of the grid optimum, and its eigenfunctions
-    are as accurate as the grid method's (subspace sine against the truth)."""
+    learned proposals (each with its 3-bandwidth CV check) is faster than the
+    16-bandwidth CV grids, its covariance CV score stays within 5% of the grid
+    optimum, its eigenfunctions are as accurate as the grid method's (subspace sine
+    against the truth), and it beats the constant proposal (the median training
+    labels through the same checks) on accuracy or on time."""
     from paper_1510_04439_gb300 import bandwidth as bw
     X, Y, M, _ = bw.make_table(ctx, torch, np.arange(300))
     Xs, mu, sd = bw.standardize(X)
     th, hist = bw.train(ctx, torch, Xs, Y, M, epochs=150)
     assert hist[-1] < 0.2 * hist[0]
-    rows = bw.evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(24))
+    const = bw.median_labels(Y, M, np.rint(X[:, 0]).astype(int))
+    rows = bw.evaluate(ctx, torch, th, mu, sd, 10 ** 6 + np.arange(40), const=const)
     s = bw.summarize(rows)
+    print(json.dumps(s))
     assert s["within5"] >= 0.9, s
     assert s["fpca_learned_s"] < s["fpca_grid_s"], s
     assert s["sine_learned_median"] <= s["sine_grid_median"] + 0.02, s
     assert s["sine_grid_median"] < 0.5, s          # the fits do recover the eigenfunctions
+    c = s["constant_proposal"]
+    better_accuracy = (s["within5"] > c["within5"] or s["fallback_rate"] < c["fallback_rate"]
+                       or s["sine_learned_mean"] < c["sine_mean"])
+    assert better_accuracy or s["fpca_learned_s"] < c["fpca_s"], s
     for r in rows:
         assert np.isfinite(r["sine_grid"]) and np.isfinite(r["sine_learned"])
 

@@ -121,7 +121,8 @@ def test_sparse_64x64_fold_fits_and_cv_vs_oracle(hh, npts):
     err = win = wout = 0.0
     for f in range(F):
         # the GPU's fit on the training bins of fold f (pooled minus fold f)
-        Ct, Wt, Vt = (x.sum(0) - x[f] for x in (Cg, Wg, Vg))
+        Ct = (Cg.sum(0) - Cg[f]).to(torch.int32)   # torch sums int32 into int64
+        Wt, Vt = (x.sum(0) - x[f] for x in (Wg, Vg))
         Gf = torch.empty(P, P, dtype=torch.float32, device=DEV)
         sf = torch.empty(P, P, dtype=torch.uint8, device=DEV)
         ctx.smooth_cov_project(m, Ct, Wt, Vt, [(hh, hh)], B.F32C, gamma=Gf, status=sf)
@@ -146,7 +147,11 @@ def test_sparse_64x64_fold_fits_and_cv_vs_oracle(hh, npts):
         ref, rst = sm.smooth_cov_points(pairs, m, (hh, hh), Ctr, Wtr, Vtr)
         gs = g[pairs[:, 0], pairs[:, 1]]
         ss = s[pairs[:, 0], pairs[:, 1]]
-        assert_status_band(ss, rst, pairs, m, (hh, hh), Ctr, Wtr, Vtr, max_mismatch=2)
+        # sparse windows (h = 0.03: 3 x 3 bins each side, ~16% of bin pairs hold a
+        # pair) often give near-singular systems: every status mismatch must lie in
+        # the pivot band FP32 moments cannot decide
+        nbad = assert_status_band(ss, rst, pairs, m, (hh, hh), Ctr, Wtr, Vtr)
+        assert nbad <= len(pairs) // 2
         ok = (rst == sm.STATUS_OK) & (ss == sm.STATUS_OK)
         assert ok.sum() > npts // 4
         assert rel_l2(gs[ok], ref[ok]) <= 1e-5
