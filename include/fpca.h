@@ -140,6 +140,26 @@ fpca_status fpca_alu_probe(fpca_ctx* ctx, int fp64, int blocks, int iters, doubl
  * grouping of the FP32 partial sums, within the stated FP32 tolerance. */
 fpca_status fpca_set_sweep_kernel(fpca_ctx* ctx, int kernel);
 
+/* Schedule of the K-fold CV grid of the FP32 d = 2 covariance smoother
+ * (fpca_smooth_cov_project with cv != NULL, fold bins, symmetric bins, no raw
+ * mean, t-planes 8, 16, 32 or 64 wide).
+ *  0  item by item: each (bandwidth, fold) item's t-side runs right after its
+ *     s-side, with the sweep kernel fpca_set_sweep_kernel selects;
+ *  1  batched: the s-side passes of every item run first, each into arrays of
+ *     its own (40 P^2 bytes per item in the context's workspace), then ONE
+ *     persistent launch of the scalar t-side sweep takes the tiles of all items
+ *     from a shared counter and scores each against its held-out fold;
+ *  2  automatic (default): on the first call for a (grid, folds, precision,
+ *     number of bandwidths, and whether the widest window's tile leaves room
+ *     for two batched CTAs per SM), the two schedules are timed on the
+ *     context's stream (after one untimed item-by-item pass) and the faster is
+ *     remembered in the context.
+ * Batched falls back to item by item when the items' arrays do not fit in 80%
+ * of the free device memory, when the widest window's tile exceeds the shared
+ * memory, or when sweep kernel 2 is forced.  Both compute the same fits and CV
+ * terms (the same sums per point, FP32 tolerance). */
+fpca_status fpca_set_cv_batch(fpca_ctx* ctx, int batch);
+
 /* Self-check of the device-side failure detection.  Launches one thread
  * that waits on an on-chip barrier (an mbarrier expecting one arrival) with
  * the bounded wait every waiting kernel of this library uses.  arrive != 0:
@@ -204,7 +224,10 @@ fpca_status fpca_smooth_mean_cv(fpca_ctx* ctx, const fpca_data* data, const fpca
  *   entries (only j == l pairs) set to zero.  prec FPCA_F64 uses FP64
  *   CUDA-core products (w, v double); FPCA_BF16 uses tcgen05 tensor cores
  *   with BF16 operands and FP32 accumulation (w, v float); counts are exact
- *   for n < 2^24.  fold/nfold/q are not used for dense data (pass NULL/0).
+ *   for n < 2^24.  FPCA_F32 uses FP32 CUDA-core products (w, v, q float; the
+ *   terms w_i R R and their sums rounded to FP32) and is the one dense
+ *   precision that takes fold/nfold and q, with the meaning they have for
+ *   sparse data; FPCA_F64 and FPCA_BF16 need fold = NULL, nfold = 0, q = NULL.
  *  Sparse data: integer-exact pair scatter; FPCA_F64 or FPCA_F32 sums.
  *   fold (length n, values 0..nfold-1) splits the pairs into nfold slices;
  *   q (may be NULL) receives sum w (R R)^2 for cross-validation.

@@ -71,8 +71,11 @@ def draw_dataset(seed):
         D = fs.make_sparse(d, m, n, lam, sigma=sigma, mean=mean, seed=seed, nfold=0)
         offs, t, y = D.offs, D.t, D.y
     fold = (np.random.default_rng(seed + 7).permutation(n) % NFOLD).astype(np.int32)
-    return dict(d=d, m=m, offs=offs, t=np.ascontiguousarray(t), y=np.ascontiguousarray(y),
-                fold=fold, specs=D.specs, lam=np.asarray(lam), seed=seed)
+    out = dict(d=d, m=m, offs=offs, t=np.ascontiguousarray(t), y=np.ascontiguousarray(y),
+               fold=fold, specs=D.specs, lam=np.asarray(lam), seed=seed)
+    if kind == "dense":   # the grid form too: its covariance bins are Gram products
+        out.update(grid_y=np.ascontiguousarray(D.y), grid_mask=np.ascontiguousarray(D.mask))
+    return out
 
 
 class Labeller:
@@ -84,7 +87,8 @@ class Labeller:
         self.dev = ctx.device
 
     def upload(self, ds):
-        return {k: self.torch.from_numpy(ds[k]).to(self.dev) for k in ("offs", "t", "y", "fold")}
+        keys = ("offs", "t", "y", "fold") + (("grid_y", "grid_mask") if "grid_y" in ds else ())
+        return {k: self.torch.from_numpy(ds[k]).to(self.dev) for k in keys}
 
     def prepare(self, ds, tensors=None):
         """Mean bins of all subjects (the smoothers' input; the mean fit comes later)."""
@@ -94,9 +98,13 @@ class Labeller:
         bufs = pipeline.alloc_sparse_cv(torch, self.dev, P, NFOLD, len(HGRID))
         t = tensors if tensors is not None else self.upload(ds)
         data = self.ctx.sparse(t["offs"], t["t"], t["y"])
+        # gridded data: covariance bins from the grid form (FP32 Gram products per
+        # fold) instead of the pair scatter of its points; the same sums
+        grid = self.ctx.dense(t["grid_y"], t["grid_mask"]) if "grid_y" in t else None
         v2 = torch.empty_like(bufs.w)
         self.ctx.bin_mean(data, m, bufs.cnt, bufs.w, bufs.v, v2)
-        return dict(bufs=bufs, tensors=t, data=data, m=m, d=len(m), v2=v2, feat=None, h_mu=None)
+        return dict(bufs=bufs, tensors=t, data=data, grid=grid, m=m, d=len(m), v2=v2, feat=None,
+                    h_mu=None)
 
     def mean_cv(self, prep, hs):
         """CV score of the mean smoother at each isotropic bandwidth in hs."""
@@ -110,7 +118,8 @@ class Labeller:
         b = prep["bufs"]
         m = prep["m"]
         self.ctx.smooth_mean(m, b.cnt, b.w, b.v, [float(h_mu)] * len(m), b.mu)
-        self.ctx.bin_cov(prep["data"], m, b.mu, B.F32, b.ccnt, b.cw, b.cv_, q=b.cq,
+        src = prep["grid"] if prep["grid"] is not None else prep["data"]
+        self.ctx.bin_cov(src, m, b.mu, B.F32, b.ccnt, b.cw, b.cv_, q=b.cq,
                          fold=prep["tensors"]["fold"], nfold=NFOLD)
         prep["h_mu"] = float(h_mu)
 

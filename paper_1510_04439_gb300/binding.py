@@ -32,6 +32,7 @@ SYMBOLS = (
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
     "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait", "fpca_set_sweep_kernel",
+    "fpca_set_cv_batch",
     "fpca_bw_mlp_init", "fpca_bw_mlp_io", "fpca_smooth_mean_cv", "fpca_alu_probe",
 )
 
@@ -113,6 +114,7 @@ def load(path=LIB_PATH):
     lib.fpca_launch_count.restype = ctypes.c_uint64
     lib.fpca_check_wait.argtypes = [vp, i32]
     lib.fpca_set_sweep_kernel.argtypes = [vp, i32]
+    lib.fpca_set_cv_batch.argtypes = [vp, i32]
     lib.fpca_alu_probe.argtypes = [vp, i32, i32, i32, dbl_p]
     lib.fpca_bw_mlp_init.argtypes = [vp, ctypes.c_uint64, vp]
     lib.fpca_smooth_mean_cv.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32,
@@ -217,6 +219,12 @@ class Context:
     def set_sweep_kernel(self, kernel):
         """0 automatic (timed once per grid and windows), 1 scalar, 2 packed pairs."""
         self._check(self.lib.fpca_set_sweep_kernel(self.h, int(kernel)))
+
+    def set_cv_batch(self, batch):
+        """K-fold CV grid schedule: True (one t-side launch for the whole grid),
+        False (item by item) or "auto" (the default: timed once, faster kept)."""
+        mode = 2 if batch == "auto" else (1 if batch else 0)
+        self._check(self.lib.fpca_set_cv_batch(self.h, mode))
 
     def bw_mlp_init(self, params, seed):
         """He-normal initial network parameters from a counter-based generator."""

@@ -245,6 +245,14 @@ fpca_status fpca_set_sweep_kernel(fpca_ctx* ctx, int kernel) {
   return FPCA_OK;
 }
 
+fpca_status fpca_set_cv_batch(fpca_ctx* ctx, int batch) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  if (batch < 0 || batch > 2)
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "CV schedule must be 0, 1 or 2 (automatic)");
+  ctx->cv_batch = batch;
+  return FPCA_OK;
+}
+
 fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive) {
   if (!ctx) return FPCA_E_INVALID_ARG;
   fpca_prof_mark(ctx);
@@ -363,9 +371,19 @@ fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* 
   if ((long long)P * P > (1ll << 31))
     return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
                      "P*P = %lld exceeds the materialised-covariance limit 2^31", (long long)P * P);
+  if (nfold < 0 || nfold > 64 || (nfold > 0 && !fold))
+    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "nfold must be 0..64 with fold ids when > 0");
   if (data->layout == FPCA_DENSE) {
+    if (prec == FPCA_F32) {
+      if (data->n >= (1 << 24))
+        return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "n >= 2^24 breaks exact FP32 pair counts");
+      return launch_cov_dense_folds(ctx, data->n, P, data->y, data->y_prec, data->mask, mu, mode,
+                                    fold, nfold, cnt, static_cast<float*>(w),
+                                    static_cast<float*>(v), static_cast<float*>(q));
+    }
     if (fold || nfold > 0 || q)
-      return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "folds and q are built for sparse data only");
+      return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
+                       "folds and q of gridded data are built for FPCA_F32 only");
     int32_t* Ni = nullptr;
     if (prec == FPCA_F64) {
       Ni = static_cast<int32_t*>(fpca_workspace(ctx, sizeof(int32_t) * data->n));
@@ -397,12 +415,10 @@ fpca_status fpca_bin_cov(fpca_ctx* ctx, const fpca_data* data, const fpca_grid* 
       return launch_gram_tc(ctx, P, Kpad, ops, cnt, static_cast<float*>(w),
                             static_cast<float*>(v));
     }
-    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "dense binning precision must be F64 or BF16");
+    return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "dense binning precision must be F64, F32 or BF16");
   }
   if (prec != FPCA_F64 && prec != FPCA_F32)
     return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "sparse binning precision must be F64 or F32");
-  if (nfold < 0 || nfold > 64 || (nfold > 0 && !fold))
-    return fpca_fail(ctx, FPCA_E_INVALID_ARG, "nfold must be 0..64 with fold ids when > 0");
   return launch_cov_sparse(ctx, data->n, grid, data->offs, data->t,
                            static_cast<const double*>(data->y), mu, mode, fold, nfold, prec, cnt,
                            w, v, q);

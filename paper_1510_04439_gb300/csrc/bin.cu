@@ -361,6 +361,243 @@ __global__ void k_cov_sparse(long long N, int P, const int64_t* __restrict__ off
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// FP32 covariance bins of gridded data, split by folds, on CUDA cores.
+// Subjects with N_i >= 2 are put in fold order (stable); each one's row gives
+// three operand rows in that order -- the mask M, the response R (zero where
+// unobserved) and R^2 -- of stride Ps (P rounded up to the tile edge, zero
+// beyond P), and its weight w_i = 1/(N_i(N_i - 1)).  Per fold f, with D_f the
+// diagonal of the fold's weights,
+//   C = M'M,  W = M' D_f M,  V = R' D_f R,  Q = (R^2)' D_f (R^2)
+// are computed 128 x 128 outputs per block, for the tile pairs on and above the
+// diagonal; the tile below is written as the transpose (all four are symmetric).
+// ---------------------------------------------------------------------------
+constexpr int FG_T = 128;   // output tile edge
+constexpr int FG_K = 16;    // subjects per pipeline stage
+constexpr int FG_NT = 256;  // threads: 16 x 16, 8 x 8 outputs each
+
+__device__ __forceinline__ int fold_slot(int i, int F, const int32_t* __restrict__ fold,
+                                         const int32_t* __restrict__ Ni, int* err) {
+  if (Ni[i] < 2) return -1;  // no pairs
+  if (!fold) return 0;
+  const int f = fold[i];
+  if (f < 0 || f >= F) {
+    atomicExch(err, DERR_BOUNDS);
+    return -1;
+  }
+  return f;
+}
+
+// Stable fold order (one block of 1024 threads): order[fstart[f] + r] is the r-th
+// subject of fold f in index order; fstart[F] is the number of subjects kept.
+__global__ void __launch_bounds__(1024)
+    k_fold_order(int n, int F, const int32_t* __restrict__ fold, const int32_t* __restrict__ Ni,
+                 int32_t* __restrict__ order, int32_t* __restrict__ fstart, int* err) {
+  __shared__ int fcount[64];
+  __shared__ int wpre[32][64];  // per warp and fold: count, then running position
+  __shared__ int base[64];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  if (tid < 64) fcount[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += 1024) {
+    const int f = fold_slot(i, F, fold, Ni, err);
+    if (f >= 0) atomicAdd(&fcount[f], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int s = 0;
+    for (int f = 0; f < F; ++f) {
+      base[f] = s;
+      fstart[f] = s;
+      s += fcount[f];
+    }
+    fstart[F] = s;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += 1024) {
+    for (int e = tid; e < 32 * 64; e += 1024) (&wpre[0][0])[e] = 0;
+    __syncthreads();
+    const int i = c0 + tid;
+    const int f = i < n ? fold_slot(i, F, fold, Ni, err) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, f);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (f >= 0 && rank == 0) wpre[wp][f] = __popc(peers);
+    __syncthreads();
+    if (tid < F) {  // exclusive prefix over the warps, fold by fold
+      int run = base[tid];
+      for (int w2 = 0; w2 < 32; ++w2) {
+        const int c = wpre[w2][tid];
+        wpre[w2][tid] = run;
+        run += c;
+      }
+      base[tid] = run;
+    }
+    __syncthreads();
+    if (f >= 0) order[wpre[wp][f] + rank] = i;
+    __syncthreads();
+  }
+}
+
+// Operand rows in fold order (block k: row k), see above; rows past fstart[F] are
+// left alone (the Gram kernel never reads them).
+__global__ void k_fold_operands(int n, int P, int Ps, int F, const void* __restrict__ y,
+                                int y_prec, const uint8_t* __restrict__ mask,
+                                const int32_t* __restrict__ Ni, const double* __restrict__ mu,
+                                int mode, const int32_t* __restrict__ order,
+                                const int32_t* __restrict__ fstart, float* __restrict__ X,
+                                float* __restrict__ ws) {
+  const int k = blockIdx.x;
+  if (k >= fstart[F]) return;
+  const int i = order[k];
+  const size_t plane = (size_t)n * Ps;
+  for (int p = threadIdx.x; p < Ps; p += blockDim.x) {
+    float m = 0.f, r = 0.f, r2 = 0.f;
+    if (p < P) {
+      const size_t idx = (size_t)i * P + p;
+      if (!mask || mask[idx]) {
+        const double yy = load_y(y, y_prec, idx);
+        const double rd = mode == FPCA_COV_RESIDUAL ? yy - mu[p] : yy;
+        m = 1.f;
+        r = (float)rd;
+        r2 = (float)(rd * rd);
+      }
+    }
+    const size_t o = (size_t)k * Ps + p;
+    X[o] = m;
+    X[plane + o] = r;
+    X[2 * plane + o] = r2;
+  }
+  if (threadIdx.x == 0) {
+    const double N = (double)Ni[i];
+    ws[k] = (float)(1.0 / (N * (N - 1.0)));
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// blockIdx.x: tile pair (bi <= bj), y: fold, z: plane (0 C, 1 W, 2 V, 3 Q).
+// Thread (ty, tx) owns rows {4ty..4ty+3, 64+4ty..} and columns {4tx.., 64+4tx..}
+// of the tile, so its shared-memory reads are float4s of consecutive addresses.
+__global__ void __launch_bounds__(FG_NT, 2)
+    k_fold_gram(int n, int P, int Ps, const float* __restrict__ X, const float* __restrict__ ws,
+                const int32_t* __restrict__ fstart, const int2* __restrict__ pairs,
+                int32_t* __restrict__ cnt, float* __restrict__ w, float* __restrict__ v,
+                float* __restrict__ q, int vec) {
+  __shared__ __align__(16) float As[2][FG_K][FG_T];
+  __shared__ __align__(16) float Bs[2][FG_K][FG_T];
+  __shared__ float Ss[2][FG_K];
+  const int2 pr = pairs[blockIdx.x];
+  const int f = blockIdx.y, z = blockIdx.z;
+  const int k0 = fstart[f], k1 = fstart[f + 1];
+  const int plane = z <= 1 ? 0 : z - 1;  // C and W from M, V from R, Q from R^2
+  const float* src = X + (size_t)plane * n * Ps;
+  const bool scaled = z > 0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int p0 = pr.x * FG_T, q0 = pr.y * FG_T;
+  // stage loader: 16 rows x 128 columns of each operand, two float4 per thread each
+  auto load = [&](int st, int kb) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * FG_NT;       // 0..511
+      const int r = e >> 5, c4 = e & 31;   // row, float4 column
+      const int k = kb + r;
+      const bool ok = k < k1;
+      const float* rowp = src + (size_t)(ok ? k : 0) * Ps;
+      cp_async16(smem_addr(&As[st][r][4 * c4]), rowp + p0 + 4 * c4, ok);
+      cp_async16(smem_addr(&Bs[st][r][4 * c4]), rowp + q0 + 4 * c4, ok);
+    }
+    if (tid < FG_K) Ss[st][tid] = (kb + tid < k1 && scaled) ? ws[kb + tid] : 1.f;
+  };
+  float2 acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  const int nchunk = (k1 - k0 + FG_K - 1) / FG_K;
+  if (nchunk > 0) load(0, k0);
+  cp_async_commit();
+  for (int c = 0; c < nchunk; ++c) {
+    const int st = c & 1;
+    if (c + 1 < nchunk) load(st ^ 1, k0 + (c + 1) * FG_K);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < FG_K; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[st][k][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[st][k][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[st][k][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[st][k][64 + 4 * tx]);
+      const float sk = Ss[st][k];
+      const float a[8] = {a0.x * sk, a0.y * sk, a0.z * sk, a0.w * sk,
+                          a1.x * sk, a1.y * sk, a1.z * sk, a1.w * sk};
+      const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                           make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float2 ai = make_float2(a[i], a[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = __ffma2_rn(ai, b[j], acc[i][j]);
+      }
+    }
+    __syncthreads();  // the stage is overwritten by the load after next
+  }
+  // epilogue: the tile (p, q) and, off the diagonal, its transpose (q, p); the
+  // p == q entries hold only j == l pairs and are zero.  vec: P % 4 == 0 and the
+  // outputs 16-byte aligned, so four consecutive columns are stored at once.
+  const long long PP = (long long)P * P;
+  const size_t fo = (size_t)f * PP;
+  auto put4 = [&](int row, int col, float4 val) {  // columns col..col+3
+    if (row >= P) return;
+    const float x[4] = {row == col ? 0.f : val.x, row == col + 1 ? 0.f : val.y,
+                        row == col + 2 ? 0.f : val.z, row == col + 3 ? 0.f : val.w};
+    const size_t o = fo + (size_t)row * P + col;
+    if (vec && col + 3 < P) {
+      if (z == 0)
+        *reinterpret_cast<int4*>(cnt + o) = make_int4(__float2int_rn(x[0]), __float2int_rn(x[1]),
+                                                      __float2int_rn(x[2]), __float2int_rn(x[3]));
+      else
+        *reinterpret_cast<float4*>((z == 1 ? w : z == 2 ? v : q) + o) =
+            make_float4(x[0], x[1], x[2], x[3]);
+      return;
+    }
+    for (int u = 0; u < 4; ++u) {
+      if (col + u >= P) break;
+      if (z == 0)
+        cnt[o + u] = __float2int_rn(x[u]);
+      else
+        (z == 1 ? w : z == 2 ? v : q)[o + u] = x[u];
+    }
+  };
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = p0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4));
+    put4(row, q0 + 4 * tx, make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y));
+    put4(row, q0 + 64 + 4 * tx, make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y));
+  }
+  if (pr.x != pr.y) {
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int j = (cc & 3) >> 1, comp = cc & 1;
+      const int jj = cc < 4 ? j : j + 2;
+      const int row = q0 + (cc < 4 ? 4 * tx + cc : 64 + 4 * tx + (cc - 4));
+      auto pick = [&](int i) { return comp ? acc[i][jj].y : acc[i][jj].x; };
+      put4(row, p0 + 4 * ty, make_float4(pick(0), pick(1), pick(2), pick(3)));
+      put4(row, p0 + 64 + 4 * ty, make_float4(pick(4), pick(5), pick(6), pick(7)));
+    }
+  }
+}
+
 }  // namespace
 
 fpca_status launch_subject_counts_dense(fpca_ctx* ctx, int n, int P, const uint8_t* mask,
@@ -476,5 +713,59 @@ fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const in
                                                      static_cast<float*>(q), ctx->d_err);
   }
   FPCA_LAUNCHED(ctx, "cov_sparse");
+  return FPCA_OK;
+}
+
+fpca_status launch_cov_dense_folds(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                   const uint8_t* mask, const double* mu, int mode,
+                                   const int32_t* fold, int nfold, int32_t* cnt, float* w,
+                                   float* v, float* q) {
+  const int F = nfold > 0 ? nfold : 1;
+  if (n == 0) {  // no subjects: every bin is empty
+    const size_t PPF = (size_t)P * P * F;
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * PPF, ctx->stream);
+    cudaMemsetAsync(w, 0, sizeof(float) * PPF, ctx->stream);
+    cudaMemsetAsync(v, 0, sizeof(float) * PPF, ctx->stream);
+    if (q) cudaMemsetAsync(q, 0, sizeof(float) * PPF, ctx->stream);
+    return fpca_check_launch(ctx, "cov_fold_gram memset");
+  }
+  const int Ps = (P + FG_T - 1) / FG_T * FG_T;
+  const int nt = Ps / FG_T;
+  const size_t need = WsCarve::round(sizeof(int32_t) * (size_t)n) * 2 +
+                      WsCarve::round(sizeof(int32_t) * 65) +
+                      WsCarve::round(sizeof(float) * 3 * (size_t)n * Ps) +
+                      WsCarve::round(sizeof(float) * (size_t)n) +
+                      WsCarve::round(sizeof(int2) * (size_t)nt * (nt + 1) / 2) + 2048;
+  void* wsp = fpca_workspace(ctx, need);
+  if (!wsp) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
+  WsCarve carve(wsp);
+  int32_t* Ni = carve.take<int32_t>(n);
+  int32_t* order = carve.take<int32_t>(n);
+  int32_t* fstart = carve.take<int32_t>(65);
+  float* X = carve.take<float>(3 * (size_t)n * Ps);
+  float* wsub = carve.take<float>(n);
+  int2* pairs = carve.take<int2>((size_t)nt * (nt + 1) / 2);
+  std::vector<int2> ph;
+  ph.reserve((size_t)nt * (nt + 1) / 2);
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = bi; bj < nt; ++bj) ph.push_back(make_int2(bi, bj));
+  // pageable source: staged before the call returns
+  if (cudaMemcpyAsync(pairs, ph.data(), sizeof(int2) * ph.size(), cudaMemcpyHostToDevice,
+                      ctx->stream) != cudaSuccess)
+    return fpca_check_launch(ctx, "fold gram tile pairs");
+  fpca_status s = launch_subject_counts_dense(ctx, n, P, mask, Ni);
+  if (s != FPCA_OK) return s;
+  k_fold_order<<<1, 1024, 0, ctx->stream>>>(n, F, nfold > 0 ? fold : nullptr, Ni, order, fstart,
+                                            ctx->d_err);
+  FPCA_LAUNCHED(ctx, "fold_order");
+  k_fold_operands<<<n, 128, 0, ctx->stream>>>(n, P, Ps, F, y, y_prec, mask, Ni, mu, mode, order,
+                                              fstart, X, wsub);
+  FPCA_LAUNCHED(ctx, "fold_operands");
+  const dim3 grid((unsigned)ph.size(), F, q ? 4 : 3);
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int vec = (P % 4 == 0 && al16(cnt) && al16(w) && al16(v) && (!q || al16(q))) ? 1 : 0;
+  k_fold_gram<<<grid, FG_NT, 0, ctx->stream>>>(n, P, Ps, X, wsub, fstart, pairs, cnt, w, v, q,
+                                                vec);
+  FPCA_LAUNCHED(ctx, "cov_fold_gram");
   return FPCA_OK;
 }

@@ -47,6 +47,11 @@ struct fpca_ctx {
   // 1 or 2 as above
   int tside_kernel = 0;
   std::map<std::array<int, 6>, int> tside_choice;
+  // schedule of the K-fold CV grid of the FP32 d = 2 smoother: 0 item by item,
+  // 1 batched (one persistent t-side launch), 2 automatic; the automatic choice
+  // per (M1, M2, folds, compensated, taps of every bandwidth) once timed: 0 or 1
+  int cv_batch = 2;
+  std::map<std::vector<int>, int> cv_choice;
 };
 
 // Device error codes written by kernels into ctx->d_err.
@@ -114,6 +119,11 @@ fpca_status launch_cov_operands_bf16(fpca_ctx* ctx, int n, int P, int Kpad, cons
 fpca_status launch_cov_dense_f64(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
                                  const uint8_t* mask, const int32_t* Ni, const double* mu,
                                  int mode, int32_t* cnt, double* w, double* v);
+// FP32 bins of gridded data split by folds (q may be NULL; nfold 0 = one slice)
+fpca_status launch_cov_dense_folds(fpca_ctx* ctx, int n, int P, const void* y, int y_prec,
+                                   const uint8_t* mask, const double* mu, int mode,
+                                   const int32_t* fold, int nfold, int32_t* cnt, float* w,
+                                   float* v, float* q);
 fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const int64_t* offs,
                               const double* t, const double* y, const double* mu, int mode,
                               const int32_t* fold, int nfold, int prec, int32_t* cnt, void* w,

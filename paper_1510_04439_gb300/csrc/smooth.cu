@@ -21,6 +21,7 @@
 // the number of non-empty bin pairs in each window.
 #include <algorithm>
 #include <array>
+#include <vector>
 #include <cmath>
 
 #include "fpca_internal.cuh"
@@ -1286,12 +1287,14 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
                            const T* v, const int32_t* sub_cnt, const T* sub_w, const T* sub_v,
                            const double* h, const double* tab, T* mids, T* varr,
                            const double* mu_raw, T* gamma, uint8_t* status, Epilogue<T> ep,
-                           bool symmetric) {
+                           bool symmetric, bool sside_only = false) {
   const int d = g->d;
   const int P = grid_P(g);
   const long long PP = (long long)P * P;
   const int Tax[2] = {host_taps(h[0], g->m[0]), d > 1 ? host_taps(h[1], g->m[1]) : 0};
   auto tabk = [&](int k) { return tab + (size_t)k * TROWS * TW; };
+  // sside_only: the s-side passes into varr and nothing else (the batched CV grid
+  // runs every item's t-side in one launch, in half mode)
   if (d == 2) {
     const int M1 = g->m[0], M2 = g->m[1];
     // Will the t-side run in half mode (FP32 sweep kernel, symmetric bins, no fused
@@ -1327,6 +1330,7 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
     if (!launch_vpass<T, COMP>(ctx, j2, 6, P, M1, M2, M2, Tax[0], tabk(0), band2))
       return fpca_check_launch(ctx, "cov_vpass_s1");
     FPCA_LAUNCHED(ctx, "cov_vpass_s1");
+    if (sside_only) return FPCA_OK;
     // t-side + solve
     if constexpr (sizeof(T) == 4) {
       Hs2Geom hg = hs2_geometry(P, M1, M2, Tax[0], Tax[1]);
@@ -1448,6 +1452,90 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
   return FPCA_OK;
 }
 
+// Shared memory of the batched CV-grid sweep: sized for the widest window of the grid.
+size_t cv_grid_smem(const fpca_grid* g, const double* h, int nh) {
+  const int P = grid_P(g), M1 = g->m[0], M2 = g->m[1];
+  int ntr = 0, ntc = 0, nrp = 0, rs = 0;
+  for (int ih = 0; ih < nh; ++ih) {
+    const Hs2Geom hg = hs2_geometry(P, M1, M2, host_taps(h[2 * ih], M1), host_taps(h[2 * ih + 1], M2));
+    ntr = std::max(ntr, hg.ntr);
+    ntc = std::max(ntc, hg.ntc);
+    nrp = std::max(nrp, hg.nrp);
+    rs = std::max(rs, hg.RS);
+  }
+  const int SC = M2 | 1;
+  const size_t in_f = (size_t)10 * nrp * M2, slot_f = (size_t)NSL * HT * SC;
+  return sizeof(float) * ((size_t)TROWS * (ntr + ntc) + (size_t)NMID * HT * rs +
+                          (in_f > slot_f ? in_f : slot_f));
+}
+
+// The t-sides of all (bandwidth, fold) items of a CV grid in one persistent launch
+// (k_hsolve2_grid), from the items' s-side arrays, then the escalated fits.
+template <bool COMP>
+fpca_status cv_grid_batched(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins* bins,
+                            const double* h, int nh, int F, const double* tab_all,
+                            const float* varr_all, double* cvacc, CvGridItem* items_d,
+                            int* esc_item, unsigned* counter, float* esc_slots, int2* esc_idx,
+                            unsigned* esc_count, int esc_cap) {
+  const int P = grid_P(g), M1 = g->m[0], M2 = g->m[1];
+  const long long PP = (long long)P * P;
+  const int nitems = nh * F;
+  const float* fw = static_cast<const float*>(bins->w);
+  const float* fv = static_cast<const float*>(bins->v);
+  const float* fq = static_cast<const float*>(bins->q);
+  std::vector<CvGridItem> items(nitems);
+  int ntr = 0, ntc = 0, rs = 0;
+  for (int ih = 0; ih < nh; ++ih) {
+    for (int f = 0; f < F; ++f) {
+      CvGridItem& it = items[ih * F + f];
+      it.varr = varr_all + (size_t)(ih * F + f) * 10 * PP;
+      it.tab = tab_all + (size_t)ih * 3 * TROWS * TW;
+      it.g = hs2_geometry(P, M1, M2, host_taps(h[2 * ih], M1), host_taps(h[2 * ih + 1], M2));
+      it.g.half = 1;
+      it.ep = Epilogue<float>{};
+      it.ep.wf = fw + (size_t)f * PP;
+      it.ep.vf = fv + (size_t)f * PP;
+      it.ep.qf = fq + (size_t)f * PP;
+      it.ep.cvacc = cvacc + 3 * ((size_t)ih * F + f);
+      it.ep.esc_slots = esc_slots;
+      it.ep.esc_idx = esc_idx;
+      it.ep.esc_count = esc_count;
+      it.ep.esc_cap = esc_cap;
+      it.item = ih * F + f;
+      ntr = std::max(ntr, it.g.ntr);
+      ntc = std::max(ntc, it.g.ntc);
+      rs = std::max(rs, it.g.RS);
+    }
+  }
+  const size_t smem = cv_grid_smem(g, h, nh);
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(items_d, items.data(), sizeof(CvGridItem) * nitems, cudaMemcpyHostToDevice,
+                      ctx->stream) != cudaSuccess)
+    return fpca_check_launch(ctx, "cv grid items");
+  cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream);
+  cudaMemsetAsync(esc_count, 0, sizeof(unsigned), ctx->stream);
+  const int nblk = ((M1 + HT - 1) / HT) * P;
+  const int per_sm = smem * 2 <= ctx->smem_optin ? 2 : 1;
+  const dim3 grid(ctx->num_sms * per_sm);
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, NT2, smem, ctx->stream>>>(items_d, nitems, nblk, counter, ntr, ntc, rs, esc_item,
+                                           ctx->d_err);
+  };
+  switch (M2) {
+    case 8: launch(k_hsolve2_grid<COMP, 8>); break;
+    case 16: launch(k_hsolve2_grid<COMP, 16>); break;
+    case 32: launch(k_hsolve2_grid<COMP, 32>); break;
+    default: launch(k_hsolve2_grid<COMP, 64>); break;
+  }
+  FPCA_LAUNCHED(ctx, "cov_cv_grid");
+  k_escalated<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(P, esc_slots, esc_idx, esc_count, esc_cap,
+                                                          nullptr, nullptr, nullptr,
+                                                          Epilogue<float>{}, 1, items_d, esc_item);
+  FPCA_LAUNCHED(ctx, "cov_escalated");
+  return FPCA_OK;
+}
+
 template <typename T, bool COMP>
 fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbins* bins,
                              const double* h, int nh, const double* mu_raw, const float* omega,
@@ -1459,22 +1547,62 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
   const int nmid = d == 2 ? 6 : 0;
   // queue of escalated FP32 fits (d = 2 FP32 kernel): up to 2^21 points
   const int esc_cap = (sizeof(T) == 4 && d == 2) ? (int)std::min<long long>(PP, 1ll << 21) : 0;
-  const size_t need = WsCarve::round(sizeof(double) * 3 * TROWS * TW) +
+  const size_t need = WsCarve::round(sizeof(double) * 3 * TROWS * TW * (size_t)nh) +
                       WsCarve::round(sizeof(T) * PP * (size_t)(nmid + narr(d))) +
                       (F > 1 ? WsCarve::round(sizeof(T) * PP) * 2 + WsCarve::round(4 * PP) : 0) +
                       WsCarve::round(sizeof(double) * 3 * (size_t)nh * F) +
                       WsCarve::round(sizeof(float) * 21 * (size_t)esc_cap) +
                       WsCarve::round(sizeof(int2) * (size_t)esc_cap) + 8192;
-  void* ws = fpca_workspace(ctx, need);
+  // The CV grid batched: every (bandwidth, fold) item keeps its s-side arrays and
+  // one persistent launch runs all their t-sides (FP32, d = 2, symmetric bins,
+  // the scalar sweep's shapes, and the items' arrays fit in free device memory).
+  const int nitems = nh * F;
+  bool batched = false;
+  size_t need_b = 0;
+  if constexpr (sizeof(T) == 4) {
+    const int M2 = d == 2 ? g->m[1] : 0;
+    if (cv && ctx->cv_batch != 0 && d == 2 && F >= 2 && bins->asym == 0 && !mu_raw &&
+        ctx->tside_kernel != 2 && (M2 == 8 || M2 == 16 || M2 == 32 || M2 == 64)) {
+      batched = cv_grid_smem(g, h, nh) <= ctx->smem_optin;
+      need_b = WsCarve::round(sizeof(float) * 10 * (size_t)PP * nitems) +
+               WsCarve::round(sizeof(CvGridItem) * (size_t)nitems) +
+               WsCarve::round(sizeof(int) * (size_t)esc_cap) + 1024;
+      size_t fr = 0, tot = 0;
+      if (batched && need + need_b > ctx->ws_bytes) {
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+          cudaGetLastError();
+          fr = 0;
+        }
+        // leave room: grow only into at most 80% of what is free
+        batched = need + need_b <= ctx->ws_bytes + (size_t)(0.8 * (double)fr);
+      }
+    }
+  }
+  void* ws = fpca_workspace(ctx, need + (batched ? need_b : 0));
+  if (!ws && batched) {
+    batched = false;
+    ws = fpca_workspace(ctx, need);
+  }
   if (!ws) return fpca_fail(ctx, FPCA_E_OOM, "workspace (%zu bytes)", need);
   WsCarve carve(ws);
-  double* tab = carve.take<double>(3 * TROWS * TW);
+  // tap tables of every bandwidth (TROWS x TW per axis, 3 axes)
+  double* tab_all = carve.take<double>(3 * TROWS * TW * (size_t)nh);
   T* mids = carve.take<T>((size_t)PP * nmid);
   T* varr = carve.take<T>((size_t)PP * narr(d));
   double* cvacc = carve.take<double>((size_t)3 * nh * F);
   float* esc_slots = carve.take<float>((size_t)21 * esc_cap);
   int2* esc_idx = carve.take<int2>((size_t)esc_cap);
   unsigned* esc_count = carve.take<unsigned>(1);
+  float* varr_all = nullptr;
+  CvGridItem* items_d = nullptr;
+  int* esc_item = nullptr;
+  unsigned* counter = nullptr;
+  if (batched) {
+    varr_all = carve.take<float>(10 * (size_t)PP * nitems);
+    items_d = carve.take<CvGridItem>(nitems);
+    esc_item = carve.take<int>(esc_cap);
+    counter = carve.take<unsigned>(4);
+  }
   auto with_queue = [&](Epilogue<T>& ep) {
     if (esc_cap > 0) {
       ep.esc_slots = reinterpret_cast<float*>(esc_slots);
@@ -1502,7 +1630,6 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
     cnt = cp;
   }
   if (y) cudaMemsetAsync(y, 0, sizeof(float) * (size_t)nh * P * l, ctx->stream);
-  if (cv) cudaMemsetAsync(cvacc, 0, sizeof(double) * 3 * (size_t)nh * F, ctx->stream);
   for (int ih = 0; ih < nh; ++ih) {
     const double* hh = h + (size_t)ih * d;
     TapParams tp{};
@@ -1511,7 +1638,8 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
       tp.m[k] = k < d ? g->m[k] : 1;
       tp.h[k] = k < d ? hh[k] : 1.0;
     }
-    k_taps<<<d, 128, 0, ctx->stream>>>(tp, tab);
+    double* tabh = tab_all + (size_t)ih * 3 * TROWS * TW;
+    k_taps<<<d, 128, 0, ctx->stream>>>(tp, tabh);
     FPCA_LAUNCHED(ctx, "taps");
     // the fit on all bins: Gamma_hat, status, projection
     if (gamma || status || y) {
@@ -1523,16 +1651,20 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
         ep.y = y + (size_t)ih * P * l;
       }
       fpca_status s = cov_smooth_one<T, COMP>(
-          ctx, g, cnt, w, v, nullptr, nullptr, nullptr, hh, tab, mids, varr, mu_raw,
+          ctx, g, cnt, w, v, nullptr, nullptr, nullptr, hh, tabh, mids, varr, mu_raw,
           gamma ? gamma + (size_t)ih * PP : nullptr, status ? status + (size_t)ih * PP : nullptr,
           ep, bins->asym == 0);
       if (s != FPCA_OK) return s;
     }
-    // K-fold CV: fit on the other folds, score the held-out fold
-    if (cv) {
-      const T* fw = static_cast<const T*>(bins->w);
-      const T* fv = static_cast<const T*>(bins->v);
-      const T* fq = static_cast<const T*>(bins->q);
+  }
+  // K-fold CV: for each (bandwidth, fold) item, fit on the other folds and score
+  // the held-out fold; item by item, or batched (all s-sides, then one t-side launch)
+  auto run_items = [&]() -> fpca_status {
+    cudaMemsetAsync(cvacc, 0, sizeof(double) * 3 * (size_t)nh * F, ctx->stream);
+    const T* fw = static_cast<const T*>(bins->w);
+    const T* fv = static_cast<const T*>(bins->v);
+    const T* fq = static_cast<const T*>(bins->q);
+    for (int ih = 0; ih < nh; ++ih) {
       for (int f = 0; f < F; ++f) {
         Epilogue<T> ep{};
         with_queue(ep);
@@ -1542,11 +1674,71 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
         ep.cvacc = cvacc + 3 * ((size_t)ih * F + f);
         fpca_status s = cov_smooth_one<T, COMP>(
             ctx, g, cnt, w, v, bins->cnt + (size_t)f * PP, fw + (size_t)f * PP,
-            fv + (size_t)f * PP, hh, tab, mids, varr, mu_raw, nullptr, nullptr, ep,
-            bins->asym == 0);
+            fv + (size_t)f * PP, h + (size_t)ih * d, tab_all + (size_t)ih * 3 * TROWS * TW, mids,
+            varr, mu_raw, nullptr, nullptr, ep, bins->asym == 0);
         if (s != FPCA_OK) return s;
       }
     }
+    return FPCA_OK;
+  };
+  auto run_batched = [&]() -> fpca_status {
+    if constexpr (sizeof(T) == 4) {
+      cudaMemsetAsync(cvacc, 0, sizeof(double) * 3 * (size_t)nh * F, ctx->stream);
+      const T* fw = static_cast<const T*>(bins->w);
+      const T* fv = static_cast<const T*>(bins->v);
+      for (int ih = 0; ih < nh; ++ih) {
+        for (int f = 0; f < F; ++f) {
+          T* vi = reinterpret_cast<T*>(varr_all) + (size_t)(ih * F + f) * 10 * PP;
+          fpca_status s = cov_smooth_one<T, COMP>(
+              ctx, g, cnt, w, v, bins->cnt + (size_t)f * PP, fw + (size_t)f * PP,
+              fv + (size_t)f * PP, h + (size_t)ih * d, tab_all + (size_t)ih * 3 * TROWS * TW,
+              mids, vi, nullptr, nullptr, nullptr, Epilogue<T>{}, true, true);
+          if (s != FPCA_OK) return s;
+        }
+      }
+      return cv_grid_batched<COMP>(ctx, g, bins, h, nh, F, tab_all, varr_all, cvacc, items_d,
+                                   esc_item, counter, esc_slots, esc_idx, esc_count, esc_cap);
+    }
+    return FPCA_OK;
+  };
+  if (cv) {
+    fpca_status st = FPCA_OK;
+    if (!batched) {
+      st = run_items();
+    } else if (ctx->cv_batch == 1) {
+      st = run_batched();
+    } else {
+      // automatic: time both schedules once per (grid, folds, precision, number of
+      // bandwidths, whether the widest window leaves room for two batched CTAs per
+      // SM) -- after one untimed item-by-item pass, so the sweep choices those items
+      // make are already settled -- and remember the faster in the context.  The
+      // key leaves the windows themselves out: the checks of nearby bandwidths on
+      // many datasets share one decision instead of each paying for the timing.
+      const int wide = 2 * cv_grid_smem(g, h, nh) > ctx->smem_optin ? 1 : 0;
+      const std::vector<int> key = {g->m[0], g->m[1], F, COMP ? 1 : 0, nh, wide};
+      auto it = ctx->cv_choice.find(key);
+      if (it == ctx->cv_choice.end()) {
+        st = run_items();
+        cudaEvent_t ev[3];
+        for (auto& x : ev) cudaEventCreate(&x);
+        cudaEventRecord(ev[0], ctx->stream);
+        if (st == FPCA_OK) st = run_batched();
+        cudaEventRecord(ev[1], ctx->stream);
+        if (st == FPCA_OK) st = run_items();
+        cudaEventRecord(ev[2], ctx->stream);
+        if (st == FPCA_OK && cudaEventSynchronize(ev[2]) != cudaSuccess)
+          st = fpca_check_launch(ctx, "CV schedule autotune");
+        float tb = 0.f, ti = 0.f;
+        cudaEventElapsedTime(&tb, ev[0], ev[1]);
+        cudaEventElapsedTime(&ti, ev[1], ev[2]);
+        for (auto& x : ev) cudaEventDestroy(x);
+        if (st != FPCA_OK) return st;
+        ctx->cv_choice.emplace(key, tb < ti ? 1 : 0);
+      } else {
+        st = it->second == 1 ? run_batched() : run_items();
+      }
+    }
+    if (st != FPCA_OK) return st;
   }
   if (cv) {
     k_cv_finish<<<(nh + 63) / 64, 64, 0, ctx->stream>>>(nh, F, cvacc, cv);

@@ -10,6 +10,10 @@ last block of t1-rows, from 7 to 39 taps, in the t >= s half mode (symmetric
 bins, mirrored), with the fused projection y = Gamma_hat Omega (every pair
 fitted) and with the K-fold CV epilogue.
 
+The K-fold CV grid also runs batched: every (bandwidth, fold) item's s-side
+arrays first, then one persistent t-side launch over all items' tiles; its
+scores are compared with the oracle and with the item-by-item path.
+
 Tolerances: FP32 moments rel-L2 <= 1e-5 on points both sides fit with the full
 local linear model; statuses equal outside the pivot band (assert_status_band);
 CV score rel 1e-4 with the same argmin; y rel-L2 <= 1e-5.
@@ -119,11 +123,13 @@ def test_sweeps_projection_epilogue(B, kern):
     assert rel_l2(y.cpu().numpy().astype(np.float64), g @ om.astype(np.float64)) <= 1e-5
 
 
-@pytest.mark.parametrize("kern", [1, 2])
-def test_sweeps_cv_epilogue(B, kern):
-    """K-fold CV scores through either sweep against the oracle's CV."""
+@pytest.mark.parametrize("kern,batch", [(1, False), (2, False), (0, True)])
+def test_sweeps_cv_epilogue(B, kern, batch):
+    """K-fold CV scores through either sweep, item by item or as one batched
+    launch over the whole (bandwidth, fold) grid, against the oracle's CV."""
     ctx = B.Context(0)
     ctx.set_sweep_kernel(kern)
+    ctx.set_cv_batch(batch)
     m = (16, 32)
     D = fs.make_sparse(2, m, 3000, [2.0, 1.0], nmin=5, nmax=20, sigma=0.5, seed=12, nfold=5)
     mu = np.linspace(-0.2, 0.3, D.P)
@@ -164,3 +170,65 @@ def test_sweep_choice_is_remembered(B):
     ctx.sync()
     assert first == second + 4      # two timing runs of each sweep, once
     assert torch.equal(G, g1)       # the remembered choice gives the same surface
+
+
+@pytest.mark.parametrize("m,comp", [((16, 64), True), ((21, 32), False), ((12, 16), True)])
+def test_cv_grid_batched_matches_items_and_oracle(B, m, comp):
+    """One launch over the whole CV grid (bandwidths of different windows on each
+    axis, so the items' tiles differ in shape) gives the item-by-item scores and
+    the oracle's; the grid kernel runs once, the per-item sweeps not at all."""
+    K = 4
+    D = fs.make_sparse(2, m, 2500, [2.0, 1.0], nmin=6, nmax=18, sigma=0.5, seed=31, nfold=K)
+    mu = np.linspace(-0.1, 0.2, D.P)
+    r = sm.residuals_sparse(D.t, D.y, mu, m)
+    C, W, V, Q = sm.bin_cov_sparse(D.offs, D.t, r, m, D.fold, K)
+    taps = [(2, 5), (4, 3), (3, 9), (6, 6)] if m[1] < 64 else [(2, 5), (3, 9)]
+    hs = [((T1 + 0.5) / m[0], (T2 + 0.5) / m[1]) for T1, T2 in taps]
+    prec = B.F32C if comp else B.F32
+    args = (m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32), hs, prec)
+    out = {}
+    for batch in (True, False):
+        ctx = B.Context(0)
+        ctx.set_sweep_kernel(1)
+        ctx.set_cv_batch(batch)
+        cv = torch.empty(len(hs), dtype=torch.float64, device=DEV)
+        ctx.profile(True)
+        ctx.smooth_cov_project(*args, q=dev(Q, torch.float32), nfold=K, cv=cv)
+        ctx.sync()
+        out[batch] = (cv.cpu().numpy(), ctx.profile_read())
+    (cb, pb), (ci, pi) = out[True], out[False]
+    assert pb["cov_cv_grid"][1] == 1 and "cov_hpass_solve" not in pb
+    assert "cov_cv_grid" not in pi and pi["cov_hpass_solve"][1] == len(hs) * K
+    ref = np.array([ocv.cv_score(m, list(h), C, W, V, Q, smooth=og.smooth_cov) for h in hs])
+    fin = np.isfinite(ref)
+    for got in (cb, ci):
+        assert np.array_equal(np.isfinite(got), fin)
+        assert np.allclose(got[fin], ref[fin], rtol=1e-4)
+    # the same sums per point: batched and item-by-item agree far inside the tolerance
+    assert np.allclose(cb[fin], ci[fin], rtol=1e-6)
+
+
+def test_cv_schedule_choice_is_remembered(B):
+    """Automatic CV schedule: the first call runs the grid item by item, then times
+    the batched and the item-by-item schedule; later calls run only the one kept,
+    with the same scores."""
+    K = 5
+    m = (16, 32)
+    D = fs.make_sparse(2, m, 1500, [2.0, 1.0], nmin=6, nmax=18, sigma=0.5, seed=7, nfold=K)
+    mu = np.zeros(D.P)
+    r = sm.residuals_sparse(D.t, D.y, mu, m)
+    C, W, V, Q = sm.bin_cov_sparse(D.offs, D.t, r, m, D.fold, K)
+    hs = [((T + 0.5) / m[0], (T + 0.5) / m[1]) for T in (2, 3, 5)]
+    ctx = B.Context(0)
+    args = (m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32), hs, B.F32C)
+    out = []
+    for _ in range(3):
+        cv = torch.empty(len(hs), dtype=torch.float64, device=DEV)
+        l0 = ctx.launches
+        ctx.smooth_cov_project(*args, q=dev(Q, torch.float32), nfold=K, cv=cv)
+        ctx.sync()
+        out.append((ctx.launches - l0, cv.cpu().numpy()))
+    (n1, c1), (n2, c2), (n3, c3) = out
+    assert n2 == n3 and n1 > 2 * n2          # three schedules' worth of launches, once
+    # (the FP64 atomic sums of the CV terms may add in another order)
+    assert np.allclose(c2, c1, rtol=1e-6) and np.allclose(c2, c3, rtol=1e-12)
