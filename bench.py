@@ -310,38 +310,98 @@ def job_value(units_per_rank, world, ms):
 
 
 # ----------------------------------------------------------------------------
-# oracle timing (CPU): Gamma_hat at sampled output pairs by window sums
+# oracle timing (CPU), the oracle as it stands on the machine's host cores
 # ----------------------------------------------------------------------------
 
-def oracle_sample_rate(seconds, min_points=20, seed=0):
-    """Points/s of the FP64 oracle's covariance smoother on this workload.
-
-    The oracle bins the full data once (not timed), then evaluates Gamma_hat
-    by its per-point window sums at random output pairs inside the domain
-    until ``seconds`` of CPU time have passed.
-    """
+def _dense_oracle_inputs():
     import numpy as np
 
     import fpca_synth as fs
     from oracle import smoother as sm
     D = fs.dense_2d_disk()
     y = D.y.astype(np.float32).astype(np.float64)
+    return D, y, sm
+
+
+def oracle_dense_rate(fit_rows=16, seed=0):
+    """Points/s of the FP64 oracle on the dense 64 x 64 step, in its fastest form:
+    mean bins and fit, covariance bins as BLAS Gram products (R'R), the separable
+    FP64 moment sums of the whole grid (oracle/grid.py: one band-matrix product
+    per axis and moment) and the stacked 5 x 5 solves (block.solve_points) on
+    ``fit_rows`` random in-domain s-rows, extrapolated per point to all P^2
+    points.  The eigendecomposition is not included.  Returns the rate and the
+    timed parts (seconds)."""
+    import numpy as np
+
+    from oracle import grid as og
+    D, y, sm = _dense_oracle_inputs()
+    P = D.P
+    t0 = time.perf_counter()
     cnt, Wm, Vm, _ = sm.bin_mean_dense(y, D.mask, D.m)
     mu, _ = sm.smooth_mean(D.m, H, cnt, Wm, Vm)
     mu = np.where(np.isnan(mu), 0.0, mu)
+    t1 = time.perf_counter()
     C, W, V = sm.bin_cov_dense(sm.residuals_dense(y, D.mask, mu), D.mask)
+    t2 = time.perf_counter()
+    S, T = og.moments(D.m, H, W, V)
+    ne = og.nonempty(D.m, H, C)
+    t3 = time.perf_counter()
+    rows = np.random.default_rng(seed).choice(np.nonzero(cnt > 0)[0], fit_rows, replace=False)
+    p = np.repeat(rows, P)
+    q = np.tile(np.arange(P), rows.size)
+    og.fit_pairs(S, T, ne, 2, p, q)
+    t4 = time.perf_counter()
+    per_point = (t4 - t3) / p.size
+    total = (t1 - t0) + (t2 - t1) + (t3 - t2) + per_point * P * P
+    parts = {"mean_s": t1 - t0, "bins_s": t2 - t1, "moments_s": t3 - t2,
+             "solve_us_per_point": per_point * 1e6, "sample_points": int(p.size),
+             "extrapolated_step_s": total, "cpu_s": t4 - t0}
+    return P * P / total, parts
+
+
+def oracle_cv_rate(parts, items):
+    """Points/s of the FP64 oracle's CV grid on the 64 x 64 grid, per fitted point,
+    derived from the dense sample's timed parts: each (bandwidth, fold) item costs
+    the oracle one whole-grid pass of separable moment sums and one stacked solve
+    per point on the same 64 x 64 grid (vectorised NumPy, so the cost does not
+    depend on the bin values); the CV terms are an elementwise sum (< 1% of it)
+    and the sparse binning is done once per grid (not counted)."""
+    P2 = 64 ** 4
+    item_s = parts["moments_s"] + parts["solve_us_per_point"] * 1e-6 * P2
+    return P2 / item_s, {"item_s": item_s, "grid_s": item_s * items,
+                         "derived_from": "the dense sample's moments_s and solve_us_per_point"}
+
+
+def oracle_fused3_rate(seconds=10.0, min_tiles=2, seed=0):
+    """Points/s of the FP64 oracle's block smoother (oracle/block.py) on the 32^3
+    workload: random 6-D tiles of 4 x 4 x 4 s-nodes by 4 x 4 x 4 t-nodes (4096
+    output pairs each) evaluated from the data until ``seconds`` have passed;
+    the mean fit is precomputed.  Extrapolated per point."""
+    import numpy as np
+
+    import fpca_synth as fs
+    from oracle import block as ob
+    from oracle import smoother as sm
+    D = fs.dense_3d()
+    h = (0.15, 0.15, 0.15)
+    y = D.y.astype(np.float32).astype(np.float64)
+    cnt, Wm, Vm, _ = sm.bin_mean_dense(y, D.mask, D.m)
+    mu, _ = sm.smooth_mean(D.m, h, cnt, Wm, Vm)
     rng = np.random.default_rng(seed)
-    inside = np.nonzero(cnt > 0)[0]
-    done = 0
+    M = D.m[0]
+    tiles = 0
     t0 = time.perf_counter()
     while True:
-        pairs = np.stack([rng.choice(inside, 10), rng.choice(inside, 10)], 1)
-        sm.smooth_cov_points(pairs, D.m, H, C, W, V)
-        done += len(pairs)
+        ls = rng.integers(0, M - 3, 3)
+        lt = rng.integers(0, M - 3, 3)
+        S = np.array([((ls[0] + a) * M + ls[1] + b) * M + ls[2] + c
+                      for a in range(4) for b in range(4) for c in range(4)])
+        ob.smooth_cov_block(y, D.mask, mu, D.m, h, S, list(lt), list(lt + 4))
+        tiles += 1
         el = time.perf_counter() - t0
-        if el >= seconds and done >= min_points:
+        if el >= seconds and tiles >= min_tiles:
             break
-    return done / el, done, el
+    return tiles * 4096 / el, {"tiles": tiles, "seconds": el}
 
 
 def workload_config():
@@ -356,21 +416,19 @@ def run_reference(args):
         return 0
     import numpy as np  # noqa: F401
 
-    import fpca_synth as fs
-    from oracle import smoother as sm
-    D = fs.dense_2d_disk()
-    y = D.y.astype(np.float32).astype(np.float64)
+    from oracle import block as ob
+    D, y, sm = _dense_oracle_inputs()
     cnt, Wm, Vm, _ = sm.bin_mean_dense(y, D.mask, D.m)
     mu, _ = sm.smooth_mean(D.m, H, cnt, Wm, Vm)
     mu = np.where(np.isnan(mu), 0.0, mu)
-    C, W, V = sm.bin_cov_dense(sm.residuals_dense(y, D.mask, mu), D.mask)
     rng = np.random.default_rng(1)
     inside = np.nonzero(cnt > 0)[0]
-    per_step = 60
+    rows_per_step = 16
+    per_step = rows_per_step * D.P
 
     def step():
-        pairs = np.stack([rng.choice(inside, per_step), rng.choice(inside, per_step)], 1)
-        sm.smooth_cov_points(pairs, D.m, H, C, W, V)
+        # Gamma_hat on whole s-rows, evaluated from the data (oracle/block.py)
+        ob.smooth_cov_rows(y, D.mask, mu, D.m, H, rng.choice(inside, rows_per_step, replace=False))
 
     for _ in range(args.warmup):
         step()
@@ -385,11 +443,13 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": dict(workload_config(), sample=f"{per_step} output pairs per step",
+        "config": dict(workload_config(), sample=f"{rows_per_step} whole s-rows ({per_step} output "
+                                                 "pairs) per step",
                        precision="FP64 oracle (binned local linear fits written out)"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 oracle window sums at {per_step} random in-domain "
-                                   "output pairs per step; bins precomputed"},
+                         "sample": f"FP64 block oracle (oracle/block.py) on {rows_per_step} "
+                                   "random in-domain s-rows per step, from the data; mean fit "
+                                   "precomputed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -700,20 +760,56 @@ def main():
         so, st_, sy, sf = (torch.from_numpy(a).to(dev) for a in (Ds.offs, Ds.t, Ds.y, Ds.fold))
         pipeline.run_sparse_cv(ctx, Ds.m, so, st_, sy, sf, Ds.nfold, (0.1, 0.1), hs, sb)
         torch.cuda.synchronize()
-        ctx.profile(True)
-        evs = []
-        for _ in range(3):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+
+        def time_cv(reps=3):
+            ctx.profile(True)
+            evs = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pipeline.run_sparse_cv(ctx, Ds.m, so, st_, sy, sf, Ds.nfold, (0.1, 0.1), hs, sb)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            pr = ctx.profile_read()
+            ctx.profile(False)
+            return sum(a.elapsed_time(b) for a, b in evs) / len(evs), pr
+
+        # the schedule the autotuner keeps, then each schedule forced (the first
+        # call above ran the tuning); the timed region is the whole CV pipeline
+        # (bins, pooled folds, every item's sweeps, the scores)
+        ms_cv, prof_cv = time_cv()
+        chosen = "batched" if "cov_cv_grid" in prof_cv else "item_by_item"
+        sched = {}
+        for name, mode in (("batched", True), ("item_by_item", False)):
+            ctx.set_cv_batch(mode)
             pipeline.run_sparse_cv(ctx, Ds.m, so, st_, sy, sf, Ds.nfold, (0.1, 0.1), hs, sb)
-            b.record(stream)
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        prof_cv = ctx.profile_read()
-        ctx.profile(False)
-        ms_cv = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+            ms_s, pr_s = time_cv()
+            top = "cov_cv_grid" if mode else ("cov_tsweep" if "cov_tsweep" in pr_s else "cov_hpass_solve")
+            t_side = pr_s.get(top, (0.0, 0))
+            sched[name] = {"ms_per_grid": ms_s, "t_side_kernel": top,
+                           "t_side_ms": t_side[0] / 3, "t_side_launches": t_side[1] // 3}
+        ctx.set_cv_batch("auto")
+        # the t-side sweeps' FP32 work over the grid: per item and evaluated (t >= s)
+        # point, 2 (15 L1 + 21 L2) + 100 flops with L the mean in-grid window lengths
+        Ms = Ds.m[0]
+        cv_flops = 0.0
+        for hh in hs:
+            Th = taps(hh, Ms)
+            cv_flops += Ds.nfold * (2.0 * 36 * mean_window(Ms, Th) + 100.0) * Ps * (Ps + 1) / 2
+        top_k = sched[chosen]["t_side_kernel"]
+        t_ms = sched[chosen]["t_side_ms"]
+        cv_roof = None
+        if t_ms > 0 and peaks and peaks.get("fp32_tflops"):
+            ach = cv_flops / (t_ms * 1e-3) / 1e12
+            cv_roof = {"kernel": top_k, "bound": "alu", "achieved": ach,
+                       "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                       "frac": ach / peaks["fp32_tflops"], "ms_t_side_per_grid": t_ms,
+                       "flops_basis": "sum over the 80 items of (2 (15 L1 + 21 L2) + 100) "
+                                      "flops x P (P + 1) / 2 evaluated points",
+                       "peak_basis": "measured FP32 FMA peak (alu_peaks_measured)"}
         scores = sb.scores.cpu().numpy()
         fits = len(hs) * Ds.nfold
         # Section 3.3's trust-region search over the (anisotropic) bandwidth vector on
@@ -724,6 +820,7 @@ def main():
                                               (hs[len(hs) // 2],) * 2)
         t_tr = time.perf_counter() - t0
         cvx = {"workload": f"sparse_2d_64x64_n{Ds.n}_5fold_16h", "ms_per_grid": ms_cv,
+               "schedule_chosen": chosen, "schedules": sched, "roofline": cv_roof,
                "fits": fits, "value": fits * float(Ps) * Ps / (ms_cv * 1e-3), "unit": UNIT,
                "best_h": hs[int(np.argmin(scores))], "best_cv": float(np.min(scores)),
                "trust_region": {"h": list(h_tr), "cv": cv_tr, "evaluations": len(tr),
@@ -760,10 +857,31 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, npts, el = oracle_sample_rate(args.cpu_seconds)
+        rate, parts = oracle_dense_rate()
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"FP64 oracle window sums at {npts} random in-domain output pairs "
-                         f"({el:.1f} s; bins precomputed, numpy default threading)"}
+               "sample": ("FP64 oracle, fastest form: mean, BLAS Gram bins and the separable "
+                          "moment sums of the whole 64x64 grid timed, stacked 5x5 solves timed "
+                          f"on {parts['sample_points']} points of random in-domain s-rows and "
+                          "extrapolated per point to all 16.8M (eigendecomposition excluded); "
+                          "numpy default threading"),
+               "parts": parts}
+        if cvx is not None:
+            rcv, pcv = oracle_cv_rate(parts, cvx["fits"])
+            cvx["cpu_baseline"] = {
+                "value": rcv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": ("derived, not timed separately: per (bandwidth, fold) item one "
+                           "whole-grid pass of the oracle's separable moment sums and stacked "
+                           "solves on the same 64x64 grid, from the dense sample's timed parts; "
+                           "per fitted point"),
+                "parts": pcv}
+        if f3x is not None:
+            r3, p3 = oracle_fused3_rate()
+            f3x["cpu_baseline"] = {
+                "value": r3, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": ("oracle/block.py on random 4x4x4 by 4x4x4 tiles of the 32^3 "
+                           "workload from the data (4096 pairs each, mean precomputed); "
+                           "extrapolated per point"),
+                "parts": p3}
 
     if rank == 0:
         kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
