@@ -1088,6 +1088,12 @@ fpca_status launch_jacobi_rr(fpca_ctx* ctx, int l, double* A, double* V, double*
 // which no rotation mixes with the real indices (their coupling is exactly zero).
 constexpr int BJ_S = 16;
 constexpr int BJ_W = 2 * BJ_S;  // subproblem width
+constexpr int BJ_SWEEPS = 12;   // sweeps at most (each ends with the convergence test)
+// The FP32 sweeps stop once the off-diagonal mass is at most this fraction of the
+// diagonal mass (off-diagonal norm 1e-4 of the diagonal's; FP32 round-off alone
+// leaves about (n eps)^2 ~ 4e-9 at n = 1024); the three FP64 refinement steps take
+// the eigenvectors from there (each squares the error: 1e-4 -> 1e-8 -> 1e-16).
+constexpr double BJ_TOL = 1e-8;
 
 inline int bj_ne(int n) { return (n + BJ_W - 1) / BJ_W * BJ_W; }
 
@@ -1126,25 +1132,50 @@ __global__ void __launch_bounds__(1024)
     vs[i * ld + j] = i == j ? 1.f : 0.f;
   }
   __syncthreads();
-  rr_jacobi_f32<1>(BJ_W, a0, a1, vs, 3, 1e-12f, red, cs, &sdone);
+  rr_jacobi_f32<1>(BJ_W, a0, a1, vs, 1, 1e-12f, red, cs, &sdone);
   __syncthreads();
   float* out = Jg + (size_t)blockIdx.x * BJ_W * BJ_W;
   for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x)
     out[e] = vs[(e / BJ_W) * ld + e % BJ_W];
 }
 
-// A[P_a, P_b] <- J_a' A[P_a, P_b] J_b for the pairs a = blockIdx.y, b = blockIdx.x.
+// One launch per round applies the round's rotations:
+//  blockIdx.y < npairs:  A[P_a, P_b] <- J_a' A[P_a, P_b] J_b (a = blockIdx.y, b = blockIdx.x);
+//                        with mass != NULL the block adds the squared off-diagonal and
+//                        diagonal entries of its new tile to mass[0], mass[1];
+//  blockIdx.y >= npairs: V[rows, P_b] <- V[rows, P_b] J_b for BJ_W rows
+//                        (row block blockIdx.y - npairs, pair b = blockIdx.x).
 __global__ void __launch_bounds__(256)
-    k_bj_apply_a(int ne, int round, float* __restrict__ A, const float* __restrict__ Jg,
-                 const int* __restrict__ done) {
+    k_bj_apply(int ne, int round, float* __restrict__ A, float* __restrict__ V,
+               const float* __restrict__ Jg, const int* __restrict__ done,
+               double* __restrict__ mass) {
   __shared__ float ja[BJ_W][BJ_W + 1], jb[BJ_W][BJ_W + 1], m[BJ_W][BJ_W + 1], t[BJ_W][BJ_W + 1];
+  __shared__ float red[8][2];
   if (*done) return;
-  const int nb = ne / BJ_S;
-  int Ia, Ja, Ib, Jb;
-  rr_pair(nb, round, blockIdx.y, Ia, Ja);
+  const int nb = ne / BJ_S, npairs = ne / BJ_W;
+  int Ib, Jb;
   rr_pair(nb, round, blockIdx.x, Ib, Jb);
-  const float* JA = Jg + (size_t)blockIdx.y * BJ_W * BJ_W;
   const float* JB = Jg + (size_t)blockIdx.x * BJ_W * BJ_W;
+  if ((int)blockIdx.y >= npairs) {
+    const int r0 = (blockIdx.y - npairs) * BJ_W;
+    for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+      const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+      jb[i][j] = JB[e];
+      m[i][j] = V[(long long)(r0 + i) * ne + bj_index(Ib, Jb, j)];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
+      const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
+      float s = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < BJ_W; ++k) s = fmaf(m[i][k], jb[k][j], s);
+      V[(long long)(r0 + i) * ne + bj_index(Ib, Jb, j)] = s;
+    }
+    return;
+  }
+  int Ia, Ja;
+  rr_pair(nb, round, blockIdx.y, Ia, Ja);
+  const float* JA = Jg + (size_t)blockIdx.y * BJ_W * BJ_W;
   for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {
     const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
     ja[i][j] = JA[e];
@@ -1160,16 +1191,41 @@ __global__ void __launch_bounds__(256)
     t[i][j] = s;
   }
   __syncthreads();
+  float off = 0.f, dia = 0.f;
   for (int e = threadIdx.x; e < BJ_W * BJ_W; e += blockDim.x) {  // J_a' t
     const int i = e / BJ_W, j = e - (e / BJ_W) * BJ_W;
     float s = 0.f;
 #pragma unroll 8
     for (int k = 0; k < BJ_W; ++k) s = fmaf(ja[k][i], t[k][j], s);
-    A[(long long)bj_index(Ia, Ja, i) * ne + bj_index(Ib, Jb, j)] = s;
+    const int gi = bj_index(Ia, Ja, i), gj = bj_index(Ib, Jb, j);
+    A[(long long)gi * ne + gj] = s;
+    if (gi == gj) dia += s * s;
+    else off += s * s;
+  }
+  if (mass) {
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5][0] = off;
+      red[threadIdx.x >> 5][1] = dia;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double so = 0.0, sd = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        so += red[w][0];
+        sd += red[w][1];
+      }
+      atomicAdd(mass, so);
+      atomicAdd(mass + 1, sd);
+    }
   }
 }
 
-// V[rows, P_b] <- V[rows, P_b] J_b: BJ_W rows (blockIdx.x) of pair b = blockIdx.y.
+// V[rows, P_b] <- V[rows, P_b] J_b (the single-subproblem case): BJ_W rows
+// (blockIdx.x) of pair b = blockIdx.y.
 __global__ void __launch_bounds__(256)
     k_bj_apply_v(int ne, int round, float* __restrict__ V, const float* __restrict__ Jg,
                  const int* __restrict__ done) {
@@ -1195,34 +1251,10 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// done = 1 once the off-diagonal mass is at most tol of the diagonal mass.
-__global__ void __launch_bounds__(1024)
-    k_bj_check(int ne, const float* __restrict__ A, float tol, int* __restrict__ done) {
-  __shared__ double red[32][2];
-  double off = 0.0, dia = 0.0;
-  for (long long e = threadIdx.x; e < (long long)ne * ne; e += blockDim.x) {
-    const int i = (int)(e / ne), j = (int)(e - (long long)i * ne);
-    const double a = (double)A[e];
-    if (i == j) dia += a * a;
-    else off += a * a;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    off += __shfl_xor_sync(0xffffffffu, off, o);
-    dia += __shfl_xor_sync(0xffffffffu, dia, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5][0] = off;
-    red[threadIdx.x >> 5][1] = dia;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += red[w][0];
-      b += red[w][1];
-    }
-    if (a <= (double)tol * b) *done = 1;
-  }
+// done = 1 once the off-diagonal mass of the sweep's last round (mass[0], summed
+// by k_bj_apply) is at most tol of the diagonal mass (mass[1]).
+__global__ void k_bj_check(const double* __restrict__ mass, double tol, int* __restrict__ done) {
+  if (threadIdx.x == 0 && (mass[0] <= tol * mass[1] || mass[0] == 0.0)) *done = 1;
 }
 
 // X (n x n, FP64) <- the leading n x n of V (ne x ne); As <- sym(A64).
@@ -1237,45 +1269,59 @@ __global__ void k_bj_extract(int n, int ne, const float* __restrict__ V, const d
 }
 
 // Refinement pieces for n up to 1024 (one thread per column, lambda in global).
-__global__ void __launch_bounds__(1024)
-    k_oa_correction(int n, const double* __restrict__ A, const double* __restrict__ R,
-                    const double* __restrict__ S, double* __restrict__ E, double* __restrict__ lam) {
-  __shared__ double red[32][3];
-  __shared__ double delta;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) lam[i] = S[(long long)i * n + i] / (1.0 - R[(long long)i * n + i]);
+// Row i per block: lam[i] = S_ii / (1 - R_ii) and the squared norms of the
+// off-diagonal of S, of A and of R added to acc[0..2] (zeroed by the caller).
+__global__ void __launch_bounds__(256)
+    k_oa_norms(int n, const double* __restrict__ A, const double* __restrict__ R,
+               const double* __restrict__ S, double* __restrict__ lam, double* __restrict__ acc) {
+  __shared__ double red[8][3];
+  const int i = blockIdx.x;
+  const long long o = (long long)i * n;
   double so = 0.0, an = 0.0, rn = 0.0;
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
-    if (i != j) so += S[e] * S[e];
-    an += A[e] * A[e];
-    rn += R[e] * R[e];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double sv = S[o + j], av = A[o + j], rv = R[o + j];
+    if (j != i) so += sv * sv;
+    an += av * av;
+    rn += rv * rv;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    so += __shfl_xor_sync(0xffffffffu, so, o);
-    an += __shfl_xor_sync(0xffffffffu, an, o);
-    rn += __shfl_xor_sync(0xffffffffu, rn, o);
+  for (int k = 16; k > 0; k >>= 1) {
+    so += __shfl_xor_sync(0xffffffffu, so, k);
+    an += __shfl_xor_sync(0xffffffffu, an, k);
+    rn += __shfl_xor_sync(0xffffffffu, rn, k);
   }
-  if ((tid & 31) == 0) {
-    red[tid >> 5][0] = so;
-    red[tid >> 5][1] = an;
-    red[tid >> 5][2] = rn;
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = so;
+    red[threadIdx.x >> 5][1] = an;
+    red[threadIdx.x >> 5][2] = rn;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int w = 0; w < nt / 32; ++w) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += red[w][0];
       b += red[w][1];
       c += red[w][2];
     }
-    delta = 2.0 * (sqrt(a) + sqrt(b) * sqrt(c));
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+    atomicAdd(acc + 2, c);
+    lam[i] = S[o + i] / (1.0 - R[o + i]);
   }
-  __syncthreads();
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
-    const double gap = lam[j] - lam[i];
-    E[e] = (i == j || fabs(gap) <= delta) ? 0.5 * R[e] : (S[e] + lam[j] * R[e]) / gap;
+}
+
+// Row i per block of the correction E: eigenvalues closer than
+// delta = 2 (||offdiag S|| + ||A|| ||R||) are treated as one cluster.
+__global__ void __launch_bounds__(256)
+    k_oa_correction(int n, const double* __restrict__ R, const double* __restrict__ S,
+                    const double* __restrict__ lam, const double* __restrict__ acc,
+                    double* __restrict__ E) {
+  const int i = blockIdx.x;
+  const long long o = (long long)i * n;
+  const double delta = 2.0 * (sqrt(acc[0]) + sqrt(acc[1]) * sqrt(acc[2]));
+  const double li = lam[i];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double gap = lam[j] - li;
+    E[o + j] = (j == i || fabs(gap) <= delta) ? 0.5 * R[o + j] : (S[o + j] + lam[j] * R[o + j]) / gap;
   }
 }
 
@@ -1319,6 +1365,7 @@ inline size_t dense_eig_bytes(int n) {
   const int npairs = ne / BJ_W;
   return WsCarve::round(sizeof(float) * (size_t)ne * ne) * 2 +
          WsCarve::round(sizeof(float) * (size_t)npairs * BJ_W * BJ_W) + WsCarve::round(64) +
+         WsCarve::round(sizeof(double) * (2 * BJ_SWEEPS + 4)) +
          5 * WsCarve::round(sizeof(double) * (size_t)n * n) + WsCarve::round(sizeof(double) * n);
 }
 
@@ -1331,6 +1378,7 @@ fpca_status launch_dense_eig(fpca_ctx* ctx, int n, double* A, double* V, void* s
   float* Vf = c.take<float>((size_t)ne * ne);
   float* Jg = c.take<float>((size_t)npairs * BJ_W * BJ_W);
   int* done = c.take<int>(16);
+  double* mass = c.take<double>(2 * BJ_SWEEPS + 4);  // per sweep; the last 3: refinement norms
   const size_t nn = (size_t)n * n;
   double* As = c.take<double>(nn);
   double* X = c.take<double>(nn);
@@ -1341,45 +1389,49 @@ fpca_status launch_dense_eig(fpca_ctx* ctx, int n, double* A, double* V, void* s
   double* E = U;  // U is dead once S is formed
   const int eb = (int)std::min<long long>(((long long)ne * ne + 255) / 256, 4096);
   k_bj_init<<<eb, 256, 0, ctx->stream>>>(n, ne, A, Af, Vf, done);
-  FPCA_LAUNCHED(ctx, "dense_eig");
+  FPCA_LAUNCHED(ctx, "eig_bj_init");
+  cudaMemsetAsync(mass, 0, sizeof(double) * (2 * BJ_SWEEPS + 4), ctx->stream);
   if (nb > 1) {
-    for (int sweep = 0; sweep < 10; ++sweep) {
+    for (int sweep = 0; sweep < BJ_SWEEPS; ++sweep) {
       for (int r = 0; r < nb - 1; ++r) {
         k_bj_sub<<<npairs, 768, 0, ctx->stream>>>(ne, r, Af, Jg, done);
-        FPCA_LAUNCHED(ctx, "dense_eig");
-        k_bj_apply_a<<<dim3(npairs, npairs), 256, 0, ctx->stream>>>(ne, r, Af, Jg, done);
-        FPCA_LAUNCHED(ctx, "dense_eig");
-        k_bj_apply_v<<<dim3(ne / BJ_W, npairs), 256, 0, ctx->stream>>>(ne, r, Vf, Jg, done);
-        FPCA_LAUNCHED(ctx, "dense_eig");
+        FPCA_LAUNCHED(ctx, "eig_bj_sub");
+        k_bj_apply<<<dim3(npairs, npairs + ne / BJ_W), 256, 0, ctx->stream>>>(
+            ne, r, Af, Vf, Jg, done, r == nb - 2 ? mass + 2 * sweep : nullptr);
+        FPCA_LAUNCHED(ctx, "eig_bj_apply");
       }
-      k_bj_check<<<1, 1024, 0, ctx->stream>>>(ne, Af, 1e-12f, done);
-      FPCA_LAUNCHED(ctx, "dense_eig");
+      k_bj_check<<<1, 32, 0, ctx->stream>>>(mass + 2 * sweep, BJ_TOL, done);
+      FPCA_LAUNCHED(ctx, "eig_bj_check");
     }
   } else {
     // a single subproblem holds the whole (padded) matrix
     k_bj_sub<<<1, 768, 0, ctx->stream>>>(ne, 0, Af, Jg, done);
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_bj_sub");
     k_bj_apply_v<<<dim3(ne / BJ_W, 1), 256, 0, ctx->stream>>>(ne, 0, Vf, Jg, done);
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_bj_apply_v");
   }
   const int xb = (int)std::min<long long>(((long long)nn + 255) / 256, 4096);
   k_bj_extract<<<xb, 256, 0, ctx->stream>>>(n, ne, Vf, A, X, As);
-  FPCA_LAUNCHED(ctx, "dense_eig");
+  FPCA_LAUNCHED(ctx, "eig_bj_extract");
   const int tpb = std::min(1024, ((n + 31) / 32) * 32);
   for (int step = 0; step < 3; ++step) {
     k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, X, 1, X, R, 1.0, -1.0);   // R = I - X'X
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_oa_rowmm");
     k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, As, 0, X, U, 0.0, 1.0);   // U = A X
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_oa_rowmm");
     k_oa_rowmm<<<n, tpb, 0, ctx->stream>>>(n, X, 1, U, S, 0.0, 1.0);    // S = X' A X
-    FPCA_LAUNCHED(ctx, "dense_eig");
-    k_oa_correction<<<1, 1024, 0, ctx->stream>>>(n, As, R, S, E, lam);
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_oa_rowmm");
+    double* acc = mass + 2 * BJ_SWEEPS + 1;
+    cudaMemsetAsync(acc, 0, sizeof(double) * 3, ctx->stream);
+    k_oa_norms<<<n, 256, 0, ctx->stream>>>(n, As, R, S, lam, acc);
+    FPCA_LAUNCHED(ctx, "eig_oa_norms");
+    k_oa_correction<<<n, 256, 0, ctx->stream>>>(n, R, S, lam, acc, E);
+    FPCA_LAUNCHED(ctx, "eig_oa_correction");
     k_oa_update<<<n, tpb, sizeof(double) * n, ctx->stream>>>(n, X, E);
-    FPCA_LAUNCHED(ctx, "dense_eig");
+    FPCA_LAUNCHED(ctx, "eig_oa_update");
   }
   k_rr_out<<<xb, 256, 0, ctx->stream>>>(n, lam, X, A, V);
-  FPCA_LAUNCHED(ctx, "dense_eig");
+  FPCA_LAUNCHED(ctx, "eig_out");
   return FPCA_OK;
 }
 
