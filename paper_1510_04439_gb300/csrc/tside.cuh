@@ -467,8 +467,10 @@ __device__ __forceinline__ void tside_phase3(const float* __restrict__ slots, in
 //   phase 2  item = (unit (u, q), row i, SEG-column segment): the float2 window
 //            along row i of pair u, weights {w_q, w_q} -> slots (m, q), (m', q);
 //   phase 3  the per-point solve of k_hsolve2 (tside_phase3).
-// One CTA per SM walks the tiles; the next tile's rows are fetched by the TMA
-// engine while the current tile runs phases 2 and 3.  Tap counts are odd
+// Persistent CTAs (two per SM up to 9 taps) walk the tiles; each tile's input rows
+// come in by TMA bulk copies, and the two CTAs of an SM start half a tile apart so
+// that one's copy overlaps the other's arithmetic (the slots of phases 2-3 alias the
+// input rows, so a CTA cannot fetch ahead of itself).  Tap counts are odd
 // (2T + 1) and enter as template parameters up to TS_MAXT; every sum is formed
 // in partials of at most TS_PART taps (plain FMAs) added with Kahan compensation
 // when COMP is set.
