@@ -87,6 +87,48 @@ __global__ void k_matrixize(int P, const TG* __restrict__ G, const int32_t* __re
 constexpr int PJ_WARPS = 8;
 constexpr int PJ_U = 8;    // k values per batch of loads of S
 
+// Accumulators of k_proj: RPT rows x LM columns per thread.  PAIRED keeps them in
+// column pairs, so that one paired FMA (fma.rn.f32x2) updates two columns of a row
+// and a k step issues LM / 2 FMA instructions per row (used where the pairs fit the
+// registers without spilling: LM <= 20 with RPT = 2, LM = 8 with RPT = 4).
+template <int LM, int RPT, bool PAIRED>
+struct ProjAcc;
+template <int LM, int RPT>
+struct ProjAcc<LM, RPT, true> {
+  float2 a[RPT][LM / 2];
+  __device__ __forceinline__ ProjAcc() {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < LM / 2; ++c) a[r][c] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void fma4(int r, int c4, float sv, float4 x) {
+    const float2 s2 = make_float2(sv, sv);
+    a[r][2 * c4] = __ffma2_rn(s2, make_float2(x.x, x.y), a[r][2 * c4]);
+    a[r][2 * c4 + 1] = __ffma2_rn(s2, make_float2(x.z, x.w), a[r][2 * c4 + 1]);
+  }
+  __device__ __forceinline__ float get(int r, int c) const {
+    return (c & 1) ? a[r][c >> 1].y : a[r][c >> 1].x;
+  }
+};
+template <int LM, int RPT>
+struct ProjAcc<LM, RPT, false> {
+  float a[RPT][LM];
+  __device__ __forceinline__ ProjAcc() {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < LM; ++c) a[r][c] = 0.f;
+  }
+  __device__ __forceinline__ void fma4(int r, int c4, float sv, float4 x) {
+    a[r][4 * c4] = fmaf(sv, x.x, a[r][4 * c4]);
+    a[r][4 * c4 + 1] = fmaf(sv, x.y, a[r][4 * c4 + 1]);
+    a[r][4 * c4 + 2] = fmaf(sv, x.z, a[r][4 * c4 + 2]);
+    a[r][4 * c4 + 3] = fmaf(sv, x.w, a[r][4 * c4 + 3]);
+  }
+  __device__ __forceinline__ float get(int r, int c) const { return a[r][c]; }
+};
+
 template <int LM, int RPT>
 __global__ void __launch_bounds__(PJ_WARPS * 32, 2)
     k_proj(int P, int l, int kb, int kc, const float* __restrict__ S,
@@ -97,11 +139,7 @@ __global__ void __launch_bounds__(PJ_WARPS * 32, 2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pbase = (blockIdx.x * PJ_WARPS + warp) * 32 * RPT + lane;
   const int kend = min(P, (blockIdx.y + 1) * kb);
-  float acc[RPT][LM];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int c = 0; c < LM; ++c) acc[r][c] = 0.f;
+  ProjAcc<LM, RPT, (LM <= 20)> acc;
   for (int k0 = blockIdx.y * kb; k0 < kend; k0 += kc) {
     const int nk = min(kend - k0, kc);
     __syncthreads();
@@ -129,12 +167,7 @@ __global__ void __launch_bounds__(PJ_WARPS * 32, 2)
         for (int c4 = 0; c4 < L4; ++c4) {
           const float4 x = xs4[(k + u) * L4 + c4];
 #pragma unroll
-          for (int r = 0; r < RPT; ++r) {
-            acc[r][4 * c4 + 0] = fmaf(sv[u][r], x.x, acc[r][4 * c4 + 0]);
-            acc[r][4 * c4 + 1] = fmaf(sv[u][r], x.y, acc[r][4 * c4 + 1]);
-            acc[r][4 * c4 + 2] = fmaf(sv[u][r], x.z, acc[r][4 * c4 + 2]);
-            acc[r][4 * c4 + 3] = fmaf(sv[u][r], x.w, acc[r][4 * c4 + 3]);
-          }
+          for (int r = 0; r < RPT; ++r) acc.fma4(r, c4, sv[u][r], x);
         }
     };
     load(sa, 0);
@@ -152,7 +185,7 @@ __global__ void __launch_bounds__(PJ_WARPS * 32, 2)
     if (p < P) {
 #pragma unroll
       for (int c = 0; c < LM; ++c)
-        if (c < l) out[(long long)c * P + p] = acc[r][c];
+        if (c < l) out[(long long)c * P + p] = acc.get(r, c);
     }
   }
 }

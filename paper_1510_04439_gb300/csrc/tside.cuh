@@ -477,17 +477,23 @@ __device__ __forceinline__ void tside_phase3(const float* __restrict__ slots, in
 constexpr int TS_PART = 12;
 constexpr int TS_MAXT = 19;   // half-widths of the unrolled sweeps (taps <= 39)
 constexpr int TS_PAIRS = 8;   // mid pairs
-constexpr int TS_UNITS = 13;  // (mid pair, t2 power) units of phase 2
+constexpr int TS_UNITS = 12;  // (mid pair, t2 power) units of phase 2
 constexpr int TS_NT = 256;    // threads per CTA (two CTAs per SM)
 
-// pair u -> (mid m, mid m'); m' = -1: none (its half is zero)
-static __constant__ int8_t c_ts_mid[TS_PAIRS][2] = {{0, 1}, {3, 4}, {6, 7}, {10, 11},
-                                             {2, 5}, {8, 9}, {12, 13}, {14, -1}};
+// pair u -> (mid m, mid m'); m' = -1: none (its half is zero).  The pairs are
+// chosen for phase 2: a unit is one stored pair at one t2 power, so a pair costs
+// as many units as its mid with more t2 powers needs (m0: 3; m1, m3, m6, m10: 2;
+// the rest 1).  Pairing the 2-power mids with each other and m0 with m1 gives
+// 12 units -- 768 phase-2 items, three full rounds of the CTA's 256 threads --
+// where pairing each mid with its array's neighbour gave 13 (a fourth round a
+// quarter full).  Pairs of one s-side array (m0, m1; m10, m11) share their
+// phase-1 window; the others load two.
+static __constant__ int8_t c_ts_mid[TS_PAIRS][2] = {{0, 1}, {10, 11}, {3, 6}, {2, 4},
+                                             {5, 7},  {8, 9},   {12, 13}, {14, -1}};
 // phase-2 unit -> (pair, t2 power row, slot of .x, slot of .y; -1 = not needed)
 static __constant__ int8_t c_ts_unit[TS_UNITS][4] = {
-    {0, 0, 0, 3},  {0, 1, 4, 13}, {0, 2, 14, -1}, {1, 0, 1, 7},   {1, 1, 8, -1},
-    {2, 0, 2, 10}, {2, 1, 11, -1}, {3, 0, 15, 18}, {3, 1, 19, -1}, {4, 0, 12, 5},
-    {5, 0, 6, 9},  {6, 0, 16, 17}, {7, 3, 20, -1}};
+    {0, 0, 0, 3},   {0, 1, 4, 13}, {0, 2, 14, -1}, {1, 0, 15, 18}, {1, 1, 19, -1}, {2, 0, 1, 2},
+    {2, 1, 8, 11},  {3, 0, 12, 7}, {4, 0, 5, 10},  {5, 0, 6, 9},   {6, 0, 16, 17}, {7, 3, 20, -1}};
 
 struct TsGeom {
   int P, R, C;
