@@ -116,41 +116,36 @@ __global__ void __launch_bounds__(128, 2)
   __syncwarp();
   ptx::tc_fence_after();
   if (have) {
-    const int row = tm * BM + warp * 32 + lane;
+    // The operand stages are free once every MMA has completed: each warp takes a
+    // 32 x 33 word scratch there to turn its rows around, so that the direct tile,
+    // like the mirrored one, is written 32 consecutive words per store instruction.
+    uint32_t* scr = reinterpret_cast<uint32_t*>(smem) + warp * 32 * 33;
+    const int row0 = tm * BM + warp * 32;
+    const int row = row0 + lane;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       uint32_t r[32];
       ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, r);
       ptx::tmem_ld_wait();
       const int col0 = tn * BN + c * 32;
-      if (job.out_int) {
-        int32_t* out = static_cast<int32_t*>(job.out);
-        int32_t vals[32];
+      uint32_t bits[32];  // the output words of row `row`, columns col0 .. col0 + 31
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          vals[j] = (row == col0 + j) ? 0 : __float2int_rn(__uint_as_float(r[j]));
-        int4* dst = reinterpret_cast<int4*>(out + (size_t)row * P + col0);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          dst[j] = make_int4(vals[4 * j], vals[4 * j + 1], vals[4 * j + 2], vals[4 * j + 3]);
-        if (tm != tn) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) out[(size_t)(col0 + j) * P + row] = vals[j];
-        }
-      } else {
-        float* out = static_cast<float*>(job.out);
-        float vals[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) vals[j] = (row == col0 + j) ? 0.f : __uint_as_float(r[j]);
-        float4* dst = reinterpret_cast<float4*>(out + (size_t)row * P + col0);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          dst[j] = make_float4(vals[4 * j], vals[4 * j + 1], vals[4 * j + 2], vals[4 * j + 3]);
-        if (tm != tn) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) out[(size_t)(col0 + j) * P + row] = vals[j];
-        }
+      for (int j = 0; j < 32; ++j) {
+        const float x = (row == col0 + j) ? 0.f : __uint_as_float(r[j]);
+        bits[j] = job.out_int ? static_cast<uint32_t>(__float2int_rn(x)) : __float_as_uint(x);
       }
+      uint32_t* out = static_cast<uint32_t*>(job.out);
+      if (tm != tn) {  // mirrored tile: lanes are consecutive rows = consecutive columns there
+#pragma unroll
+        for (int j = 0; j < 32; ++j) out[(size_t)(col0 + j) * P + row] = bits[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) scr[lane * 33 + j] = bits[j];
+      __syncwarp();
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr)
+        out[(size_t)(row0 + rr) * P + col0 + lane] = scr[rr * 33 + lane];
+      __syncwarp();
     }
   }
   ptx::tc_fence_before();
