@@ -435,6 +435,9 @@ def main():
     ap.add_argument("--rows", default=None, help="write the per-dataset evaluation rows (JSON)")
     ap.add_argument("--table", default=None,
                     help="reuse the labelled table (X, Y, M, best) of an earlier run's output")
+    ap.add_argument("--net", default=None,
+                    help="also write the trained network and its feature standardisation "
+                         "with fpca_bw_mlp_io (load it back with save=False)")
     a = ap.parse_args()
     ctx = B.Context(0)
     t0 = time.time()
@@ -455,6 +458,10 @@ def main():
                 train=int(X.shape[0]), epochs=a.epochs)
     np.savez(a.out, params=th.cpu().numpy(), mu=mu, sd=sd, X=X, Y=Y, M=M, best=best,
              loss=np.array(hist))
+    if a.net:
+        fmu = torch.from_numpy(np.asarray(mu, dtype=np.float32)).to(ctx.device)
+        fsd = torch.from_numpy(np.asarray(sd, dtype=np.float32)).to(ctx.device)
+        ctx.bw_mlp_io(th, a.net, True, feat_mu=fmu, feat_sd=fsd)
     if a.rows:
         with open(a.rows, "w") as fh:
             json.dump(rows, fh)
