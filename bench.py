@@ -213,6 +213,22 @@ def measure_alu_peaks(torch, ctx, stream, sms, reps=5):
     return out
 
 
+def record_graph(B, ctx, fn):
+    """The library calls of fn recorded as one CUDA graph (fpca_graph_*): (graph,
+    None), or (None, why) when a call refused to be recorded."""
+    ctx.graph_begin()
+    err = None
+    try:
+        fn()
+    except B.FpcaError as e:
+        err = e
+    try:
+        g = ctx.graph_end()
+    except B.FpcaError as e:
+        return None, str(err or e)
+    return (g, None) if err is None else (None, str(err))
+
+
 def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5):
     """The plain method at FP64: n = 50 surfaces on a full 16 x 16 grid (65,536 4-D
     covariance points), h = 0.15, FP64 binning, FP64 moment sweeps and solves, and the
@@ -231,13 +247,18 @@ def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5):
     for _ in range(2):
         step()
     torch.cuda.synchronize()
+    # the step as one CUDA graph (its dense eigensolver alone is ~190 launches)
+    graph, note = record_graph(B, ctx, step)
     evs = []
     for _ in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step()
+        if graph is not None:
+            ctx.graph_launch(graph)
+        else:
+            step()
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
@@ -255,6 +276,8 @@ def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5):
             "value": pts / (ms * 1e-3), "unit": UNIT, "cov_points": pts,
             "evals": [float(x) for x in bufs.evals.cpu().numpy()],
             "ms_per_launch": per,
+            "launch": (f"one CUDA graph per step ({graph.launches} kernels)" if graph is not None
+                       else f"kernels launched one by one ({note})"),
             "note": "FP64 throughout; the dense eigensolver returns the top 4 of all 256 "
                     "eigenpairs; absolute times (the kernels are latency-bound at this size)"}
 
@@ -577,7 +600,10 @@ def main():
     omega = torch.from_numpy(om_np.astype(np.float32)).to(dev)
     bufs = pipeline.alloc_dense(torch, dev, P, K_EIG, B.BF16, B.F32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a created stream (a CUDA graph cannot be recorded on the legacy default stream),
+    # made torch's current stream so that every copy and flush is ordered with the steps
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     ctx = B.Context(local_rank, stream)
 
     def step(yy, mm, smooth_prec=B.F32C):
@@ -596,6 +622,22 @@ def main():
         step(y, mask)
     torch.cuda.synchronize()
 
+    def record(fn):
+        return record_graph(B, ctx, fn)
+
+    # the step's kernels as one graph after the warm-up (workspace grown, the sweep
+    # autotuner's choice made): one launch per step instead of ~50
+    graph, graph_note = record(lambda: step(y, mask))
+
+    def run_step():
+        if graph is not None:
+            ctx.graph_launch(graph)
+        else:
+            step(y, mask)
+
+    run_step()
+    torch.cuda.synchronize()
+
     # ---- timed region: device-resident inputs, L2 flushed between steps ----
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -609,7 +651,7 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(y, mask)
+        run_step()
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
@@ -645,6 +687,8 @@ def main():
     y_in = [torch.empty_like(y) for _ in range(2)]
     m_in = [torch.empty_like(mask) for _ in range(2)]
     copy_stream = torch.cuda.Stream(dev)
+    # one recorded step per input buffer
+    g_in = [record(lambda b=b: step(y_in[b], m_in[b]))[0] for b in range(2)]
     ready = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
     barrier()
@@ -670,7 +714,10 @@ def main():
         b = i % 2
         flush.zero_()
         stream.wait_event(ready[b])
-        step(y_in[b], m_in[b])
+        if g_in[b] is not None:
+            ctx.graph_launch(g_in[b])
+        else:
+            step(y_in[b], m_in[b])
         free[b].record(stream)
         ev_h.copy_(bufs.evals, non_blocking=True)
         vec_h.copy_(bufs.evecs, non_blocking=True)
@@ -896,6 +943,10 @@ def main():
                                     "FP32 compensated moments; FP32 solve, float-float "
                                     "re-solve of ill-conditioned points; Rayleigh-Ritz by FP32 "
                                     "Jacobi and two float-float refinement steps",
+                       "launch": (f"one CUDA graph per step ({graph.launches} kernels recorded "
+                                  "with fpca_graph_begin/_end, replayed with fpca_graph_launch)"
+                                  if graph is not None else
+                                  f"kernels launched one by one ({graph_note})"),
                        "symmetry": "Gamma_hat fitted at t >= s, mirrored to t < s (exact "
                                    "symmetry of the estimator)",
                        "l2": "flushed between timed steps (256 MiB write)",

@@ -170,6 +170,27 @@ fpca_status fpca_set_cv_batch(fpca_ctx* ctx, int batch);
  * the following fpca_sync() returns FPCA_OK again. */
 fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive);
 
+/* CUDA graphs of call sequences.  fpca_graph_begin starts capturing the
+ * context's stream (which must be a created stream, not the legacy default
+ * stream; kernel timing must be off); the calls that follow are recorded, not
+ * run; fpca_graph_end closes the capture and returns an instantiated graph that
+ * fpca_graph_launch replays on the context's stream with the same device
+ * pointers and scalars (the caller keeps the buffers alive and rewrites their
+ * contents between launches).  Calls that read results back to the host, grow
+ * the workspace, time an autotuner's candidates or copy from host memory cannot
+ * be captured: they return FPCA_E_UNSUPPORTED, and fpca_graph_end then returns
+ * FPCA_E_UNSUPPORTED without a graph.  So run a sequence once before capturing
+ * it (the workspace grows and the autotuners decide on that first run).
+ * fpca_graph_launches gives the number of kernels in a graph (added to the
+ * context's launch count at every launch).  Argument errors during capture are
+ * reported as outside it; device errors surface at fpca_sync after a launch. */
+typedef struct fpca_graph fpca_graph;
+fpca_status fpca_graph_begin(fpca_ctx* ctx);
+fpca_status fpca_graph_end(fpca_ctx* ctx, fpca_graph** graph);
+fpca_status fpca_graph_launch(fpca_ctx* ctx, const fpca_graph* graph);
+uint64_t fpca_graph_launches(const fpca_graph* graph);
+void fpca_graph_destroy(fpca_graph* graph);
+
 /* Kernel timing (off by default).  When enabled, a CUDA event is recorded on
  * the context stream at the start of every entry point and after every
  * kernel launch; a kernel's time is the interval between its event and the

@@ -32,9 +32,26 @@ SYMBOLS = (
     "fpca_smooth_cov_apply", "fpca_smooth_cov_tiles", "fpca_rproj_eig_factor", "fpca_sigma2",
     "fpca_smooth_cov_diag", "fpca_scores_pace", "fpca_scores_integral", "fpca_reconstruct",
     "fpca_mise", "fpca_bw_trust_region", "fpca_check_wait", "fpca_set_sweep_kernel",
-    "fpca_set_cv_batch",
+    "fpca_set_cv_batch", "fpca_graph_begin", "fpca_graph_end", "fpca_graph_launch",
+    "fpca_graph_launches", "fpca_graph_destroy",
     "fpca_bw_mlp_init", "fpca_bw_mlp_io", "fpca_smooth_mean_cv", "fpca_alu_probe",
 )
+
+
+class Graph:
+    """An instantiated CUDA graph of library calls (fpca_graph_*)."""
+
+    def __init__(self, lib, h):
+        self.lib, self.h = lib, h
+
+    @property
+    def launches(self):
+        return int(self.lib.fpca_graph_launches(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.fpca_graph_destroy(self.h)
+            self.h = None
 
 
 class FpcaError(RuntimeError):
@@ -115,6 +132,13 @@ def load(path=LIB_PATH):
     lib.fpca_check_wait.argtypes = [vp, i32]
     lib.fpca_set_sweep_kernel.argtypes = [vp, i32]
     lib.fpca_set_cv_batch.argtypes = [vp, i32]
+    lib.fpca_graph_begin.argtypes = [vp]
+    lib.fpca_graph_end.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.fpca_graph_launch.argtypes = [vp, vp]
+    lib.fpca_graph_launches.argtypes = [vp]
+    lib.fpca_graph_launches.restype = ctypes.c_uint64
+    lib.fpca_graph_destroy.argtypes = [vp]
+    lib.fpca_graph_destroy.restype = None
     lib.fpca_alu_probe.argtypes = [vp, i32, i32, i32, dbl_p]
     lib.fpca_bw_mlp_init.argtypes = [vp, ctypes.c_uint64, vp]
     lib.fpca_smooth_mean_cv.argtypes = [vp, ctypes.POINTER(Data), ctypes.POINTER(Grid), vp, i32,
@@ -164,7 +188,8 @@ def load(path=LIB_PATH):
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("fpca_destroy", "fpca_last_error", "fpca_launch_count",
-                        "fpca_bw_param_count", "fpca_cov_factor_bytes"):
+                        "fpca_bw_param_count", "fpca_cov_factor_bytes", "fpca_graph_launches",
+                        "fpca_graph_destroy"):
             f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -215,6 +240,20 @@ class Context:
 
     def sync(self):
         self._check(self.lib.fpca_sync(self.h))
+
+    # ---- CUDA graphs of call sequences ----------------------------------------
+    def graph_begin(self):
+        """Start recording this context's calls (a created stream, timing off)."""
+        self._check(self.lib.fpca_graph_begin(self.h))
+
+    def graph_end(self):
+        """Close the recording; returns a Graph (replay with graph_launch)."""
+        h = ctypes.c_void_p()
+        self._check(self.lib.fpca_graph_end(self.h, ctypes.byref(h)))
+        return Graph(self.lib, h)
+
+    def graph_launch(self, graph):
+        self._check(self.lib.fpca_graph_launch(self.h, graph.h))
 
     def set_sweep_kernel(self, kernel):
         """0 automatic (timed once per grid and windows), 1 scalar, 2 packed pairs."""

@@ -83,8 +83,18 @@ static void prof_resolve(fpca_ctx* ctx) {
     if (e != ctx->prof_last) ctx->prof_pool.push_back(e);
 }
 
+fpca_status fpca_no_capture(fpca_ctx* ctx, const char* what) {
+  if (!ctx->capturing) return FPCA_OK;
+  ctx->capture_failed = 1;
+  return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
+                   "%s cannot run inside a graph capture (run the calls once before capturing)",
+                   what);
+}
+
 void* fpca_workspace(fpca_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return ctx->ws;
+  // growing synchronises the stream and reallocates: not inside a capture
+  if (fpca_no_capture(ctx, "growing the workspace") != FPCA_OK) return nullptr;
   // Growing: the old block may still be in use by queued work.
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return nullptr;
   if (ctx->ws) cudaFree(ctx->ws);
@@ -263,6 +273,7 @@ fpca_status fpca_check_wait(fpca_ctx* ctx, int arrive) {
 
 fpca_status fpca_profile_enable(fpca_ctx* ctx, int enable) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  if (fpca_no_capture(ctx, "fpca_profile_enable") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   prof_resolve(ctx);
   ctx->prof_totals.clear();
   ctx->prof = enable ? 1 : 0;
@@ -288,8 +299,78 @@ fpca_status fpca_profile_entry(fpca_ctx* ctx, int i, const char** name, double* 
   return FPCA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CUDA graphs of call sequences
+// ---------------------------------------------------------------------------
+struct fpca_graph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;  // kernels in the graph
+};
+
+fpca_status fpca_graph_begin(fpca_ctx* ctx) {
+  if (!ctx) return FPCA_E_INVALID_ARG;
+  if (ctx->capturing) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "a capture is already open");
+  if (!ctx->stream)
+    return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
+                     "graph capture needs a context on a created stream, not the legacy default");
+  if (ctx->prof) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "kernel timing is on");
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  ctx->capturing = 1;
+  ctx->capture_failed = 0;
+  ctx->capture_launches = ctx->launches;
+  return FPCA_OK;
+}
+
+fpca_status fpca_graph_end(fpca_ctx* ctx, fpca_graph** graph) {
+  if (!ctx || !graph) return FPCA_E_INVALID_ARG;
+  *graph = nullptr;
+  if (!ctx->capturing) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "no capture is open");
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->capturing = 0;
+  const uint64_t n = ctx->launches - ctx->capture_launches;
+  ctx->launches = ctx->capture_launches;  // captured, not yet run
+  if (e != cudaSuccess || ctx->capture_failed || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (ctx->capture_failed) return FPCA_E_UNSUPPORTED;  // the refusing call set the text
+    return fpca_fail(ctx, FPCA_E_CUDA, "end capture: %s", cudaGetErrorString(e));
+  }
+  fpca_graph* out = new fpca_graph;
+  out->launches = n;
+  e = cudaGraphInstantiate(&out->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    delete out;
+    return fpca_fail(ctx, FPCA_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
+  }
+  *graph = out;
+  return FPCA_OK;
+}
+
+fpca_status fpca_graph_launch(fpca_ctx* ctx, const fpca_graph* graph) {
+  if (!ctx || !graph) return FPCA_E_INVALID_ARG;
+  if (ctx->capturing) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "a capture is open");
+  fpca_prof_mark(ctx);
+  const cudaError_t e = cudaGraphLaunch(graph->exec, ctx->stream);
+  if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "graph launch: %s", cudaGetErrorString(e));
+  ctx->launches += graph->launches;
+  if (ctx->prof) fpca_prof_end(ctx, "graph");
+  return FPCA_OK;
+}
+
+uint64_t fpca_graph_launches(const fpca_graph* graph) { return graph ? graph->launches : 0; }
+
+void fpca_graph_destroy(fpca_graph* graph) {
+  if (!graph) return;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  delete graph;
+}
+
 fpca_status fpca_sync(fpca_ctx* ctx) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  if (fpca_no_capture(ctx, "fpca_sync") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return fpca_fail(ctx, FPCA_E_CUDA, "stream: %s", cudaGetErrorString(e));
   int herr = 0;

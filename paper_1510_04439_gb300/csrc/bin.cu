@@ -625,6 +625,7 @@ fpca_status launch_bin_mean_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, con
                                    double* v, double* v2) {
   const int P = grid_P(g);
   int64_t Nobs = 0;
+  if (fpca_no_capture(ctx, "reading offs[n] of scattered data") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   cudaError_t e = cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
                                   ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -676,6 +677,7 @@ fpca_status launch_cov_sparse(fpca_ctx* ctx, int n, const fpca_grid* g, const in
   const int F = nfold > 0 ? nfold : 1;
   // total observation count (offs[n]) is needed on the host to size the launch
   int64_t Nobs = 0;
+  if (fpca_no_capture(ctx, "reading offs[n] of scattered data") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   cudaError_t e = cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
                                   ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -749,7 +751,9 @@ fpca_status launch_cov_dense_folds(fpca_ctx* ctx, int n, int P, const void* y, i
   ph.reserve((size_t)nt * (nt + 1) / 2);
   for (int bi = 0; bi < nt; ++bi)
     for (int bj = bi; bj < nt; ++bj) ph.push_back(make_int2(bi, bj));
-  // pageable source: staged before the call returns
+  // pageable source: staged before the call returns (so not capturable)
+  if (fpca_no_capture(ctx, "the fold-split binning of gridded data") != FPCA_OK)
+    return FPCA_E_UNSUPPORTED;
   if (cudaMemcpyAsync(pairs, ph.data(), sizeof(int2) * ph.size(), cudaMemcpyHostToDevice,
                       ctx->stream) != cudaSuccess)
     return fpca_check_launch(ctx, "fold gram tile pairs");

@@ -52,6 +52,12 @@ struct fpca_ctx {
   // per (M1, M2, folds, compensated, taps of every bandwidth) once timed: 0 or 1
   int cv_batch = 2;
   std::map<std::vector<int>, int> cv_choice;
+  // CUDA-graph capture of the context's stream (fpca_graph_begin / _end): set while
+  // capturing; a call that cannot be captured (a host read-back, a workspace growth,
+  // an autotuner's timing, a copy from host memory) refuses and marks the capture
+  int capturing = 0;
+  int capture_failed = 0;
+  uint64_t capture_launches = 0;  // ctx->launches when the capture began
 };
 
 // Device error codes written by kernels into ctx->d_err.
@@ -61,6 +67,9 @@ enum { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BOUNDS = 2, DERR_NUMERIC = 3 };
 #define FPCA_WAIT_LIMIT_NS 2000000000ull
 
 fpca_status fpca_fail(fpca_ctx* ctx, fpca_status st, const char* fmt, ...);
+// FPCA_OK outside a graph capture; inside one, marks the capture as failed and
+// returns FPCA_E_UNSUPPORTED naming `what` (work that cannot be captured).
+fpca_status fpca_no_capture(fpca_ctx* ctx, const char* what);
 // Checks the last launch; records the CUDA error text on failure.
 fpca_status fpca_check_launch(fpca_ctx* ctx, const char* what);
 // Returns a device buffer of at least `bytes`, growing the workspace (which

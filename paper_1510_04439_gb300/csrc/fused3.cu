@@ -1427,6 +1427,10 @@ fpca_status ensure_lists(fpca_ctx* ctx, const Geo3& g) {
   all.insert(all.end(), order.begin(), order.end());
   all.insert(all.end(), tlist.begin(), tlist.end());
   const size_t bytes = all.size() * sizeof(int);
+  // building the lists uploads from the host and waits: the first call for a grid and
+  // taps runs outside a capture; later calls find the lists cached
+  if (fpca_no_capture(ctx, "building the near-pair work lists") != FPCA_OK)
+    return FPCA_E_UNSUPPORTED;
   if (bytes > ctx->f3_lists_bytes) {
     if (ctx->f3_lists) cudaFree(ctx->f3_lists);
     ctx->f3_lists = nullptr;
@@ -1800,6 +1804,7 @@ fpca_status fpca_smooth_cov_tiles(fpca_ctx* ctx, const fpca_grid* grid, const vo
   WsCarve c(ws);
   f3_work_carve(c, w);
   int* dpairs = c.take<int>(2 * (size_t)ntiles);
+  if (fpca_no_capture(ctx, "fpca_smooth_cov_tiles") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   if (cudaMemcpyAsync(dpairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice,
                       ctx->stream) != cudaSuccess)
     return fpca_fail(ctx, FPCA_E_CUDA, "tile list upload");

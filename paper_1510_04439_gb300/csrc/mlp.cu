@@ -255,6 +255,7 @@ fpca_status fpca_bw_mlp_io(fpca_ctx* ctx, float* params, float* feat_mu, float* 
                            const char* path, int save) {
   if (!ctx) return FPCA_E_INVALID_ARG;
   if (!params || !path) return fpca_fail(ctx, FPCA_E_INVALID_ARG, "params and path are required");
+  if (fpca_no_capture(ctx, "fpca_bw_mlp_io") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   std::vector<float> buf((size_t)kParamCount + 64, 0.f);
   const size_t nbytes = sizeof(float) * buf.size();
   if (save) {

@@ -1367,6 +1367,8 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
           const std::array<int, 6> key = {M1, M2, Tax[0], Tax[1], COMP ? 1 : 0, tg.half};
           auto it = ctx->tside_choice.find(key);
           if (it == ctx->tside_choice.end()) {
+            if (fpca_no_capture(ctx, "timing the t-side sweeps") != FPCA_OK)
+              return FPCA_E_UNSUPPORTED;
             Epilogue<float> e = ef;  // no accumulating epilogues, escalations solved in place
             e.cvacc = nullptr;
             e.y = nullptr;
@@ -1508,7 +1510,8 @@ fpca_status cv_grid_batched(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbin
     }
   }
   const size_t smem = cv_grid_smem(g, h, nh);
-  // pageable source: the copy is staged before the call returns
+  // pageable source: the copy is staged before the call returns (so not capturable)
+  if (fpca_no_capture(ctx, "the batched CV grid") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   if (cudaMemcpyAsync(items_d, items.data(), sizeof(CvGridItem) * nitems, cudaMemcpyHostToDevice,
                       ctx->stream) != cudaSuccess)
     return fpca_check_launch(ctx, "cv grid items");
@@ -1718,6 +1721,7 @@ fpca_status smooth_cov_typed(fpca_ctx* ctx, const fpca_grid* g, const fpca_covbi
       const std::vector<int> key = {g->m[0], g->m[1], F, COMP ? 1 : 0, nh, wide};
       auto it = ctx->cv_choice.find(key);
       if (it == ctx->cv_choice.end()) {
+        if (fpca_no_capture(ctx, "timing the CV schedules") != FPCA_OK) return FPCA_E_UNSUPPORTED;
         st = run_items();
         cudaEvent_t ev[3];
         for (auto& x : ev) cudaEventCreate(&x);
@@ -2010,6 +2014,7 @@ fpca_status mean_cv_run(fpca_ctx* ctx, const fpca_grid* g, int n, const int64_t*
     if (g->m[k] > TMAX + 1)
       return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "mean smoothing is built for m <= %d", TMAX + 1);
   long long Nobs = 0;
+  if (fpca_no_capture(ctx, "reading offs[n] of scattered data") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   if (cudaMemcpyAsync(&Nobs, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess)

@@ -205,6 +205,8 @@ extern "C" fpca_status fpca_bw_trust_region(fpca_ctx* ctx, const fpca_grid* grid
                                             double* cv_best, int* n_evals, double* trace,
                                             int trace_cap) {
   if (!ctx) return FPCA_E_INVALID_ARG;
+  // host-driven: every iteration reads its CV values back
+  if (fpca_no_capture(ctx, "fpca_bw_trust_region") != FPCA_OK) return FPCA_E_UNSUPPORTED;
   if (!grid || grid->d < 1 || grid->d > TR_DMAX)
     return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "the trust-region search is built for d <= 2");
   if (!bins || !h0 || !h_best)
