@@ -8,6 +8,11 @@
 #include "ptx.cuh"
 
 fpca_status fpca_fail(fpca_ctx* ctx, fpca_status st, const char* fmt, ...) {
+  if (ctx && ctx->capturing && ctx->capture_failed) {
+    // a refusal inside a graph capture (fpca_no_capture) already set the text; the
+    // caller's own failure on top of it (e.g. a workspace it could not grow) keeps it
+    return FPCA_E_UNSUPPORTED;
+  }
   if (ctx) {
     char buf[512];
     va_list ap;
@@ -85,10 +90,11 @@ static void prof_resolve(fpca_ctx* ctx) {
 
 fpca_status fpca_no_capture(fpca_ctx* ctx, const char* what) {
   if (!ctx->capturing) return FPCA_OK;
+  if (!ctx->capture_failed)
+    fpca_fail(ctx, FPCA_E_UNSUPPORTED,
+              "%s cannot run inside a graph capture (run the calls once before capturing)", what);
   ctx->capture_failed = 1;
-  return fpca_fail(ctx, FPCA_E_UNSUPPORTED,
-                   "%s cannot run inside a graph capture (run the calls once before capturing)",
-                   what);
+  return FPCA_E_UNSUPPORTED;
 }
 
 void* fpca_workspace(fpca_ctx* ctx, size_t bytes) {

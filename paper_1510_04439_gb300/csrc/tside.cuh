@@ -147,7 +147,10 @@ __device__ __forceinline__ float fit_point_f32(float (&A)[D][D], float (&r)[D], 
   for (int k = 0; k < D; ++k) {
     const float piv = A[k][k];
     if (!(piv >= (float)ESCALATE_F32 * diag[k])) escalate = true;
-    const float inv = piv > 0.f ? 1.f / piv : 0.f;
+    // the fast reciprocal (about 1 ulp): a system kept in FP32 has every pivot at
+    // least 1e-2 of its diagonal, so the solution moves by a few ulps at most; the
+    // systems below that are solved again in float-float
+    const float inv = piv > 0.f ? __fdividef(1.f, piv) : 0.f;
     invp[k] = inv;
 #pragma unroll
     for (int i = k + 1; i < D; ++i) {
