@@ -857,7 +857,7 @@ __device__ __forceinline__ void slide_sum_multi(const float* __restrict__ x, int
     for (int j = 0; j < NO; ++j) out[q][j] = sum[q][j];
 }
 
-// slide_sum_multi with NCH = nt / 4 fixed at compile time (8-tap partials with COMP).
+// slide_sum_multi with NCH = nt / 4 fixed at compile time (12-tap partials with COMP).
 template <int NO, int NP, int NCH, bool COMP>
 __device__ __forceinline__ void slide_sum_multi_fixed(const float* __restrict__ x, int stride,
                                                       const float4* const (&w4)[NP],
@@ -875,14 +875,34 @@ __device__ __forceinline__ void slide_sum_multi_fixed(const float* __restrict__ 
       cmp[q][j] = 0.f;
     }
   if constexpr (COMP) {
+    // partials of up to 12 taps (three chunks), Kahan-added: one compensation step per
+    // output for windows up to 24 taps, where 8-tap partials need two from 17 taps on
+    // (these passes are bound by their instruction count)
 #pragma unroll
-    for (int kc = 0; kc < NCH; kc += 2) {
-      const bool two = kc + 1 < NCH;
+    for (int kc = 0; kc < NCH; kc += 3) {
+      const int nch = NCH - kc < 3 ? NCH - kc : 3;
 #pragma unroll
-      for (int q = 0; q < NP; ++q)
-        comp_partial8<NO>(win, 4 * kc, w4[q][kc],
-                          two ? w4[q][kc + 1] : make_float4(0.f, 0.f, 0.f, 0.f), two, kc == 0,
-                          sum[q], cmp[q]);
+      for (int q = 0; q < NP; ++q) {
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          float p = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (c >= nch) break;
+            const float4 w = w4[q][kc + c];
+            const int b = 4 * (kc + c) + j;
+            p = (c == 0) ? w.x * win[b] : fmaf(w.x, win[b], p);
+            p = fmaf(w.y, win[b + 1], p);
+            p = fmaf(w.z, win[b + 2], p);
+            p = fmaf(w.w, win[b + 3], p);
+          }
+          if (kc == 0) {
+            sum[q][j] = p;
+          } else {
+            chunk_add<true>(sum[q][j], cmp[q][j], p);
+          }
+        }
+      }
     }
   }
 #pragma unroll
