@@ -612,7 +612,7 @@ __device__ __forceinline__ bool hsolve2_tile(const float* __restrict__ varr, con
                                              float* __restrict__ gamma,
                                              uint8_t* __restrict__ status,
                                              const Epilogue<float>& ep, double* red,
-                                             int* __restrict__ err) {
+                                             int* __restrict__ err, CvThread* cvt = nullptr) {
   const int P = g.P, R = g.R;
   float* slots = in;                                    // [NSL][HT][SC]
   const int th = min(HT, R - a0);
@@ -687,7 +687,8 @@ __device__ __forceinline__ bool hsolve2_tile(const float* __restrict__ varr, con
   }
   __syncthreads();
 
-  tside_phase3<C, NT2>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red, mid);
+  tside_phase3<C, NT2>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red, mid,
+                       cvt);
   return true;
 }
 
@@ -761,6 +762,21 @@ __global__ void __launch_bounds__(NT2, 2)
   int cur = -1;  // item whose weights are in shared memory
   uint32_t parity = 0;
   const int total = nitems * nblk;
+  // CV terms of the current item gathered per thread, added to its accumulators when
+  // the CTA moves on to another item (one block reduction per item, not per tile)
+  CvThread cvt;
+  auto flush = [&]() {
+    if (cur < 0 || !items[cur].ep.cvacc) return;
+    const double s0 = block_sum<NT2>(cvt.err, red);
+    const double s1 = block_sum<NT2>(cvt.in, red);
+    const double s2 = block_sum<NT2>(cvt.out, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(items[cur].ep.cvacc + 0, s0);
+      atomicAdd(items[cur].ep.cvacc + 1, s1);
+      atomicAdd(items[cur].ep.cvacc + 2, s2);
+    }
+    cvt = CvThread{};
+  };
   while (true) {
     if (threadIdx.x == 0) {
       int w = (int)atomicAdd(counter, 1u);
@@ -784,6 +800,7 @@ __global__ void __launch_bounds__(NT2, 2)
     const int nb = (I.g.R + HT - 1) / HT;
     const int xs = r / nb, a0 = (r - xs * nb) * HT;
     if (it != cur) {
+      flush();
       load_padded_weights(I.tab, I.g.Tr, I.g.ntr, wr);
       load_padded_weights(I.tab + TROWS * TW, I.g.Tc, I.g.ntc, wc);
       cur = it;
@@ -791,11 +808,12 @@ __global__ void __launch_bounds__(NT2, 2)
     Epilogue<float> ep = I.ep;
     if (ep.esc_count) ep.esc_idx_item = esc_item, ep.esc_item_id = I.item;
     if (!hsolve2_tile<COMP, C>(I.varr, I.g, xs, a0, wr, wc, mid, in, bar, parity, nullptr,
-                               nullptr, nullptr, ep, red, err))
+                               nullptr, nullptr, ep, red, err, &cvt))
       return;
     parity ^= 1u;
     __syncthreads();  // the slots alias the next tile's input rows
   }
+  flush();
 }
 
 // NO outputs x NP powers along a line from one sliding window:
