@@ -1197,27 +1197,52 @@ __global__ void __launch_bounds__(256)
 
 // Lower triangle (t < s in flat node order) of Gamma_hat and of its status from
 // the upper one after a half-mode t-side sweep (Gamma_hat(t, s) = Gamma_hat(s, t)):
-// 32 x 32 tiles transposed through shared memory.
-__global__ void k_mirror_lower(int P, float* __restrict__ gamma, uint8_t* __restrict__ status) {
-  __shared__ float tg[32][33];
-  __shared__ uint8_t ts[32][33];
-  const int bi = blockIdx.y, bj = blockIdx.x;  // destination rows bi*32.., columns bj*32..
-  if (bj > bi) return;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int sr = bj * 32 + r, sc = bi * 32 + threadIdx.x;  // source tile (bj, bi)
-    if (sr < P && sc < P) {
-      if (gamma) tg[r][threadIdx.x] = gamma[(long long)sr * P + sc];
-      if (status) ts[r][threadIdx.x] = status[(long long)sr * P + sc];
+// one block per lower 64 x 64 tile pair, its source tile loaded with every load in
+// flight at once, then transposed through shared memory.
+constexpr int MIR_T = 64;  // mirror tile edge
+__global__ void __launch_bounds__(256)
+    k_mirror_lower(int P, float* __restrict__ gamma, uint8_t* __restrict__ status) {
+  __shared__ float tg[MIR_T][MIR_T + 1];
+  __shared__ uint8_t ts[MIR_T][MIR_T + 4];
+  // lower tile pair L -> destination rows bi*64.., columns bj*64.., bj <= bi
+  const int L = blockIdx.x;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= L) ++bi;
+  const int bj = L - bi * (bi + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // all loads of the source tile (bj, bi) first: 8 rows x 2 columns per thread
+  float gv[8][2];
+  uint8_t sv[8][2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int sr = bj * MIR_T + ty + 8 * k, sc = bi * MIR_T + tx + 32 * h;
+      const bool in = sr < P && sc < P;
+      const long long o = (long long)sr * P + sc;
+      gv[k][h] = (gamma && in) ? gamma[o] : 0.f;
+      sv[k][h] = (status && in) ? status[o] : 0;
     }
-  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      tg[ty + 8 * k][tx + 32 * h] = gv[k][h];
+      ts[ty + 8 * k][tx + 32 * h] = sv[k][h];
+    }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int dr = bi * 32 + r, dc = bj * 32 + threadIdx.x;
-    if (dr < P && dc < dr) {
-      if (gamma) gamma[(long long)dr * P + dc] = tg[threadIdx.x][r];
-      if (status) status[(long long)dr * P + dc] = ts[threadIdx.x][r];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = ty + 8 * k, c = tx + 32 * h;
+      const int dr = bi * MIR_T + r, dc = bj * MIR_T + c;
+      if (dr < P && dc < dr) {
+        const long long o = (long long)dr * P + dc;
+        if (gamma) gamma[o] = tg[c][r];
+        if (status) status[o] = ts[c][r];
+      }
     }
-  }
 }
 
 // Geometry of k_hsolve2 for a d = 2 grid and tap half-widths (Tr on t1, Tc on t2).
@@ -1449,8 +1474,8 @@ fpca_status cov_smooth_one(fpca_ctx* ctx, const fpca_grid* g, const int32_t* cnt
           FPCA_LAUNCHED(ctx, "cov_escalated");
         }
         if (tg.half && (gm || status)) {
-          const int nt = (P + 31) / 32;
-          k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>(P, gm, status);
+          const int nt = (P + MIR_T - 1) / MIR_T;
+          k_mirror_lower<<<nt * (nt + 1) / 2, 256, 0, ctx->stream>>>(P, gm, status);
           FPCA_LAUNCHED(ctx, "cov_mirror");
         }
         return FPCA_OK;
