@@ -612,7 +612,7 @@ __device__ __forceinline__ bool hsolve2_tile(const float* __restrict__ varr, con
                                              float* __restrict__ gamma,
                                              uint8_t* __restrict__ status,
                                              const Epilogue<float>& ep, double* red,
-                                             int* __restrict__ err, CvThread* cvt = nullptr) {
+                                             int* __restrict__ err, CvShared* cvs = nullptr) {
   const int P = g.P, R = g.R;
   float* slots = in;                                    // [NSL][HT][SC]
   const int th = min(HT, R - a0);
@@ -688,7 +688,7 @@ __device__ __forceinline__ bool hsolve2_tile(const float* __restrict__ varr, con
   __syncthreads();
 
   tside_phase3<C, NT2>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red, mid,
-                       cvt);
+                       cvs);
   return true;
 }
 
@@ -762,20 +762,13 @@ __global__ void __launch_bounds__(NT2, 2)
   int cur = -1;  // item whose weights are in shared memory
   uint32_t parity = 0;
   const int total = nitems * nblk;
-  // CV terms of the current item gathered per thread, added to its accumulators when
-  // the CTA moves on to another item (one block reduction per item, not per tile)
-  CvThread cvt;
+  // CV terms of the current item gathered in shared memory, added to its accumulators
+  // when the CTA moves on to another item (one flush per item, not a reduction per tile)
+  __shared__ CvShared cvs;
+  if (threadIdx.x == 0) cvs.v[0] = cvs.v[1] = cvs.v[2] = 0.0;
+  __syncthreads();
   auto flush = [&]() {
-    if (cur < 0 || !items[cur].ep.cvacc) return;
-    const double s0 = block_sum<NT2>(cvt.err, red);
-    const double s1 = block_sum<NT2>(cvt.in, red);
-    const double s2 = block_sum<NT2>(cvt.out, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(items[cur].ep.cvacc + 0, s0);
-      atomicAdd(items[cur].ep.cvacc + 1, s1);
-      atomicAdd(items[cur].ep.cvacc + 2, s2);
-    }
-    cvt = CvThread{};
+    if (cur >= 0) cv_flush(&cvs, items[cur].ep.cvacc);
   };
   while (true) {
     if (threadIdx.x == 0) {
@@ -808,7 +801,7 @@ __global__ void __launch_bounds__(NT2, 2)
     Epilogue<float> ep = I.ep;
     if (ep.esc_count) ep.esc_idx_item = esc_item, ep.esc_item_id = I.item;
     if (!hsolve2_tile<COMP, C>(I.varr, I.g, xs, a0, wr, wc, mid, in, bar, parity, nullptr,
-                               nullptr, nullptr, ep, red, err, &cvt))
+                               nullptr, nullptr, ep, red, err, &cvs))
       return;
     parity ^= 1u;
     __syncthreads();  // the slots alias the next tile's input rows

@@ -334,25 +334,56 @@ static __constant__ int8_t c_slot_pow[NSL] = {0, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0,
                                        1, 0, 1, 2, 0, 0, 0, 0, 1, 3};
 
 
-// CV terms a thread has gathered over the tiles of a persistent sweep (held-out error,
-// scored weight, weight of EMPTY points), reduced over the block once at its end.
-struct CvThread {
-  double err = 0.0, in = 0.0, out = 0.0;
+// CV terms a persistent CTA gathers over its tiles (held-out error, scored weight,
+// weight of EMPTY points) in shared memory: each warp adds its tile's sums with one
+// atomic per term, and the CTA adds the totals to ep.cvacc once (cv_flush).  No
+// register is held across tiles and no block barrier is spent per tile.
+struct CvShared {
+  double v[3];
 };
+
+__device__ __forceinline__ void cv_warp_add(CvShared* cvs, float e, float i, float o) {
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, k);
+    i += __shfl_xor_sync(0xffffffffu, i, k);
+    o += __shfl_xor_sync(0xffffffffu, o, k);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&cvs->v[0], (double)e);
+    atomicAdd(&cvs->v[1], (double)i);
+    atomicAdd(&cvs->v[2], (double)o);
+  }
+}
+
+// The CTA's CV totals into acc (every thread calls it; the caller's barrier
+// precedes it) and the shared sums cleared for the next item.
+__device__ __forceinline__ void cv_flush(CvShared* cvs, double* acc) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (acc) {
+      atomicAdd(acc + 0, cvs->v[0]);
+      atomicAdd(acc + 1, cvs->v[1]);
+      atomicAdd(acc + 2, cvs->v[2]);
+    }
+    cvs->v[0] = cvs->v[1] = cvs->v[2] = 0.0;
+  }
+  __syncthreads();
+}
 
 // Phase 3 of the t-side sweep (shared by the sweep kernels): per-point 5 x 5 solve
 // from the 21 moment slots in shared memory ([NSL][HT][SC]), write of Gamma_hat and
 // status, CV terms and the fused y = Gamma_hat Omega epilogue.  `mid` is shared
-// scratch of at least HT * C + NTH floats (the y epilogue reuses it).  With `cvt`
-// the CV terms are added to the thread's running sums (the kernel reduces them);
-// without, the block adds this tile's terms to ep.cvacc.
+// scratch of at least HT * C + NTH floats (the y epilogue reuses it).  With `cvs`
+// the CV terms go to the CTA's shared sums (the kernel flushes them); without, the
+// block adds this tile's terms to ep.cvacc.
 template <int C, int NTH>
 __device__ __forceinline__ void tside_phase3(const float* __restrict__ slots, int SC, int half,
                                              int P, int xs, int a0, int th,
                                              const double* __restrict__ mu_raw,
                                              float* __restrict__ gamma,
                                              uint8_t* __restrict__ status, const Epilogue<float>& ep,
-                                             double* red, float* mid, CvThread* cvt = nullptr) {
+                                             double* red, float* mid, CvShared* cvs = nullptr) {
   // phase 3: per-point solve, write, epilogue terms (FP32; escalated systems
   // are queued for the float-float kernel; FP64 for the block sums of the CV terms)
   float cv_err = 0.f, cv_in = 0.f, cv_out = 0.f;
@@ -422,10 +453,8 @@ __device__ __forceinline__ void tside_phase3(const float* __restrict__ slots, in
       }
     }
   }
-  if (ep.cvacc && cvt) {
-    cvt->err += (double)cv_err;
-    cvt->in += (double)cv_in;
-    cvt->out += (double)cv_out;
+  if (ep.cvacc && cvs) {
+    cv_warp_add(cvs, cv_err, cv_in, cv_out);
   } else if (ep.cvacc) {
     const double s0 = block_sum<NTH>((double)cv_err, red);
     const double s1 = block_sum<NTH>((double)cv_in, red);
@@ -749,7 +778,9 @@ __global__ void __launch_bounds__(TS_NT, (TR <= 9 && TC <= 9) ? 2 : 1)
   // overlaps the other's arithmetic instead of coinciding with it.
   if (blockIdx.x >= gridDim.x / 2) __nanosleep(3000);
   uint32_t parity = 0;
-  CvThread cvt;  // this thread's CV terms over its tiles (one reduction at the end)
+  __shared__ CvShared cvs;  // this CTA's CV terms over its tiles
+  if (threadIdx.x == 0) cvs.v[0] = cvs.v[1] = cvs.v[2] = 0.0;
+  __syncthreads();
   for (int t = ts_next(g, blockIdx.x); t < g.ntiles; parity ^= 1u) {
     int xs, a0;
     ts_tile(g, t, xs, a0);
@@ -763,7 +794,7 @@ __global__ void __launch_bounds__(TS_NT, (TR <= 9 && TC <= 9) ? 2 : 1)
     ts_phase2<C, TC, COMP>(g, mid2, w2, slots);
     __syncthreads();
     tside_phase3<C, TS_NT>(slots, g.SC, g.half, g.P, xs, a0, th, mu_raw, gamma, status, ep, red,
-                           reinterpret_cast<float*>(mid2), &cvt);
+                           reinterpret_cast<float*>(mid2), &cvs);
     // the y epilogue used the mid rows as scratch: restore their zero halo
     if (ep.y) {
       __syncthreads();
@@ -777,16 +808,7 @@ __global__ void __launch_bounds__(TS_NT, (TR <= 9 && TC <= 9) ? 2 : 1)
     __syncthreads();  // phase 3 read the slots, which alias the next tile's input rows
     t = tn;
   }
-  if (ep.cvacc) {
-    const double s0 = block_sum<TS_NT>(cvt.err, red);
-    const double s1 = block_sum<TS_NT>(cvt.in, red);
-    const double s2 = block_sum<TS_NT>(cvt.out, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(ep.cvacc + 0, s0);
-      atomicAdd(ep.cvacc + 1, s1);
-      atomicAdd(ep.cvacc + 2, s2);
-    }
-  }
+  if (ep.cvacc) cv_flush(&cvs, ep.cvacc);
 }
 
 inline TsGeom ts_geometry(int P, int M1, int M2, int Tr, int Tc) {
