@@ -234,7 +234,7 @@ def record_graph(B, ctx, fn):
     return (g, None) if err is None else (None, str(err))
 
 
-def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5):
+def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5, fp64_peak=None):
     """The plain method at FP64: n = 50 surfaces on a full 16 x 16 grid (65,536 4-D
     covariance points), h = 0.15, FP64 binning, FP64 moment sweeps and solves, and the
     full FP64 eigendecomposition of the 256 x 256 matrixised surface (top 4 returned)."""
@@ -277,10 +277,21 @@ def bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush, steps=5):
     ctx.profile(False)
     per = {kk: v[0] / v[1] for kk, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}
     pts = float(D.P) * D.P
+    # FP64 roofline of the FP64 moment sweep + solve (every output point evaluated):
+    # 2 (15 L1 + 21 L2) + 100 flops per point, L the mean in-grid window lengths
+    roof = None
+    hs = prof.get("cov_hpass_solve")
+    if hs and fp64_peak:
+        M0, M1 = D.m
+        fpp = 2.0 * (15 * mean_window(M0, taps(h[0], M0)) + 21 * mean_window(M1, taps(h[1], M1))) + 100.0
+        ach = fpp * pts / (hs[0] / hs[1] * 1e-3) / 1e12
+        roof = {"kernel": "cov_hpass_solve", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "flops_per_point": fpp,
+                "peak_basis": "measured FP64 FMA peak (fpca_alu_probe)"}
     return {"workload": "dense_2d_full_16x16_n50_h0.15_fp64", "ms_per_step": ms,
             "value": pts / (ms * 1e-3), "unit": UNIT, "cov_points": pts,
             "evals": [float(x) for x in bufs.evals.cpu().numpy()],
-            "ms_per_launch": per,
+            "ms_per_launch": per, "roofline": roof,
             "launch": (f"one CUDA graph per step ({graph.launches} kernels)" if graph is not None
                        else f"kernels launched one by one ({note})"),
             "note": "FP64 throughout; the dense eigensolver returns the top 4 of all 256 "
@@ -810,7 +821,8 @@ def main():
     # ---- the plain method at FP64 on the 16 x 16 workload (reported beside) ----
     c0x = None
     if not args.no_extras:
-        c0x = bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush)
+        c0x = bench_cfg0(torch, np, fs, B, pipeline, ctx, dev, stream, flush,
+                         fp64_peak=(peaks or {}).get("fp64_tflops"))
 
     # ---- the CV bandwidth grid on the sparse workload (reported beside) ----
     cvx = None
