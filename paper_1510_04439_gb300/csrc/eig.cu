@@ -1498,13 +1498,15 @@ fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, T
 
 // Orthonormal basis Q of range(Y) by Cholesky QR: passes = 2 (CholeskyQR2) for the
 // basis of the Rayleigh-Ritz step; one pass between power iterations, where only
-// a well-conditioned basis of the range is needed.
+// a well-conditioned basis of the range is needed.  The first of two passes writes
+// tmp (P x l) and the second reads it, so that k_apply_ff never overwrites the rows
+// it is reading.
 template <typename TS>
-fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, double* Rinv,
-                      double* work, double* part, int passes = 2) {
-  (void)work;
+fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, TS* tmp, double* G,
+                      double* Rinv, double* part, int passes = 2) {
   for (int pass = 0; pass < passes; ++pass) {
-    TS* src = pass == 0 ? Y : Q;
+    TS* src = pass == 0 ? Y : tmp;
+    TS* dst = pass == passes - 1 ? Q : tmp;
     fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
     if (gs != FPCA_OK) return gs;
     // Rinv holds R^-1 as hi and lo parts (l <= 64)
@@ -1519,7 +1521,7 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, double* G, doub
     }
     FPCA_LAUNCHED(ctx, "chol_inv");
     const long long ne = (long long)P * l;
-    k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, Q);
+    k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, dst);
     FPCA_LAUNCHED(ctx, "apply_rinv");
   }
   return FPCA_OK;
@@ -1535,7 +1537,7 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   const int n = full ? P : l;
   const size_t need = WsCarve::round(sizeof(TS) * PP) + WsCarve::round(sizeof(double) * 4) +
                       4 * WsCarve::round(sizeof(TS) * (size_t)P * l) +
-                      3 * WsCarve::round(sizeof(double) * (size_t)l * l) +
+                      2 * WsCarve::round(sizeof(double) * (size_t)l * l) +
                       2 * WsCarve::round(sizeof(double) * (size_t)n * n) +
                       WsCarve::round(sizeof(double) * 2 * n) + WsCarve::round(sizeof(int) * 3 * n) +
                       WsCarve::round(sizeof(double) * gram_part_doubles(P, l, ctx->num_sms)) +
@@ -1553,7 +1555,6 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   TS* Om = carve.take<TS>((size_t)P * l);
   double* G = carve.take<double>((size_t)l * l);
   double* Rinv = carve.take<double>((size_t)l * l);
-  double* work = carve.take<double>((size_t)l * l);
   double* A = carve.take<double>((size_t)n * n);
   double* V = carve.take<double>((size_t)n * n);
   int* order = carve.take<int>(n);
@@ -1594,12 +1595,12 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   fpca_status s = launch_proj<TS>(ctx, P, l, S, Om, Y, ppart);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part, 1);
+    s = orth_cqr2<TS>(ctx, P, l, Y, Q, Z, G, Rinv, part, 1);
     if (s != FPCA_OK) return s;
     s = launch_proj<TS>(ctx, P, l, S, Q, Y, ppart);
     if (s != FPCA_OK) return s;
   }
-  s = orth_cqr2<TS>(ctx, P, l, Y, Q, G, Rinv, work, part);
+  s = orth_cqr2<TS>(ctx, P, l, Y, Q, Z, G, Rinv, part);
   if (s != FPCA_OK) return s;
   s = launch_proj<TS>(ctx, P, l, S, Q, Z, ppart);
   if (s != FPCA_OK) return s;
@@ -1648,7 +1649,7 @@ fpca_status rproj_eig_run(fpca_ctx* ctx, const fpca_grid* g, const void* gamma, 
 // ---------------------------------------------------------------------------
 size_t rproj_ws_bytes(const fpca_ctx* ctx, int P, int l) {
   return 3 * WsCarve::round(sizeof(float) * (size_t)P * l) +
-         5 * WsCarve::round(sizeof(double) * (size_t)l * l) + WsCarve::round(sizeof(double) * 4) +
+         4 * WsCarve::round(sizeof(double) * (size_t)l * l) + WsCarve::round(sizeof(double) * 4) +
          WsCarve::round(sizeof(int) * 3 * (size_t)l) +
          WsCarve::round(sizeof(double) * gram_part_doubles(P, l, ctx->num_sms)) +
          WsCarve::round(sizeof(double) * (5 * (size_t)l * l + l)) + 2048;
@@ -1660,7 +1661,6 @@ void rproj_ws_carve(const fpca_ctx* ctx, WsCarve& c, int P, int l, RprojWs& w) {
   w.Z = c.take<float>((size_t)P * l);
   w.G = c.take<double>((size_t)l * l);
   w.Rinv = c.take<double>((size_t)l * l);
-  w.work = c.take<double>((size_t)l * l);
   w.A = c.take<double>((size_t)l * l);
   w.V = c.take<double>((size_t)l * l);
   w.trace = c.take<double>(4);
@@ -1675,12 +1675,12 @@ fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, 
   fpca_status s = op.apply(op.self, omega, w.Y);
   if (s != FPCA_OK) return s;
   for (int it = 0; it < power_iters; ++it) {
-    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part, 1);
+    s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.Z, w.G, w.Rinv, w.part, 1);
     if (s != FPCA_OK) return s;
     s = op.apply(op.self, w.Q, w.Y);
     if (s != FPCA_OK) return s;
   }
-  s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.G, w.Rinv, w.work, w.part);
+  s = orth_cqr2<float>(ctx, P, l, w.Y, w.Q, w.Z, w.G, w.Rinv, w.part);
   if (s != FPCA_OK) return s;
   s = op.apply(op.self, w.Q, w.Z);
   if (s != FPCA_OK) return s;

@@ -166,7 +166,7 @@ struct RprojOp {
 };
 struct RprojWs {
   float *Y, *Q, *Z;
-  double *G, *Rinv, *work, *A, *V, *trace;
+  double *G, *Rinv, *A, *V, *trace;
   int* order;
   double* part;  // per-block partial Gram products
   double* rr;    // Rayleigh-Ritz eigensolver scratch (5 l^2 + l)

@@ -125,25 +125,36 @@ def test_rproj_eig_small(ctx):
     assert np.allclose(host(fve), fve_ref, rtol=1e-2)
 
 
+H3 = [0.15, 0.15, 0.15]
+ROWS3 = np.array([0, 31, 1023, 16912, 20000, 32767])
+
+
+@pytest.fixture(scope="module")
+def full3(ctx):
+    """n = 2000 volumes on 32^3, the oracle's mean fit, the factored bins, and the
+    oracle's Gamma_hat on the rows ROWS3 (every column)."""
+    D = fs.dense_3d()
+    mu = oracle_mean(D, H3)
+    fac = make_factor(ctx, D, mu)
+    G, st = ob.smooth_cov_rows(D.y, None, mu, D.m, H3, ROWS3)
+    assert np.all(st == sm.STATUS_OK)
+    return D, mu, fac, G
+
+
 @pytest.mark.slow
-def test_full_size_rows_and_tiles(ctx):
+def test_full_size_rows_and_tiles(ctx, full3):
     """n = 2000 volumes on 32^3 (1.07e9 covariance points): Gamma_hat Omega on sampled
     rows and Gamma_hat on 64 random tile pairs (4x4x8 s-box by 4x4x4 t-box) against
     the FP64 oracle evaluated at exactly those output pairs."""
-    D = fs.dense_3d()
-    m, n, h = D.m, D.n, [0.15, 0.15, 0.15]
-    mu = oracle_mean(D, h)
-    fac = make_factor(ctx, D, mu)
+    D, mu, fac, G = full3
+    m, n, h = D.m, D.n, H3
     l = 64
     om = fs.gaussian_test_matrix(D.P, l, 3).astype(np.float32)
     Y = torch.empty(D.P, l, dtype=torch.float32, device=DEV)
     ctx.smooth_cov_apply(m, fac, n, h, dev(om), Y)
     ctx.sync()
     Yh = host(Y)
-    rows = np.array([0, 31, 1023, 16912, 20000, 32767])
-    G, st = ob.smooth_cov_rows(D.y, None, mu, m, h, rows)
-    assert np.all(st == sm.STATUS_OK)
-    e = rel(Yh[rows], G @ om.astype(np.float64))
+    e = rel(Yh[ROWS3], G @ om.astype(np.float64))
     assert e < TOL, e
     rng = np.random.default_rng(2026)
     tiles = []
@@ -164,6 +175,43 @@ def test_full_size_rows_and_tiles(ctx):
         assert np.all(st == sm.STATUS_OK)
         errs.append(rel(got[i], ref))
     assert max(errs) < TOL, max(errs)
+
+
+@pytest.mark.slow
+def test_full_size_eigenpairs(ctx, full3):
+    """The 32^3 step's own projection (k = 10, l = 64, no power step), too large for a
+    whole-surface oracle, checked by what Rayleigh-Ritz fixes at any size: with
+    psi = phi sqrt(dV) and theta = lambda / dV (Eq. 3.1), the psi are orthonormal, the
+    theta descend, psi' Gamma_hat psi = diag(theta) with Gamma_hat psi from the fused
+    apply, that product agrees on the sampled rows with the FP64 oracle's Gamma_hat, and
+    FVE_j is the running sum of lambda over the trace of Gamma_hat times dV, with the
+    diagonal agreeing with the oracle's on the sampled rows."""
+    D, _, fac, G = full3
+    m, n, h, P = D.m, D.n, H3, D.P
+    k, l = 10, 64
+    om = fs.gaussian_test_matrix(P, l, fs.SEED_BASE + 3).astype(np.float32)
+    ev = torch.empty(k, dtype=torch.float64, device=DEV)
+    evec = torch.empty(k, P, dtype=torch.float64, device=DEV)
+    fve = torch.empty(k, dtype=torch.float64, device=DEV)
+    ctx.rproj_eig_factor(m, fac, n, h, dev(om), k, ev, evec, fve, power_iters=0)
+    diag = torch.empty(P, dtype=torch.float64, device=DEV)
+    ctx.smooth_cov_diag(m, fac, n, h, diag)
+    ctx.sync()
+    lam, phi, fv, dg = host(ev), host(evec).T, host(fve), host(diag)
+    dv = 1.0 / P
+    psi, theta = phi * np.sqrt(dv), lam / dv
+    assert np.all(np.diff(lam) <= 0) and lam[-1] > 0
+    assert np.max(np.abs(psi.T @ psi - np.eye(k))) < 1e-6
+    X = np.zeros((P, 16), dtype=np.float32)
+    X[:, :k] = psi
+    Y = torch.empty(P, 16, dtype=torch.float32, device=DEV)
+    ctx.smooth_cov_apply(m, fac, n, h, dev(X), Y)
+    ctx.sync()
+    Z = host(Y)[:, :k].astype(np.float64)
+    assert rel(psi.T @ Z, np.diag(theta)) < TOL
+    assert rel(Z[ROWS3], G @ psi) < TOL
+    assert rel(dg[ROWS3], G[np.arange(len(ROWS3)), ROWS3]) < TOL
+    assert np.allclose(fv, np.cumsum(lam) / (dg.sum() * dv), rtol=1e-9)
 
 
 def test_fused_rejects_what_it_does_not_cover(ctx):
