@@ -13,6 +13,7 @@
 
 #include "fpca_internal.cuh"
 #include "ff.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -211,15 +212,120 @@ __global__ void k_proj_sum(int P, int l, int ranges, const float* __restrict__ p
   Y[(long long)p * l + c] = s;
 }
 
-// Launch shape of k_proj: rows per thread and the k ranges, chosen so that the
-// grid is about two blocks per SM (the kernel's residency).
+// Y = S X as above, for 8 < l <= 20 and P a multiple of 8, with the rows of S
+// brought into shared memory by the TMA engine: a stage holds PJT_KS values of k,
+// each one bulk copy of the tile's (up to) 512 entries of row k, and PJT_ST stages
+// are in flight on mbarriers (issued by thread 0, a slot released by the block
+// barrier that ends its stage), so no register holds a load in flight.  Thread
+// (rg, cg) = (t / 4, t % 4) owns rows 4 rg .. 4 rg + 3 and 256 + 4 rg .. 256 + 4 rg + 3
+// of the tile and columns 5 cg .. 5 cg + 4 (X staged as [k][cg][8], three zero pads):
+// per k, two 128-bit reads of S (a warp's eight row groups are 128 contiguous
+// bytes), a 128-bit and a 32-bit read of X, and 20 paired FMAs over row pairs.
+// Each (p, c) adds its products over k in the order of k_proj: the same bits.
+constexpr int PJT_KS = 8;
+constexpr int PJT_ST = 4;
+constexpr int PJT_ROWS = 512;
+constexpr int PJT_KC = 128;   // k values of X per staged chunk (16 KB)
+
+inline size_t proj_tma_smem(int kc) {
+  return sizeof(float) * ((size_t)PJT_ST * PJT_KS * PJT_ROWS + (size_t)kc * 32);
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_proj_tma(int P, int l, int kb, int kc, const float* __restrict__ S,
+               const float* __restrict__ X, float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(128) float pts[];
+  __shared__ __align__(8) uint64_t bars[PJT_ST];
+  float* ss = pts;                                             // [PJT_ST][PJT_KS][512]
+  float* xs = pts + (size_t)PJT_ST * PJT_KS * PJT_ROWS;        // [kc][4][8]
+  const int t = threadIdx.x, rg = t >> 2, cg = t & 3;
+  const int p_tile = blockIdx.x * PJT_ROWS;
+  const int nrows = min(PJT_ROWS, P - p_tile);                 // a multiple of 8
+  const uint32_t rbytes = (uint32_t)nrows * 4u;
+  const int kbeg = blockIdx.y * kb, kend = min(P, kbeg + kb);
+  if (t == 0) {
+    for (int i = 0; i < PJT_ST; ++i) ptx::mbar_init(ptx::smem_u32(&bars[i]), 1);
+    ptx::fence_mbar_init();
+  }
+  float2 acc[4][5];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  int g = 0;   // stages consumed before this chunk (slot and phase of the next one)
+  for (int k0 = kbeg; k0 < kend; k0 += kc) {
+    const int ns = min(kend - k0, kc) / PJT_KS;   // kb, kc and P are multiples of PJT_KS
+    __syncthreads();   // the barriers' init (first chunk) / last chunk's reads of X
+    for (int e = t; e < ns * PJT_KS * 32; e += 256) {
+      const int j = e & 7, c = ((e >> 3) & 3) * 5 + j;
+      xs[e] = (j < 5 && c < l) ? X[(long long)(k0 + (e >> 5)) * l + c] : 0.f;
+    }
+    // stage st of this chunk into slot (g + st) % PJT_ST (thread 0)
+    auto issue = [&](int st) {
+      const int slot = (g + st) % PJT_ST;
+      const uint32_t bar = ptx::smem_u32(&bars[slot]);
+      ptx::mbar_arrive_expect_tx(bar, rbytes * PJT_KS);
+      for (int u = 0; u < PJT_KS; ++u)
+        ptx::bulk_load(ptx::smem_u32(ss + ((size_t)slot * PJT_KS + u) * PJT_ROWS),
+                       S + (long long)(k0 + st * PJT_KS + u) * P + p_tile, rbytes, bar);
+    };
+    if (t == 0)
+      for (int st = 0; st < min(ns, PJT_ST); ++st) issue(st);
+    __syncthreads();   // X staged
+    for (int st = 0; st < ns; ++st) {
+      const int gi = g + st, slot = gi % PJT_ST;
+      const bool landed = ptx::mbar_wait(ptx::smem_u32(&bars[slot]), (gi / PJT_ST) & 1, err);
+      if (landed) {
+        const float* sb = ss + (size_t)slot * PJT_KS * PJT_ROWS;
+        const float* xb = xs + (size_t)st * PJT_KS * 32 + cg * 8;
+#pragma unroll
+        for (int u = 0; u < PJT_KS; ++u) {
+          const float4 a = *reinterpret_cast<const float4*>(sb + u * PJT_ROWS + 4 * rg);
+          const float4 b = *reinterpret_cast<const float4*>(sb + u * PJT_ROWS + 256 + 4 * rg);
+          const float4 x4 = *reinterpret_cast<const float4*>(xb + u * 32);
+          const float xv[5] = {x4.x, x4.y, x4.z, x4.w, xb[u * 32 + 4]};
+          const float2 sp[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                make_float2(b.x, b.y), make_float2(b.z, b.w)};
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            const float2 xx = make_float2(xv[c], xv[c]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r][c] = __ffma2_rn(sp[r], xx, acc[r][c]);
+          }
+        }
+      }
+      // every thread is done with the slot; a copy that never landed ends the block
+      if (__syncthreads_or(!landed)) return;
+      if (t == 0 && st + PJT_ST < ns) issue(st + PJT_ST);
+    }
+    g += ns;
+  }
+  float* out = part + (long long)blockIdx.y * l * P + p_tile;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const int col = cg * 5 + c;
+    if (col >= l) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = h * 256 + 4 * rg;
+      if (row < nrows)
+        *reinterpret_cast<float4*>(out + (long long)col * P + row) =
+            make_float4(acc[2 * h][c].x, acc[2 * h][c].y, acc[2 * h + 1][c].x, acc[2 * h + 1][c].y);
+    }
+  }
+}
+
+// Launch shape of k_proj / k_proj_tma: rows per thread and the k ranges, chosen so
+// that the grid is about two blocks per SM (the kernels' residency).
 struct ProjShape {
   int rpt, lm, tiles, kb, kc, ranges;
+  bool tma;   // k_proj_tma (8 < l <= 20, P a multiple of 8)
 };
 
 inline ProjShape proj_shape(int P, int l, int num_sms) {
   ProjShape s;
   s.lm = l <= 8 ? 8 : l <= 20 ? 20 : l <= 24 ? 24 : 64;
+  s.tma = l > 8 && l <= 20 && P % PJT_KS == 0;
   s.rpt = l <= 8 ? 4 : l <= 24 ? 2 : 1;
   const int rows = PJ_WARPS * 32 * s.rpt;
   s.tiles = (P + rows - 1) / rows;
@@ -227,7 +333,7 @@ inline ProjShape proj_shape(int P, int l, int num_sms) {
   constexpr int q = 2 * PJ_U;
   s.kb = ((P + want - 1) / want + q - 1) / q * q;
   s.ranges = (P + s.kb - 1) / s.kb;
-  s.kc = min(s.kb, (32768 / (int)sizeof(float) / s.lm) / q * q);   // <= 32 KB of X
+  s.kc = s.tma ? min(s.kb, PJT_KC) : min(s.kb, (32768 / (int)sizeof(float) / s.lm) / q * q);
   return s;
 }
 
@@ -1484,7 +1590,12 @@ fpca_status launch_proj(fpca_ctx* ctx, int P, int l, const TS* S, const TS* X, T
   } else {
     if (l > 64) return fpca_fail(ctx, FPCA_E_UNSUPPORTED, "projection built for l <= 64");
     const ProjShape sh = proj_shape(P, l, ctx->num_sms);
-    if (sh.lm == 8) proj_launch<8, 4>(ctx, sh, P, l, S, X, part);
+    if (sh.tma) {
+      const size_t smem = proj_tma_smem(sh.kc);
+      cudaFuncSetAttribute(k_proj_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_proj_tma<<<dim3(sh.tiles, sh.ranges), 256, smem, ctx->stream>>>(P, l, sh.kb, sh.kc, S, X,
+                                                                       part, ctx->d_err);
+    } else if (sh.lm == 8) proj_launch<8, 4>(ctx, sh, P, l, S, X, part);
     else if (sh.lm == 20) proj_launch<20, 2>(ctx, sh, P, l, S, X, part);
     else if (sh.lm == 24) proj_launch<24, 2>(ctx, sh, P, l, S, X, part);
     else proj_launch<64, 1>(ctx, sh, P, l, S, X, part);

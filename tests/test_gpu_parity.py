@@ -351,12 +351,14 @@ def test_eig_dense_and_rproj_vs_oracle(ctx, B):
 
 @pytest.mark.parametrize("m,l", [((23, 31), 6), ((23, 31), 12), ((23, 31), 18), ((17, 45), 24),
                                  ((17, 45), 40), ((40, 41), 64),
-                                 ((22, 31), 6), ((22, 31), 18), ((34, 45), 24), ((80, 80), 18)])
+                                 ((22, 31), 6), ((22, 31), 18), ((34, 45), 24), ((24, 30), 12),
+                                 ((80, 80), 18)])
 def test_rproj_widths_and_ragged_grids(ctx, m, l):
     """Random projection at every width the projection kernel is built for (l <= 8, 20,
     24, 64), on grids whose node counts leave ragged row tiles and k ranges, with a
-    ragged domain; the same Omega on both sides (80 x 80: k ranges longer than one
-    staged chunk of Omega)."""
+    ragged domain; the same Omega on both sides.  For 8 < l <= 20 and P a multiple of 8
+    (24 x 30, 80 x 80) the rows of Sigma arrive by bulk copies; 80 x 80 has k ranges
+    longer than one staged chunk of Omega and a half-filled last row tile."""
     P = m[0] * m[1]
     rng = np.random.default_rng(l + P)
     s = (np.arange(m[0]) + 0.5) / m[0]
