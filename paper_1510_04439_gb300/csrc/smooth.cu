@@ -1106,9 +1106,9 @@ size_t vpass2_smem(int Ma, int ntp, bool with_sub) {
                           (with_sub ? (size_t)Ma * VCOLS : 0));
 }
 
-// FP64 fits of the queued (escalated) points: one thread per point, so the
-// slow FP64 pipe runs full warps; writes Gamma_hat, status and the epilogue
-// terms the t-side kernel skipped.
+// Float-float fits of the queued (escalated) points, whose FP32 elimination met a
+// pivot below ESCALATE_F32 of its diagonal: one thread per point; writes
+// Gamma_hat, status and the epilogue terms the t-side kernel skipped.
 __global__ void __launch_bounds__(256)
     k_escalated(int P, const float* __restrict__ esc_slots, const int2* __restrict__ esc_idx,
                 const unsigned* __restrict__ esc_count, int cap, const double* __restrict__ mu_raw,

@@ -100,6 +100,79 @@ def test_sweeps_vs_oracle(B, m, T):
         assert rel_l2(g2[ok], g1[ok]) <= 1e-5
 
 
+def pivot_ratios(m, h, W, V, ne):
+    """Smallest Cholesky pivot ratio (Schur-complement diagonal over the original
+    diagonal, natural order) of every output pair's (2d+1)^2 system, from the FP64
+    moments; 0 where a pivot is not positive, NaN where the window is empty or has
+    fewer than 2d+1 non-empty bins (those are not solved)."""
+    d = len(m)
+    D = 2 * d + 1
+    S, _ = og.moments(m, h, W, V)
+    unit = [tuple(int(j > 0 and k == j - 1) for k in range(2 * d)) for j in range(D)]
+    P = S[(0,) * (2 * d)].shape[0]
+    A = np.empty((P * P, D, D))
+    for i in range(D):
+        for j in range(D):
+            A[:, i, j] = S[tuple(a + b for a, b in zip(unit[i], unit[j]))].ravel()
+    diag = np.einsum("nii->ni", A).copy()
+    ratio = np.full(P * P, np.inf)
+    live = np.ones(P * P, dtype=bool)
+    for k in range(D):
+        piv = A[:, k, k]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rk = np.where(diag[:, k] > 0, piv / diag[:, k], 0.0)
+        ratio = np.where(live, np.minimum(ratio, rk), ratio)
+        live &= piv > 0
+        safe = np.where(piv > 0, piv, 1.0)
+        for i in range(k + 1, D):
+            lik = A[:, i, k] / safe
+            A[:, i, k + 1:] -= lik[:, None] * A[:, k, k + 1:]
+    ratio[~live] = 0.0
+    ratio[(diag[:, 0] <= 0) | (ne.ravel() < D)] = np.nan
+    return ratio.reshape(P, P)
+
+
+def test_escalated_points_vs_fp64(B):
+    """The points whose FP32 elimination meets a pivot below 1e-2 of its diagonal are
+    solved again in float-float (about 48 bits) rather than FP64.  Their inputs are
+    the FP32 moments, rounded to about u = 2^-24 of their scale, so the fitted value
+    moves by about u times the system's conditioning, which the smallest pivot ratio
+    r bounds (kappa ~ 1/r); the float-float rounding (~2^-48 kappa) is 2^24 times
+    smaller, so an FP64 solve of the same moments would give the same values to that
+    order.  Checked against the FP64 oracle (FP64 moments, FP64 solve) on a disk grid
+    with 20 % dropout, where the one-sided windows at the rim give small ratios: per
+    band of r, the rel-L2 error on points both sides fit stays within
+    64 u / r_low (r_low the band's lower edge), the points with r >= 1e-2 (FP32 solve
+    only) within 64 u / 1e-2."""
+    ctx = B.Context(0)
+    m = (32, 32)
+    h = same_taps_h(m, 4)
+    C, W, V = dense_bins(m, 60, seed=77)
+    P = m[0] * m[1]
+    rG, rst = og.smooth_cov(m, h, C, W, V)
+    ratio = pivot_ratios(m, h, W, V, og.nonempty(m, h, C))
+    G = torch.empty(P, P, dtype=torch.float32, device=DEV)
+    st = torch.empty(P, P, dtype=torch.uint8, device=DEV)
+    ctx.smooth_cov_project(m, dev(C, torch.int32), dev(W, torch.float32), dev(V, torch.float32),
+                           [h], B.F32C, gamma=G, status=st)
+    ctx.sync()
+    g = G.cpu().numpy().astype(np.float64)
+    s = st.cpu().numpy()
+    both = (rst == sm.STATUS_OK) & (s == sm.STATUS_OK)
+    u = 2.0 ** -24
+    report = {}
+    for lo, hi in [(1e-2, np.inf), (1e-3, 1e-2), (1e-4, 1e-3), (1e-5, 1e-4)]:
+        sel = both & (ratio >= lo) & (ratio < hi)
+        if not sel.any():
+            continue
+        err = rel_l2(g[sel], rG[sel])
+        worst = float(np.max(np.abs(g[sel] - rG[sel])) / np.max(np.abs(rG[sel])))
+        report[lo] = (int(sel.sum()), err, worst)
+        assert err <= 64 * u / lo, (lo, report)
+    print("escalation bands (r_low: points, rel-L2, max |err| / max |Gamma|):", report)
+    assert sum(v[0] for lo, v in report.items() if lo < 1e-2) >= 1000, report
+
+
 @pytest.mark.parametrize("kern", [1, 2])
 def test_sweeps_projection_epilogue(B, kern):
     """y = Gamma_hat Omega fused into the sweep (every pair fitted, no mirror)."""
