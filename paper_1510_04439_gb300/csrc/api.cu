@@ -201,15 +201,17 @@ fpca_status fpca_create(fpca_ctx** out, int device, void* cuda_stream) {
   }
   ctx->num_sms = prop.multiProcessorCount;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
-  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) {
+  // the device error word and, after it, the last-block ticket of the Gram kernel
+  if (cudaMalloc(&ctx->d_err, 2 * sizeof(int)) != cudaSuccess) {
     delete ctx;
     return FPCA_E_OOM;
   }
-  if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(ctx->d_err, 0, 2 * sizeof(int)) != cudaSuccess) {
     cudaFree(ctx->d_err);
     delete ctx;
     return FPCA_E_CUDA;
   }
+  ctx->d_ticket = reinterpret_cast<unsigned*>(ctx->d_err + 1);
   *out = ctx;
   return FPCA_OK;
 }
