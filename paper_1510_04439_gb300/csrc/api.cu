@@ -201,17 +201,15 @@ fpca_status fpca_create(fpca_ctx** out, int device, void* cuda_stream) {
   }
   ctx->num_sms = prop.multiProcessorCount;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
-  // the device error word and, after it, the last-block ticket of the Gram kernel
-  if (cudaMalloc(&ctx->d_err, 2 * sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) {
     delete ctx;
     return FPCA_E_OOM;
   }
-  if (cudaMemset(ctx->d_err, 0, 2 * sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
     cudaFree(ctx->d_err);
     delete ctx;
     return FPCA_E_CUDA;
   }
-  ctx->d_ticket = reinterpret_cast<unsigned*>(ctx->d_err + 1);
   *out = ctx;
   return FPCA_OK;
 }

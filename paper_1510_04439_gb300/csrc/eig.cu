@@ -373,17 +373,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - z)) + (b - z);
 }
 
-// This block's partial product over rows [r0, r1): entry e = i l + j of A'B into
-// out[e], by a block of NT threads with at most EPT entries per thread.
-template <typename TX, int EPT, int NT>
-__device__ __forceinline__ void cross_gram_rows(int l, int r0, int r1, const TX* __restrict__ A,
-                                                const TX* __restrict__ B, double* __restrict__ out,
-                                                TX* As, TX* Bs) {
-  const int ne = l * l, nt = NT;
-  float hs[EPT], hc[EPT];
-  double dsum[EPT];
+template <typename TX>
+__global__ void __launch_bounds__(256)
+    k_cross_gram(int P, int l, int rows, const TX* __restrict__ A, const TX* __restrict__ B,
+                 double* __restrict__ part) {
+  __shared__ TX As[GR_SUB * 64], Bs[GR_SUB * 64];
+  const int r0 = blockIdx.x * rows, r1 = min(P, r0 + rows);
+  const int ne = l * l;
+  // up to 16 entries per thread (l <= 64, 256 threads)
+  float hs[16], hc[16];
+  double dsum[16];
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
+  for (int k = 0; k < 16; ++k) {
     hs[k] = 0.f;
     hc[k] = 0.f;
     dsum[k] = 0.0;
@@ -391,14 +392,14 @@ __device__ __forceinline__ void cross_gram_rows(int l, int r0, int r1, const TX*
   for (int rb = r0; rb < r1; rb += GR_SUB) {
     const int nr = min(GR_SUB, r1 - rb);
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * l; e += nt) {
+    for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
       As[e] = A[(long long)rb * l + e];
       Bs[e] = B[(long long)rb * l + e];
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = threadIdx.x + k * nt;
+    for (int k = 0; k < 16; ++k) {
+      const int e = threadIdx.x + k * 256;
       if (e >= ne) break;
       const int i = e / l, j = e - (e / l) * l;
       if constexpr (sizeof(TX) == 4) {
@@ -422,21 +423,12 @@ __device__ __forceinline__ void cross_gram_rows(int l, int r0, int r1, const TX*
     }
   }
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int e = threadIdx.x + k * nt;
+  for (int k = 0; k < 16; ++k) {
+    const int e = threadIdx.x + k * 256;
     if (e >= ne) break;
-    out[e] = sizeof(TX) == 4 ? (double)hs[k] + (double)hc[k] : dsum[k];
+    part[(long long)blockIdx.x * ne + e] =
+        sizeof(TX) == 4 ? (double)hs[k] + (double)hc[k] : dsum[k];
   }
-}
-
-template <typename TX>
-__global__ void __launch_bounds__(256)
-    k_cross_gram(int P, int l, int rows, const TX* __restrict__ A, const TX* __restrict__ B,
-                 double* __restrict__ part) {
-  __shared__ TX As[GR_SUB * 64], Bs[GR_SUB * 64];
-  const int r0 = blockIdx.x * rows, r1 = min(P, r0 + rows);
-  // up to 16 entries per thread (l <= 64, 256 threads)
-  cross_gram_rows<TX, 16, 256>(l, r0, r1, A, B, part + (long long)blockIdx.x * l * l, As, Bs);
 }
 
 // G = sum over blocks of the partial products (FP64), one warp per entry: each
@@ -507,11 +499,11 @@ __device__ __forceinline__ ff::F2 ff_of(double x) {
 inline size_t chol_ff_smem(int l) { return sizeof(float) * (4 * (size_t)l * (l + 1) + 2 * l + 1); }
 inline int chol_ff_threads(int l) { return l <= 32 ? (l * l + 31) / 32 * 32 : 1024; }
 
-// The factorisation and inverse by the whole block (any size; OWN entries of the
-// l x l arrays per thread, OWN * blockDim.x >= l^2); G may be in shared memory.
 template <int OWN>
-__device__ __forceinline__ void chol_ff_block(int l, const double* G, float* __restrict__ Ih,
-                                              float* __restrict__ Il, float* chs) {
+__global__ void __launch_bounds__(1024) k_chol_ff(int l, const double* __restrict__ G,
+                                                  float* __restrict__ Ih,
+                                                  float* __restrict__ Il) {
+  extern __shared__ float chs[];
   const int ld = l + 1;
   float* Gh = chs;              // [l][ld] trailing matrix, then R by rows
   float* Gl = Gh + l * ld;
@@ -611,94 +603,6 @@ __device__ __forceinline__ void chol_ff_block(int l, const double* G, float* __r
       Il[i * l + c] = x.lo;
     }
   }
-}
-
-template <int OWN>
-__global__ void __launch_bounds__(1024) k_chol_ff(int l, const double* __restrict__ G,
-                                                  float* __restrict__ Ih,
-                                                  float* __restrict__ Il) {
-  extern __shared__ float chs[];
-  chol_ff_block<OWN>(l, G, Ih, Il, chs);
-}
-
-// Cholesky QR's Gram matrix and factorisation in one launch for FP32 blocks and
-// l <= 32: GC_NT-thread blocks of gram_chol_rows() rows (at most GC_NB blocks)
-// each write their partial product of A'B (the compensated sums of
-// k_cross_gram); the last block to finish, found by a ticket counter (no block
-// waits for another), adds the partials in block order into G (FP64, in shared
-// memory and, if G_out is given, in global memory), then, if Ih is given, factors
-// G = R'R and forms R^-1 in float-float (chol_ff_block), and resets the ticket
-// for the next launch on the stream.
-constexpr int GC_NT = 512;
-constexpr int GC_NB = 32;
-
-inline int gram_chol_rows(int P) { return max(16, ((P + GC_NB - 1) / GC_NB + 15) / 16 * 16); }
-
-template <int OWN>
-__global__ void __launch_bounds__(GC_NT)
-    k_gram_chol(int P, int l, int rows, const float* __restrict__ A, const float* __restrict__ B,
-                double* __restrict__ part, double* __restrict__ G_out,
-                unsigned* __restrict__ ticket, float* __restrict__ Ih, float* __restrict__ Il) {
-  __shared__ float As[GR_SUB * 32], Bs[GR_SUB * 32];
-  __shared__ double Gs[32 * 32];
-  __shared__ int is_last;
-  extern __shared__ float chs[];
-  const int ne = l * l, nb = gridDim.x;
-  const int r0 = blockIdx.x * rows, r1 = min(P, r0 + rows);
-  cross_gram_rows<float, 2, GC_NT>(l, r0, r1, A, B, part + (long long)blockIdx.x * ne, As, Bs);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == (unsigned)(nb - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    double v[GC_NB];
-#pragma unroll
-    for (int b = 0; b < GC_NB; ++b) v[b] = b < nb ? __ldcg(part + (long long)b * ne + e) : 0.0;
-    double sum = 0.0;
-#pragma unroll
-    for (int b = 0; b < GC_NB; ++b) sum += v[b];
-    Gs[e] = sum;
-    if (G_out) G_out[e] = sum;
-  }
-  __syncthreads();
-  if (Ih) chol_ff_block<OWN>(l, Gs, Ih, Il, chs);
-  if (threadIdx.x == 0) *ticket = 0u;
-}
-
-// G = A'B (l x l, FP64) and, if Ih is given, R^-1 of G = R'R (float-float hi and
-// lo parts, l x l each): one launch (k_gram_chol) for FP32 blocks with l <= 32,
-// else the partial products, their sum and the factorisation as three.
-template <typename TX>
-fpca_status launch_gram_chol(fpca_ctx* ctx, int P, int l, const TX* A, const TX* B,
-                             double* part, double* G, float* Ih, float* Il, const char* name) {
-  if constexpr (sizeof(TX) == 4) {
-    if (l <= 32) {
-      const int rows = gram_chol_rows(P);
-      const int nb = (P + rows - 1) / rows;
-      const size_t smem = Ih ? chol_ff_smem(l) : 0;
-      if (l * l <= GC_NT)
-        k_gram_chol<1><<<nb, GC_NT, smem, ctx->stream>>>(P, l, rows, A, B, part, G,
-                                                         ctx->d_ticket, Ih, Il);
-      else
-        k_gram_chol<2><<<nb, GC_NT, smem, ctx->stream>>>(P, l, rows, A, B, part, G,
-                                                         ctx->d_ticket, Ih, Il);
-      FPCA_LAUNCHED(ctx, name);
-      return FPCA_OK;
-    }
-  }
-  fpca_status gs = launch_cross_gram<TX>(ctx, P, l, A, B, part, G, name);
-  if (gs != FPCA_OK || !Ih) return gs;
-  if (l <= 32)
-    k_chol_ff<1><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
-  else {
-    cudaFuncSetAttribute(k_chol_ff<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)chol_ff_smem(l));
-    k_chol_ff<4><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
-  }
-  FPCA_LAUNCHED(ctx, "chol_inv");
-  return FPCA_OK;
 }
 
 // Q = Y R^-1 with R^-1 from k_chol_ff, one thread per entry (row r, column j):
@@ -1714,11 +1618,19 @@ fpca_status orth_cqr2(fpca_ctx* ctx, int P, int l, TS* Y, TS* Q, TS* tmp, double
   for (int pass = 0; pass < passes; ++pass) {
     TS* src = pass == 0 ? Y : tmp;
     TS* dst = pass == passes - 1 ? Q : tmp;
+    fpca_status gs = launch_cross_gram<TS>(ctx, P, l, src, src, part, G, "gram");
+    if (gs != FPCA_OK) return gs;
     // Rinv holds R^-1 as hi and lo parts (l <= 64)
     float* Ih = reinterpret_cast<float*>(Rinv);
     float* Il = Ih + l * l;
-    fpca_status gs = launch_gram_chol<TS>(ctx, P, l, src, src, part, G, Ih, Il, "gram");
-    if (gs != FPCA_OK) return gs;
+    if (l <= 32)
+      k_chol_ff<1><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
+    else {
+      cudaFuncSetAttribute(k_chol_ff<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)chol_ff_smem(l));
+      k_chol_ff<4><<<1, chol_ff_threads(l), chol_ff_smem(l), ctx->stream>>>(l, G, Ih, Il);
+    }
+    FPCA_LAUNCHED(ctx, "chol_inv");
     const long long ne = (long long)P * l;
     k_apply_ff<TS><<<(int)((ne + 255) / 256), 256, 0, ctx->stream>>>(P, l, src, Ih, Il, dst);
     FPCA_LAUNCHED(ctx, "apply_rinv");
@@ -1803,7 +1715,7 @@ fpca_status rproj_typed(fpca_ctx* ctx, const fpca_grid* g, const TG* gamma, cons
   if (s != FPCA_OK) return s;
   s = launch_proj<TS>(ctx, P, l, S, Q, Z, ppart);
   if (s != FPCA_OK) return s;
-  s = launch_gram_chol<TS>(ctx, P, l, Q, Z, part, A, nullptr, nullptr, "ritz_gram");
+  s = launch_cross_gram<TS>(ctx, P, l, Q, Z, part, A, "ritz_gram");
   if (s != FPCA_OK) return s;
   {
     fpca_status js = launch_jacobi_rr(ctx, l, A, V, rrs);
@@ -1883,7 +1795,7 @@ fpca_status rproj_operator(fpca_ctx* ctx, int P, int l, int k, int power_iters, 
   if (s != FPCA_OK) return s;
   s = op.apply(op.self, w.Q, w.Z);
   if (s != FPCA_OK) return s;
-  s = launch_gram_chol<float>(ctx, P, l, w.Q, w.Z, w.part, w.A, nullptr, nullptr, "ritz_gram");
+  s = launch_cross_gram<float>(ctx, P, l, w.Q, w.Z, w.part, w.A, "ritz_gram");
   if (s != FPCA_OK) return s;
   s = launch_jacobi_rr(ctx, l, w.A, w.V, w.rr);
   if (s != FPCA_OK) return s;

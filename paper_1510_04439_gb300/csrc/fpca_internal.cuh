@@ -21,7 +21,6 @@ struct fpca_ctx {
   void* ws = nullptr;        // workspace, grown on demand
   size_t ws_bytes = 0;
   int* d_err = nullptr;      // device error word (DERR_*)
-  unsigned* d_ticket = nullptr;  // last-block counter of k_gram_chol (0 between launches)
   uint64_t launches = 0;     // kernels queued by this context
   int num_sms = 0;
   size_t smem_optin = 0;
